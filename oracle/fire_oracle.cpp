@@ -1,0 +1,817 @@
+// CPU oracle for the renderer hot path -- TEST INFRASTRUCTURE ONLY.
+//
+// Plain single-threaded C++17, compiled with -O2 -ffp-contract=off so that no
+// multiply-add is fused unless written as std::fmaf.  Only tests/, the smoke
+// check and the benchmark's CPU-baseline leg load it.  It shares no code,
+// header or constant with the CUDA library; both restate the same definitions
+// (listed per function below) independently.
+//
+// Precision: the plain method is FP32 (every workload of this build is FP32),
+// and integer decisions taken from floats (Morton codes, nearest-hit argmin,
+// shadow visibility) are taken in FP32 on both sides.  The operation order of
+// each FP32 expression is fixed here and documented; the gradient checks use
+// the FP64 twin at the end of the file.
+//
+// Parity unpinned: tree quality (node visits per ray) is reported, not pinned.
+#include "fire_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <vector>
+
+namespace {
+
+// float(pi) and float(1/pi), nearest floats.
+const float kPiF = 3.14159265358979323846f;
+const float kInvPiF = 0.318309886183790671538f;
+const double kPiD = 3.14159265358979323846;
+const float kInfF = std::numeric_limits<float>::infinity();
+
+struct V3 { float x, y, z; };
+static inline V3 mk(float x, float y, float z) { V3 r = {x, y, z}; return r; }
+static inline V3 sub3(V3 a, V3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline V3 add3(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static inline V3 neg3(V3 a) { return mk(-a.x, -a.y, -a.z); }
+// dot(a,b) = fma(ax,bx, fma(ay,by, az*bz))
+static inline float dot3(V3 a, V3 b) { return std::fmaf(a.x, b.x, std::fmaf(a.y, b.y, a.z * b.z)); }
+// cross(a,b).x = fma(ay,bz, -(az*by)), cyclic
+static inline V3 cross3(V3 a, V3 b) {
+  return mk(std::fmaf(a.y, b.z, -(a.z * b.y)), std::fmaf(a.z, b.x, -(a.x * b.z)),
+            std::fmaf(a.x, b.y, -(a.y * b.x)));
+}
+// normalize(v) = v / sqrt(dot(v,v)), three correctly rounded divisions
+static inline V3 normalize3(V3 v) {
+  float len = std::sqrt(dot3(v, v));
+  return mk(v.x / len, v.y / len, v.z / len);
+}
+
+struct D3 { double x, y, z; };
+static inline D3 dk(double x, double y, double z) { D3 r = {x, y, z}; return r; }
+static inline D3 dsub(D3 a, D3 b) { return dk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static inline D3 dcross(D3 a, D3 b) {
+  return dk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static inline D3 dnorm(D3 v) { double l = std::sqrt(ddot(v, v)); return dk(v.x / l, v.y / l, v.z / l); }
+static inline D3 tod(V3 v) { return dk(v.x, v.y, v.z); }
+
+struct Box { float lo[3], hi[3]; };
+
+}  // namespace
+
+struct orc_scene {
+  int64_t nv = 0, nt = 0;
+  int32_t nmat = 0, nbody = 0;
+  std::vector<float> rest;        // [nv*4]
+  std::vector<uint32_t> idx;      // [nt*3]
+  std::vector<uint32_t> tri_mat;  // [nt]
+  std::vector<uint16_t> vbody;    // [nv]
+  std::vector<orc_material> mats;
+  // per-frame state
+  std::vector<V3> world;          // [nv]
+  bool built = false;
+  std::vector<uint64_t> morton;   // by original triangle
+  std::vector<uint32_t> order;    // sorted position -> original triangle
+  std::vector<int32_t> child;     // [(nt-1)*2] Karras codes
+  std::vector<int32_t> parent;    // [2nt-1]
+  std::vector<Box> box;           // [2nt-1] by Karras code
+  float cb[6] = {0, 0, 0, 0, 0, 0};  // centroid bounds
+  Box scene_box;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// §IV-C / §IV-B-3 step (4): per-body rigid transform of the rest vertices.
+// x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row of the 3x4 matrix.
+// ---------------------------------------------------------------------------
+void transform(orc_scene& S, const float* xf) {
+  S.world.resize(S.nv);
+  for (int64_t i = 0; i < S.nv; ++i) {
+    const float* m = xf + 12 * (int64_t)S.vbody[i];
+    float x = S.rest[4 * i], y = S.rest[4 * i + 1], z = S.rest[4 * i + 2];
+    S.world[i] = mk(std::fmaf(m[0], x, std::fmaf(m[1], y, std::fmaf(m[2], z, m[3]))),
+                    std::fmaf(m[4], x, std::fmaf(m[5], y, std::fmaf(m[6], z, m[7]))),
+                    std::fmaf(m[8], x, std::fmaf(m[9], y, std::fmaf(m[10], z, m[11]))));
+  }
+}
+
+inline void tri_verts(const orc_scene& S, int64_t t, V3& a, V3& b, V3& c) {
+  a = S.world[S.idx[3 * t]];
+  b = S.world[S.idx[3 * t + 1]];
+  c = S.world[S.idx[3 * t + 2]];
+}
+
+Box tri_box(const orc_scene& S, int64_t t) {
+  V3 a, b, c;
+  tri_verts(S, t, a, b, c);
+  Box r;
+  const float A[3] = {a.x, a.y, a.z}, B[3] = {b.x, b.y, b.z}, C[3] = {c.x, c.y, c.z};
+  for (int k = 0; k < 3; ++k) {
+    r.lo[k] = std::min(A[k], std::min(B[k], C[k]));
+    r.hi[k] = std::max(A[k], std::max(B[k], C[k]));
+  }
+  return r;
+}
+
+Box box_union(const Box& a, const Box& b) {
+  Box r;
+  for (int k = 0; k < 3; ++k) {
+    r.lo[k] = std::min(a.lo[k], b.lo[k]);
+    r.hi[k] = std::max(a.hi[k], b.hi[k]);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Morton code of a centroid: q_a = min(floor((c_a - lo_a) * s_a), 2^21 - 1),
+// s_a = 2^21 / (hi_a - lo_a) (0 if hi_a == lo_a); bit k of q_x -> bit 3k+2,
+// of q_y -> 3k+1, of q_z -> 3k.  Written as a plain per-bit loop.
+// ---------------------------------------------------------------------------
+uint32_t quantise(float c, float lo, float s) {
+  float f = (c - lo) * s;
+  if (!(f > 0.0f)) return 0u;
+  if (f >= 2097151.0f) return 2097151u;
+  return (uint32_t)f;
+}
+
+uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz) {
+  uint64_t code = 0;
+  for (int k = 0; k < 21; ++k) {
+    code |= (uint64_t)((qx >> k) & 1u) << (3 * k + 2);
+    code |= (uint64_t)((qy >> k) & 1u) << (3 * k + 1);
+    code |= (uint64_t)((qz >> k) & 1u) << (3 * k);
+  }
+  return code;
+}
+
+int clz64(uint64_t x) { int n = 0; for (int b = 63; b >= 0 && !((x >> b) & 1u); --b) ++n; return n; }
+int clz32(uint32_t x) { int n = 0; for (int b = 31; b >= 0 && !((x >> b) & 1u); --b) ++n; return n; }
+
+// Length of the common prefix of sorted keys i and j, keys augmented with
+// their position when equal (Karras 2012).
+int delta(const std::vector<uint64_t>& k, int64_t i, int64_t j) {
+  if (k[i] != k[j]) return clz64(k[i] ^ k[j]);
+  return 64 + clz32((uint32_t)i ^ (uint32_t)j);
+}
+
+// Top-down construction of the same radix tree the parallel Karras build
+// produces: a range [first, last] is split after the last position that
+// still shares more than delta(first, last) prefix bits with `first`
+// (binary search); the child covering [first, split] is numbered `split`,
+// the one covering [split+1, last] is numbered `split+1`; one-element ranges
+// are leaves (code T-1+position).
+void build_range(orc_scene& S, const std::vector<uint64_t>& k, int32_t node, int64_t first,
+                 int64_t last) {
+  const int64_t T = S.nt;
+  int common = delta(k, first, last);
+  int64_t lo = first, hi = last - 1;  // invariant: answer in [lo, hi], delta(first, lo) > common or lo==first
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) / 2;
+    if (delta(k, first, mid) > common) lo = mid; else hi = mid - 1;
+  }
+  int64_t split = lo;
+  int32_t left = (split == first) ? (int32_t)(T - 1 + split) : (int32_t)split;
+  int32_t right = (split + 1 == last) ? (int32_t)(T - 1 + split + 1) : (int32_t)(split + 1);
+  S.child[2 * node] = left;
+  S.child[2 * node + 1] = right;
+  S.parent[left] = node;
+  S.parent[right] = node;
+  if (split != first) build_range(S, k, (int32_t)split, first, split);
+  if (split + 1 != last) build_range(S, k, (int32_t)(split + 1), split + 1, last);
+}
+
+Box refit_node(orc_scene& S, int32_t code) {
+  const int64_t T = S.nt;
+  if (code >= T - 1) {
+    S.box[code] = tri_box(S, S.order[code - (T - 1)]);
+  } else {
+    Box a = refit_node(S, S.child[2 * code]);
+    Box b = refit_node(S, S.child[2 * code + 1]);
+    S.box[code] = box_union(a, b);
+  }
+  return S.box[code];
+}
+
+void build(orc_scene& S) {
+  const int64_t T = S.nt;
+  S.morton.assign(T, 0);
+  S.order.resize(T);
+  S.child.assign(T > 1 ? 2 * (T - 1) : 0, -1);
+  S.parent.assign(T > 0 ? 2 * T - 1 : 0, -1);
+  S.box.resize(T > 0 ? 2 * T - 1 : 0);
+  if (T == 0) { S.built = true; return; }
+  std::vector<float> cen(3 * T);
+  float lo[3] = {kInfF, kInfF, kInfF}, hi[3] = {-kInfF, -kInfF, -kInfF};
+  for (int64_t t = 0; t < T; ++t) {
+    Box b = tri_box(S, t);
+    for (int a = 0; a < 3; ++a) {
+      float c = 0.5f * (b.lo[a] + b.hi[a]);
+      cen[3 * t + a] = c;
+      lo[a] = std::min(lo[a], c);
+      hi[a] = std::max(hi[a], c);
+    }
+  }
+  float s[3];
+  for (int a = 0; a < 3; ++a) {
+    s[a] = (hi[a] > lo[a]) ? 2097152.0f / (hi[a] - lo[a]) : 0.0f;
+    S.cb[a] = lo[a];
+    S.cb[3 + a] = hi[a];
+  }
+  for (int64_t t = 0; t < T; ++t)
+    S.morton[t] = interleave(quantise(cen[3 * t], lo[0], s[0]), quantise(cen[3 * t + 1], lo[1], s[1]),
+                             quantise(cen[3 * t + 2], lo[2], s[2]));
+  std::iota(S.order.begin(), S.order.end(), 0u);
+  std::stable_sort(S.order.begin(), S.order.end(),
+                   [&](uint32_t a, uint32_t b) { return S.morton[a] < S.morton[b]; });
+  std::vector<uint64_t> k(T);
+  for (int64_t i = 0; i < T; ++i) k[i] = S.morton[S.order[i]];
+  if (T > 1) build_range(S, k, 0, 0, T - 1);
+  S.built = true;
+}
+
+void refit_all(orc_scene& S) {
+  const int64_t T = S.nt;
+  if (T == 0) return;
+  Box root = refit_node(S, 0);  // T == 1: code 0 is leaf 0
+  S.scene_box = root;
+}
+
+// ---------------------------------------------------------------------------
+// Ray/triangle test (Moller-Trumbore) with the fixed FP32 operation order.
+// ---------------------------------------------------------------------------
+bool mt_hit(V3 o, V3 d, V3 v0, V3 v1, V3 v2, float& t, float& u, float& v) {
+  V3 e1 = sub3(v1, v0), e2 = sub3(v2, v0);
+  V3 p = cross3(d, e2);
+  float det = dot3(e1, p);
+  if (det == 0.0f) return false;
+  float inv = 1.0f / det;
+  V3 s = sub3(o, v0);
+  u = dot3(s, p) * inv;
+  V3 q = cross3(s, e1);
+  v = dot3(d, q) * inv;
+  t = dot3(e2, q) * inv;
+  return u >= 0.0f && v >= 0.0f && (u + v) <= 1.0f;
+}
+
+struct Hit {
+  int32_t prim = -1;
+  float t = kInfF, u = 0, v = 0;
+  int32_t prim2 = -1;
+  float t2 = kInfF;
+};
+
+// Lexicographic (t, original index) order: equal t -> smaller index wins.
+// Only finite t reach here, so "no hit yet" (t = inf) always loses.
+inline bool better(float t, int32_t i, float tb, int32_t ib) {
+  return t < tb || (t == tb && i < ib);
+}
+
+void consider(Hit& h, int32_t tri, float t, float u, float v) {
+  if (better(t, tri, h.t, h.prim)) {
+    h.t2 = h.t; h.prim2 = h.prim;
+    h.t = t; h.u = u; h.v = v; h.prim = tri;
+  } else if (tri != h.prim && better(t, tri, h.t2, h.prim2)) {
+    h.t2 = t; h.prim2 = tri;
+  }
+}
+
+// Conservative box test in double: box inflated by an absolute margin and
+// the ray interval by a relative one, so that it never rejects a box whose
+// triangles the FP32 triangle test would accept (the traversal must equal
+// brute force; a few extra visits do not matter here).
+bool box_hit(const Box& b, V3 o, V3 d, double tmin, double tmax, double& tnear) {
+  const double O[3] = {o.x, o.y, o.z}, Dd[3] = {d.x, d.y, d.z};
+  double t0 = tmin, t1 = tmax * (1.0 + 1e-3) + 1e-6;
+  for (int a = 0; a < 3; ++a) {
+    double m = 1e-4 * (1.0 + std::fabs((double)b.lo[a]) + std::fabs((double)b.hi[a]));
+    double lo = (double)b.lo[a] - m, hi = (double)b.hi[a] + m;
+    if (Dd[a] == 0.0) {
+      if (O[a] < lo || O[a] > hi) return false;
+      continue;
+    }
+    double ta = (lo - O[a]) / Dd[a], tb = (hi - O[a]) / Dd[a];
+    if (ta > tb) std::swap(ta, tb);
+    t0 = std::max(t0, ta);
+    t1 = std::min(t1, tb);
+  }
+  tnear = t0;
+  return t0 <= t1;
+}
+
+// Karras code 0 is the root: internal node 0, or leaf 0 when T == 1.
+int32_t root_code(const orc_scene&) { return 0; }
+inline bool is_leaf(const orc_scene& S, int32_t code) { return code >= S.nt - 1; }
+
+void trace_bvh(const orc_scene& S, V3 o, V3 d, float tmin, Hit& h, bool want2) {
+  std::vector<int32_t> stack;
+  stack.push_back(root_code(S));
+  while (!stack.empty()) {
+    int32_t code = stack.back();
+    stack.pop_back();
+    double bound = want2 ? (double)h.t2 : (double)h.t;
+    double tn;
+    if (!box_hit(S.box[code], o, d, tmin, bound, tn)) continue;
+    if (is_leaf(S, code)) {
+      int32_t tri = (int32_t)S.order[code - (S.nt - 1)];
+      V3 a, b, c;
+      tri_verts(S, tri, a, b, c);
+      float t, u, v;
+      if (mt_hit(o, d, a, b, c, t, u, v) && t > tmin && t < kInfF) consider(h, tri, t, u, v);
+    } else {
+      stack.push_back(S.child[2 * code + 1]);
+      stack.push_back(S.child[2 * code]);
+    }
+  }
+}
+
+void trace_brute(const orc_scene& S, V3 o, V3 d, float tmin, Hit& h) {
+  for (int64_t tri = 0; tri < S.nt; ++tri) {
+    V3 a, b, c;
+    tri_verts(S, tri, a, b, c);
+    float t, u, v;
+    if (mt_hit(o, d, a, b, c, t, u, v) && t > tmin && t < kInfF) consider(h, (int32_t)tri, t, u, v);
+  }
+}
+
+Hit trace(const orc_scene& S, V3 o, V3 d, float tmin, bool bvh, bool want2) {
+  Hit h;
+  if (S.nt == 0) return h;
+  if (bvh) trace_bvh(S, o, d, tmin, h, want2); else trace_brute(S, o, d, tmin, h);
+  return h;
+}
+
+// Any hit with 0 < t < tmax, skipping triangle `skip`.
+bool occluded(const orc_scene& S, V3 o, V3 d, float tmax, int32_t skip, bool bvh) {
+  if (S.nt == 0) return false;
+  auto test = [&](int64_t tri) {
+    if ((int32_t)tri == skip) return false;
+    V3 a, b, c;
+    tri_verts(S, tri, a, b, c);
+    float t, u, v;
+    return mt_hit(o, d, a, b, c, t, u, v) && t > 0.0f && t < tmax;
+  };
+  if (!bvh) {
+    for (int64_t tri = 0; tri < S.nt; ++tri) if (test(tri)) return true;
+    return false;
+  }
+  std::vector<int32_t> stack;
+  stack.push_back(root_code(S));
+  while (!stack.empty()) {
+    int32_t code = stack.back();
+    stack.pop_back();
+    double tn;
+    if (!box_hit(S.box[code], o, d, 0.0, (double)tmax, tn)) continue;
+    if (is_leaf(S, code)) {
+      if (test(S.order[code - (S.nt - 1)])) return true;
+    } else {
+      stack.push_back(S.child[2 * code + 1]);
+      stack.push_back(S.child[2 * code]);
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Camera (§IV-A-1 view transform restated as a pinhole ray generator):
+// f = normalize(target - pos), r = normalize(cross(f, up)), u = cross(r, f);
+// sy_scale = float(tan(vfov/2)) (double tan, rounded), sx_scale = sy_scale *
+// (W / H); sample k of pixel (x, y) has offset (ox, oy) on the 4-sample
+// rotated grid (or the pixel centre at 1 spp):
+//   fx = x + (0.5 + ox);  ndx = (2 fx) / W - 1;  sx = ndx * sx_scale
+//   fy = y + (0.5 + oy);  ndy = 1 - (2 fy) / H;  sy = ndy * sy_scale
+//   d = normalize(fma(sx, r, fma(sy, u, f)))   (componentwise)
+// ---------------------------------------------------------------------------
+struct Cam { V3 o, f, r, u; float sxs, sys; int W, H, spp; };
+
+const float kGrid4[4][2] = {{-0.125f, -0.375f}, {0.375f, -0.125f}, {-0.375f, 0.125f}, {0.125f, 0.375f}};
+
+Cam make_cam(const orc_camera* c) {
+  Cam k;
+  V3 pos = mk(c->pos[0], c->pos[1], c->pos[2]);
+  V3 tgt = mk(c->target[0], c->target[1], c->target[2]);
+  V3 up = mk(c->up[0], c->up[1], c->up[2]);
+  k.o = pos;
+  k.f = normalize3(sub3(tgt, pos));
+  k.r = normalize3(cross3(k.f, up));
+  k.u = cross3(k.r, k.f);
+  k.sys = (float)std::tan((double)c->vfov_deg * kPiD / 360.0);
+  k.sxs = k.sys * ((float)c->width / (float)c->height);
+  k.W = c->width; k.H = c->height; k.spp = c->spp;
+  return k;
+}
+
+V3 cam_dir(const Cam& k, int x, int y, int s) {
+  float ox = 0.0f, oy = 0.0f;
+  if (k.spp == 4) { ox = kGrid4[s][0]; oy = kGrid4[s][1]; }
+  float fx = (float)x + (0.5f + ox);
+  float fy = (float)y + (0.5f + oy);
+  float ndx = (2.0f * fx) / (float)k.W - 1.0f;
+  float ndy = 1.0f - (2.0f * fy) / (float)k.H;
+  float sx = ndx * k.sxs, sy = ndy * k.sys;
+  V3 dir = mk(std::fmaf(sx, k.r.x, std::fmaf(sy, k.u.x, k.f.x)),
+              std::fmaf(sx, k.r.y, std::fmaf(sy, k.u.y, k.f.y)),
+              std::fmaf(sx, k.r.z, std::fmaf(sy, k.u.z, k.f.z)));
+  return normalize3(dir);
+}
+
+// ---------------------------------------------------------------------------
+// §IV-B-1: f = f_d + f_s,  f_s = D F G / (4 (n.l)(n.v)) with
+//   D = a2 / (pi ((n.h)^2 (a2 - 1) + 1)^2),  a = r^2, a2 = a^2 (GGX, Walter 2007)
+//   F = F0 + (1 - F0)(1 - v.h)^5                  (Schlick 1994)
+//   G = G1(n.l) G1(n.v), G1(x) = x / (x (1-k) + k), k = (r+1)^2/8  (Karis 2013)
+//   G / (4 nl nv) = 1 / (4 (nl(1-k)+k)(nv(1-k)+k))  (cancelled form)
+//   F0 = 0.04 (1 - m) + albedo m,  f_d = (1 - F)(1 - m) albedo / pi (Lambert)
+// FP32 operation order as written below.
+// ---------------------------------------------------------------------------
+void brdf32(V3 n, V3 v, V3 l, const orc_material& M, float f[3]) {
+  V3 hu = add3(l, v);
+  V3 h = normalize3(hu);
+  float nl = std::max(dot3(n, l), 0.0f);
+  float nv = std::max(dot3(n, v), 0.0f);
+  float nh = std::max(dot3(n, h), 0.0f);
+  float vh = std::max(dot3(v, h), 0.0f);
+  float r = M.roughness, m = M.metallic;
+  float a = r * r;
+  float a2 = a * a;
+  float dd = std::fmaf(nh * nh, a2 - 1.0f, 1.0f);
+  float D = a2 / ((kPiF * dd) * dd);
+  float rp1 = r + 1.0f;
+  float k = (rp1 * rp1) * 0.125f;
+  float omk = 1.0f - k;
+  float gl = std::fmaf(nl, omk, k);
+  float gv = std::fmaf(nv, omk, k);
+  float vis = 0.25f / (gl * gv);
+  float Dv = D * vis;
+  float w = 1.0f - vh;
+  float w2 = w * w;
+  float w5 = (w2 * w2) * w;
+  float omm = 1.0f - m;
+  for (int c = 0; c < 3; ++c) {
+    float alb = M.albedo[c];
+    float F0 = std::fmaf(m, alb - 0.04f, 0.04f);
+    float F = std::fmaf(1.0f - F0, w5, F0);
+    float spec = Dv * F;
+    float kd = (1.0f - F) * omm;
+    float diff = (kd * alb) * kInvPiF;
+    f[c] = diff + spec;
+  }
+}
+
+struct SampleOut { int32_t prim; float t, t2; uint16_t vis; float rgb[3]; };
+
+float scene_eps(const orc_scene& S) {
+  if (S.nt == 0) return 0.0f;
+  V3 ext = mk(S.scene_box.hi[0] - S.scene_box.lo[0], S.scene_box.hi[1] - S.scene_box.lo[1],
+              S.scene_box.hi[2] - S.scene_box.lo[2]);
+  return 1e-4f * std::sqrt(dot3(ext, ext));
+}
+
+// Light vector of light j from point po (§IV-B-3: the shadow ray runs from the
+// fragment's world position to the light's position; a directional light is
+// at infinity).  E = I / d^2 for a point light, I for a directional one.
+void light_vec(const orc_light& L, V3 po, V3& l, float& E, float& tmax) {
+  if (L.type == 0) {
+    V3 lv = sub3(mk(L.v[0], L.v[1], L.v[2]), po);
+    float d2 = dot3(lv, lv);
+    float dist = std::sqrt(d2);
+    l = mk(lv.x / dist, lv.y / dist, lv.z / dist);
+    E = L.intensity / d2;
+    tmax = dist;
+  } else {
+    l = normalize3(mk(L.v[0], L.v[1], L.v[2]));
+    E = L.intensity;
+    tmax = kInfF;
+  }
+}
+
+// Hit-point frame: p = fma(t, d, o); n = normalize(cross(e1, e2)) turned to
+// face the ray; shadow origin po = fma(eps, n, p).
+void hit_frame(const orc_scene& S, int32_t prim, V3 o, V3 d, float t, float eps, V3& n, V3& po) {
+  V3 a, b, c;
+  tri_verts(S, prim, a, b, c);
+  V3 e1 = sub3(b, a), e2 = sub3(c, a);
+  n = normalize3(cross3(e1, e2));
+  if (dot3(n, d) > 0.0f) n = neg3(n);
+  V3 p = mk(std::fmaf(t, d.x, o.x), std::fmaf(t, d.y, o.y), std::fmaf(t, d.z, o.z));
+  po = mk(std::fmaf(eps, n.x, p.x), std::fmaf(eps, n.y, p.y), std::fmaf(eps, n.z, p.z));
+}
+
+SampleOut shade_sample(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, int y,
+                       int s, bool bvh, bool want2) {
+  SampleOut out;
+  out.vis = 0;
+  out.rgb[0] = out.rgb[1] = out.rgb[2] = 0.0f;
+  V3 o = K.o, d = cam_dir(K, x, y, s);
+  Hit h = trace(S, o, d, 0.0f, bvh, want2);
+  out.prim = h.prim;
+  out.t = h.t;
+  out.t2 = h.t2;
+  if (h.prim < 0) return out;
+  float eps = scene_eps(S);
+  V3 n, po;
+  hit_frame(S, h.prim, o, d, h.t, eps, n, po);
+  V3 v = neg3(d);
+  const orc_material& M = S.mats[S.tri_mat[h.prim]];
+  for (int j = 0; j < nl; ++j) {
+    V3 l;
+    float E, tmax;
+    light_vec(L[j], po, l, E, tmax);
+    float ndl = dot3(n, l);
+    if (!(ndl > 0.0f)) continue;
+    out.vis |= (uint16_t)(1u << (8 + j));
+    if (occluded(S, po, l, tmax, h.prim, bvh)) continue;
+    out.vis |= (uint16_t)(1u << j);
+    float f[3];
+    brdf32(n, v, l, M, f);
+    float En = E * ndl;
+    for (int c = 0; c < 3; ++c) out.rgb[c] = out.rgb[c] + f[c] * En;
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 twin of the shading (fixed visibility), with its analytic gradient.
+// ---------------------------------------------------------------------------
+struct Geo64 { D3 n, v; int nlights; D3 l[8]; double g[8], ndl[8]; bool lit[8]; };
+
+bool geo64(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, int y, int s,
+           int32_t prim, float t, uint16_t vis, Geo64& G) {
+  if (prim < 0) return false;
+  V3 d32 = cam_dir(K, x, y, s);
+  D3 o = tod(K.o), d = tod(d32);
+  V3 a, b, c;
+  tri_verts(S, prim, a, b, c);
+  D3 n = dnorm(dcross(dsub(tod(b), tod(a)), dsub(tod(c), tod(a))));
+  if (ddot(n, d) > 0) n = dk(-n.x, -n.y, -n.z);
+  double eps = (double)scene_eps(S);
+  D3 p = dk(o.x + (double)t * d.x, o.y + (double)t * d.y, o.z + (double)t * d.z);
+  D3 po = dk(p.x + eps * n.x, p.y + eps * n.y, p.z + eps * n.z);
+  G.n = n;
+  G.v = dk(-d.x, -d.y, -d.z);
+  G.nlights = nl;
+  for (int j = 0; j < nl; ++j) {
+    G.lit[j] = (vis >> j) & 1u;
+    if (L[j].type == 0) {
+      D3 lv = dsub(dk(L[j].v[0], L[j].v[1], L[j].v[2]), po);
+      double d2 = ddot(lv, lv);
+      G.l[j] = dnorm(lv);
+      G.g[j] = 1.0 / d2;
+    } else {
+      G.l[j] = dnorm(dk(L[j].v[0], L[j].v[1], L[j].v[2]));
+      G.g[j] = 1.0;
+    }
+    G.ndl[j] = ddot(n, G.l[j]);
+    if (!(G.ndl[j] > 0)) G.lit[j] = false;
+  }
+  return true;
+}
+
+// f_c and its derivatives d/d albedo_c, d/d rough, d/d metal (kmode 0).
+struct Brdf64 { double f[3], dalb[3], dr[3], dm[3]; };
+
+Brdf64 brdf64(D3 n, D3 v, D3 l, const double* alb, double r, double m) {
+  D3 h = dnorm(dk(l.x + v.x, l.y + v.y, l.z + v.z));
+  double nl = std::max(ddot(n, l), 0.0), nv = std::max(ddot(n, v), 0.0);
+  double nh = std::max(ddot(n, h), 0.0), vh = std::max(ddot(v, h), 0.0);
+  double a = r * r, a2 = a * a;
+  double dd = nh * nh * (a2 - 1.0) + 1.0;
+  double D = a2 / (kPiD * dd * dd);
+  double dD_da2 = (dd - 2.0 * a2 * nh * nh) / (kPiD * dd * dd * dd);
+  double dD_dr = dD_da2 * 4.0 * r * r * r;
+  double k = (r + 1.0) * (r + 1.0) / 8.0, dk_dr = (r + 1.0) / 4.0;
+  double gl = nl * (1.0 - k) + k, gv = nv * (1.0 - k) + k;
+  double vis = 1.0 / (4.0 * gl * gv);
+  double dvis_dk = -vis * ((1.0 - nl) / gl + (1.0 - nv) / gv);
+  double w = 1.0 - vh, w5 = w * w * w * w * w;
+  Brdf64 B;
+  for (int c = 0; c < 3; ++c) {
+    double F0 = 0.04 * (1.0 - m) + alb[c] * m;
+    double F = F0 + (1.0 - F0) * w5;
+    double spec = D * vis * F;
+    double diff = (1.0 - F) * (1.0 - m) * alb[c] / kPiD;
+    B.f[c] = diff + spec;
+    double dF_dF0 = 1.0 - w5;
+    double dfdF = D * vis - (1.0 - m) * alb[c] / kPiD;
+    B.dalb[c] = (1.0 - F) * (1.0 - m) / kPiD + dfdF * dF_dF0 * m;
+    B.dm[c] = dfdF * dF_dF0 * (alb[c] - 0.04) - (1.0 - F) * alb[c] / kPiD;
+    B.dr[c] = F * (dD_dr * vis + D * dvis_dk * dk_dr);
+  }
+  return B;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C API
+// ===========================================================================
+extern "C" {
+
+orc_scene* orc_scene_new(const float* verts4, int64_t nv, const uint32_t* idx, int64_t nt,
+                         const uint32_t* tri_mat, const uint16_t* vert_body,
+                         const orc_material* mats, int32_t nmat, int32_t nbody) {
+  if (nv < 0 || nt < 0 || nmat < 1 || nbody < 1) return nullptr;
+  for (int64_t i = 0; i < 3 * nt; ++i) if (idx[i] >= (uint64_t)nv) return nullptr;
+  for (int64_t i = 0; i < nt; ++i) if (tri_mat[i] >= (uint32_t)nmat) return nullptr;
+  for (int64_t i = 0; i < nv; ++i) if (vert_body[i] >= (uint32_t)nbody) return nullptr;
+  orc_scene* S = new orc_scene;
+  S->nv = nv; S->nt = nt; S->nmat = nmat; S->nbody = nbody;
+  S->rest.assign(verts4, verts4 + 4 * nv);
+  S->idx.assign(idx, idx + 3 * nt);
+  S->tri_mat.assign(tri_mat, tri_mat + nt);
+  S->vbody.assign(vert_body, vert_body + nv);
+  S->mats.assign(mats, mats + nmat);
+  return S;
+}
+
+void orc_scene_free(orc_scene* s) { delete s; }
+
+int32_t orc_set_materials(orc_scene* s, const orc_material* mats, int32_t nmat) {
+  if (nmat != s->nmat) return -1;
+  s->mats.assign(mats, mats + nmat);
+  return 0;
+}
+
+int32_t orc_update(orc_scene* s, const float* xforms, int32_t rebuild) {
+  transform(*s, xforms);
+  if (rebuild || !s->built) build(*s);
+  refit_all(*s);
+  return 0;
+}
+
+int32_t orc_get(const orc_scene* s, int32_t what, void* dst) {
+  const int64_t T = s->nt;
+  switch (what) {
+    case 0: std::memcpy(dst, s->world.data(), sizeof(V3) * s->nv); return 0;
+    case 1: std::memcpy(dst, s->morton.data(), 8 * T); return 0;
+    case 2: std::memcpy(dst, s->order.data(), 4 * T); return 0;
+    case 3: std::memcpy(dst, s->child.data(), 4 * s->child.size()); return 0;
+    case 4: std::memcpy(dst, s->parent.data(), 4 * s->parent.size()); return 0;
+    case 5: std::memcpy(dst, s->box.data(), sizeof(Box) * s->box.size()); return 0;
+    case 6: std::memcpy(dst, s->cb, sizeof(float) * 6); return 0;
+    case 7: std::memcpy(dst, &s->scene_box, sizeof(Box)); return 0;
+  }
+  return -1;
+}
+
+void orc_trace(const orc_scene* s, const float* o, const float* d, int64_t n, float tmin,
+               int32_t use_bvh, int32_t* prim, float* t, float* u, float* v, float* t2) {
+  for (int64_t i = 0; i < n; ++i) {
+    Hit h = trace(*s, mk(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
+                  tmin, use_bvh != 0, t2 != nullptr);
+    prim[i] = h.prim;
+    t[i] = h.t;
+    if (u) u[i] = h.u;
+    if (v) v[i] = h.v;
+    if (t2) t2[i] = h.t2;
+  }
+}
+
+void orc_occluded(const orc_scene* s, const float* o, const float* d, const float* tmax,
+                  const int32_t* skip, int64_t n, int32_t use_bvh, uint8_t* out) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = occluded(*s, mk(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
+                      tmax[i], skip ? skip[i] : -1, use_bvh != 0) ? 1 : 0;
+}
+
+void orc_camera_ray(const orc_camera* c, int32_t x, int32_t y, int32_t k, float* o3, float* d3) {
+  Cam K = make_cam(c);
+  V3 d = cam_dir(K, x, y, k);
+  o3[0] = K.o.x; o3[1] = K.o.y; o3[2] = K.o.z;
+  d3[0] = d.x; d3[1] = d.y; d3[2] = d.z;
+}
+
+void orc_render_samples(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                        const int64_t* ids, int64_t n, int32_t use_bvh,
+                        int32_t* prim, float* t, float* t2, uint16_t* vis, float* rgb) {
+  Cam K = make_cam(c);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t id = ids[i];
+    int sidx = (int)(id % K.spp);
+    int64_t pix = id / K.spp;
+    int x = (int)(pix % K.W), y = (int)(pix / K.W);
+    SampleOut so = shade_sample(*s, K, L, nl, x, y, sidx, use_bvh != 0, t2 != nullptr);
+    if (prim) prim[i] = so.prim;
+    if (t) t[i] = so.t;
+    if (t2) t2[i] = so.t2;
+    if (vis) vis[i] = so.vis;
+    if (rgb) { rgb[3 * i] = so.rgb[0]; rgb[3 * i + 1] = so.rgb[1]; rgb[3 * i + 2] = so.rgb[2]; }
+  }
+}
+
+// Box-filter resolve (§IV-B-2, multisample resolve): pixel = (sum over the
+// samples in order k = 0..spp-1) / spp; alpha = hits / spp.
+void orc_render_rows(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                     int32_t row0, int32_t row1, int32_t use_bvh, float* rgba) {
+  Cam K = make_cam(c);
+  for (int y = row0; y < row1; ++y)
+    for (int x = 0; x < K.W; ++x) {
+      float acc[3] = {0.0f, 0.0f, 0.0f};
+      int hits = 0;
+      for (int k = 0; k < K.spp; ++k) {
+        SampleOut so = shade_sample(*s, K, L, nl, x, y, k, use_bvh != 0, false);
+        for (int ch = 0; ch < 3; ++ch) acc[ch] = acc[ch] + so.rgb[ch];
+        hits += so.prim >= 0;
+      }
+      float* px = rgba + 4 * ((int64_t)y * K.W + x);
+      for (int ch = 0; ch < 3; ++ch) px[ch] = acc[ch] / (float)K.spp;
+      px[3] = (float)hits / (float)K.spp;
+    }
+}
+
+void orc_brdf_f32(const float* n, const float* v, const float* l, const orc_material* m, float* f_rgb) {
+  brdf32(mk(n[0], n[1], n[2]), mk(v[0], v[1], v[2]), mk(l[0], l[1], l[2]), *m, f_rgb);
+}
+
+double orc_ggx_d(double nh, double alpha) {
+  double a2 = alpha * alpha;
+  double dd = nh * nh * (a2 - 1.0) + 1.0;
+  return a2 / (kPiD * dd * dd);
+}
+
+double orc_schlick_f(double vh, double f0) { return f0 + (1.0 - f0) * std::pow(1.0 - vh, 5.0); }
+
+double orc_smith_g(double nl, double nv, double rough, int32_t kmode) {
+  double k = kmode == 0 ? (rough + 1.0) * (rough + 1.0) / 8.0 : rough * rough / 2.0;
+  return (nl / (nl * (1.0 - k) + k)) * (nv / (nv * (1.0 - k) + k));
+}
+
+void orc_brdf_f64(const double* n, const double* v, const double* l, const double* albedo,
+                  double rough, double metal, int32_t kmode, double* fd_rgb, double* fs_rgb) {
+  D3 N = dk(n[0], n[1], n[2]), V = dk(v[0], v[1], v[2]), L = dk(l[0], l[1], l[2]);
+  D3 h = dnorm(dk(L.x + V.x, L.y + V.y, L.z + V.z));
+  double nl = std::max(ddot(N, L), 0.0), nv = std::max(ddot(N, V), 0.0);
+  double nh = std::max(ddot(N, h), 0.0), vh = std::max(ddot(V, h), 0.0);
+  double D = orc_ggx_d(nh, rough * rough);
+  double k = kmode == 0 ? (rough + 1.0) * (rough + 1.0) / 8.0 : rough * rough / 2.0;
+  double visq = 1.0 / (4.0 * (nl * (1.0 - k) + k) * (nv * (1.0 - k) + k));
+  for (int c = 0; c < 3; ++c) {
+    double F0 = 0.04 * (1.0 - metal) + albedo[c] * metal;
+    double F = orc_schlick_f(vh, F0);
+    fs_rgb[c] = D * F * visq;
+    fd_rgb[c] = (1.0 - F) * (1.0 - metal) * albedo[c] / kPiD;
+  }
+}
+
+float orc_shadow_eps(const orc_scene* s) { return scene_eps(*s); }
+
+void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                   const int32_t* prim, const float* t, const uint16_t* vis,
+                   const double* params, const double* inten, double* img) {
+  Cam K = make_cam(c);
+  for (int y = 0; y < K.H; ++y)
+    for (int x = 0; x < K.W; ++x) {
+      double acc[3] = {0, 0, 0};
+      for (int k = 0; k < K.spp; ++k) {
+        int64_t id = ((int64_t)y * K.W + x) * K.spp + k;
+        Geo64 G;
+        if (!geo64(*s, K, L, nl, x, y, k, prim[id], t[id], vis[id], G)) continue;
+        const double* P = params + 5 * s->tri_mat[prim[id]];
+        for (int j = 0; j < nl; ++j) {
+          if (!G.lit[j]) continue;
+          Brdf64 B = brdf64(G.n, G.v, G.l[j], P, P[3], P[4]);
+          for (int ch = 0; ch < 3; ++ch) acc[ch] += B.f[ch] * inten[j] * G.g[j] * G.ndl[j];
+        }
+      }
+      for (int ch = 0; ch < 3; ++ch) img[3 * ((int64_t)y * K.W + x) + ch] = acc[ch] / K.spp;
+    }
+}
+
+void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                  const int32_t* prim, const float* t, const uint16_t* vis,
+                  const double* params, const double* inten, const double* dimg,
+                  double* dparams, double* dinten) {
+  Cam K = make_cam(c);
+  std::fill(dparams, dparams + 5 * s->nmat, 0.0);
+  std::fill(dinten, dinten + nl, 0.0);
+  for (int y = 0; y < K.H; ++y)
+    for (int x = 0; x < K.W; ++x) {
+      const double* gp = dimg + 3 * ((int64_t)y * K.W + x);
+      for (int k = 0; k < K.spp; ++k) {
+        int64_t id = ((int64_t)y * K.W + x) * K.spp + k;
+        Geo64 G;
+        if (!geo64(*s, K, L, nl, x, y, k, prim[id], t[id], vis[id], G)) continue;
+        uint32_t mat = s->tri_mat[prim[id]];
+        const double* P = params + 5 * mat;
+        double* dP = dparams + 5 * mat;
+        for (int j = 0; j < nl; ++j) {
+          if (!G.lit[j]) continue;
+          Brdf64 B = brdf64(G.n, G.v, G.l[j], P, P[3], P[4]);
+          double w = G.g[j] * G.ndl[j] / K.spp;
+          for (int ch = 0; ch < 3; ++ch) {
+            double up = gp[ch] * w;  // dL/d f_c, per unit intensity
+            dP[ch] += up * inten[j] * B.dalb[ch];
+            dP[3] += up * inten[j] * B.dr[ch];
+            dP[4] += up * inten[j] * B.dm[ch];
+            dinten[j] += up * B.f[ch];
+          }
+        }
+      }
+    }
+}
+
+}  // extern "C"
