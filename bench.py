@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the renderer's per-frame hot path on B300.
+
+One step = one frame of the headline workload: fire_bvh_refit (64 rigid
+bodies moved by that frame's poses) + fire_render (7,299,072 triangles,
+1920x1080, 4 spp, 2 lights).  Frame 0 (the LBVH build) is in the warm-up.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (the path has no exchange
+step): each rank renders its own frames; the time is the max over ranks and
+the value is the whole job's ms per frame.  Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "ms/frame & Grays/s at 7.3M tris 1080p 4spp; batched & backward vs plain"
+UNIT = "ms/frame"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(w, nframes):
+    cam = w.camera
+    return {"workload": (f"frame7m: {w.scene.nt:,} triangles (1,400 icospheres of 5,120 + 256x256-cell "
+                         f"terrain), 64 rigid bodies moved every frame, refit + render per frame, "
+                         f"{cam.width}x{cam.height}, {cam.spp} spp rotated grid, {len(w.lights)} point lights"),
+            "triangles": w.scene.nt, "width": cam.width, "height": cam.height, "spp": cam.spp,
+            "lights": len(w.lights), "bodies": w.scene.nbody - 1, "frames": nframes,
+            "l2": "inputs larger than L2: every refit rewrites 467 MB of nodes + 350 MB of triangles",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region (read-only queries)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- roofline
+def algorithmic_bytes(nt: int, nv: int, samples: int, pixels: int):
+    """Minimum bytes each kernel must move per launch (one frame):
+    refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, sorted
+               index records (16 B) + material (4 B) + leaf slot (4 B) per
+               triangle; write the 48-B triangle record; per internal node
+               write 2 child boxes (48 B), read them back (48 B), counter
+               atomic (8 B) and parent slot (4 B)
+    primary -- read the whole tree once (64 B per internal node + 48 B per
+               triangle) + write a 16-B G-buffer record per sample
+    shade   -- read the whole tree once + the 16-B G-buffer record per
+               sample + write a 16-B pixel."""
+    tree = 64 * max(nt - 1, 0) + 48 * nt
+    return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48) + max(nt - 1, 0) * (48 + 48 + 8 + 4),
+            "primary": tree + 16 * samples,
+            "shade": tree + 16 * samples + 16 * pixels}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU baseline
+def cpu_oracle_frame(w, xf_build, xf_frame, nsamples: int, seed: int = 7):
+    """The oracle as it stands on the host: one refit of the frame (timed)
+    plus a bounded random sample of the frame's samples (timed), scaled to a
+    whole frame.  Single-threaded."""
+    import oracle
+    S = oracle.OracleScene(w.scene)
+    S.update(xf_build, rebuild=True)
+    t0 = time.perf_counter()
+    S.update(xf_frame, rebuild=False)
+    t_refit = time.perf_counter() - t0
+    cam = w.camera
+    n = cam.width * cam.height * cam.spp
+    ids = np.random.default_rng(seed).choice(n, nsamples, replace=False)
+    t0 = time.perf_counter()
+    S.render_samples(cam, w.lights, ids, want_t2=False)
+    t_samp = time.perf_counter() - t0
+    ms = 1e3 * (t_refit + t_samp * n / nsamples)
+    return ms, {"refit_s": t_refit, "sample_s": t_samp, "samples": nsamples}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    w = sg.workload_frame7m()
+    xf0 = w.motion.xforms()
+    frames = [w.motion.step() for _ in range(args.warmup + args.steps)]
+    import oracle
+    S = oracle.OracleScene(w.scene)
+    S.update(xf0, rebuild=True)
+    cam = w.camera
+    n = cam.width * cam.height * cam.spp
+    per = max(200, args.ref_samples)
+    rng = np.random.default_rng(11)
+    times = []
+    for i, xf in enumerate(frames):
+        t0 = time.perf_counter()
+        S.update(xf, rebuild=False)
+        t1 = time.perf_counter()
+        ids = rng.choice(n, per, replace=False)
+        S.render_samples(cam, w.lights, ids, want_t2=False)
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            times.append(1e3 * ((t1 - t0) + (t2 - t1) * n / per))
+    ms = float(np.mean(times))
+    sample = (f"each step: oracle refit of the frame + {per} random samples of its "
+              f"{n:,}, scaled to the frame; single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, args.steps),
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- side runs
+def batch_ratio(fb, torch, reps=5):
+    """Batched (one graph-replayed persistent launch) vs the same 64 frames
+    rendered by 64 fire_render calls; same images."""
+    scenes, cams, cam_scene, lights = sg.batch16()
+    G = []
+    for sc in scenes:
+        g = fb.Scene.from_numpy(sc)
+        g.build(sc.identity_xforms())
+        G.append(g)
+    outs = [torch.zeros((c.height, c.width, 4), device="cuda") for c in cams]
+    fb.render_batch(G, cams, cam_scene, lights, outs)  # autotune + capture
+    cfg = fb.batch_last_config()
+    for _ in range(2):
+        fb.render_batch(G, cams, cam_scene, lights, outs)
+    seq = [torch.zeros_like(o) for o in outs]
+    for c, si, o in zip(cams, cam_scene, seq):
+        G[si].render(c, lights[si], out=o)
+    same = all(torch.equal(a, b) for a, b in zip(outs, seq))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fb.render_batch(G, cams, cam_scene, lights, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        for c, si, o in zip(cams, cam_scene, seq):
+            G[si].render(c, lights[si], out=o)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / reps
+    tris = [s.nt for s in scenes]
+    return {"batched_ms": t_batch, "sequential_ms": t_seq, "ratio": t_seq / t_batch, "identical": bool(same),
+            "cameras": len(cams), "scenes": len(scenes), "tris_min": min(tris), "tris_max": max(tris),
+            "tuned": cfg}
+
+
+def backward_ratio(fb, torch, reps=20):
+    """Backward of the shading stage vs its forward (512x512, 1 spp, 32
+    materials, 2 lights, 499,712 triangles)."""
+    w = sg.workload_grad500k()
+    cam, lights = w.camera, w.lights
+    G = fb.Scene.from_numpy(w.scene)
+    G.build(w.scene.identity_xforms())
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, lights, gbuf=gb)
+    P = np.zeros((len(w.scene.mats), 5), np.float32)
+    for i, m in enumerate(w.scene.mats):
+        P[i, :3], P[i, 3], P[i, 4] = m["albedo"], m["roughness"], m["metallic"]
+    params = torch.from_numpy(P).cuda()
+    inten = torch.tensor([l.intensity for l in lights], dtype=torch.float32, device="cuda")
+    dimg = torch.randn((cam.height, cam.width, 4), device="cuda")
+    dP, dI = torch.zeros_like(params), torch.zeros_like(inten)
+    G.profile(True)
+    for _ in range(3):
+        G.shade(gb, cam, lights, params, inten)
+        G.shade_backward(gb, cam, lights, params, inten, dimg, dP, dI)
+    G.profile_read()
+    out = torch.zeros((cam.height, cam.width, 4), device="cuda")
+    for _ in range(reps):
+        G.shade(gb, cam, lights, params, inten, out=out)
+        G.shade_backward(gb, cam, lights, params, inten, dimg, dP, dI)
+    p = G.profile_read()
+    fwd = p["shade_gbuf"][0] / max(1, p["shade_gbuf"][1])
+    bwd = p["backward"][0] / max(1, p["backward"][1])
+    return {"forward_shade_ms": fwd, "backward_ms": bwd, "ratio": bwd / fwd, "pixels": cam.width * cam.height}
+
+
+# --------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-samples", type=int, default=6000, help="oracle samples for the CPU baseline")
+    ap.add_argument("--ref-samples", type=int, default=1500, help="oracle samples per reference step")
+    ap.add_argument("--no-side", action="store_true", help="skip the batched and backward side runs")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, local_rank, world = env_rank()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_2410_05095_b300 as fb
+    from paper_2410_05095_b300 import _build
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    w = sg.workload_frame7m()
+    K, W = args.steps, args.warmup
+    xf_build = w.motion.xforms()
+    frames = np.stack([w.motion.step() for _ in range(W + 2 * K)])
+    cam, lights = w.camera, w.lights
+    G = fb.Scene.from_numpy(w.scene)
+    xf_dev = torch.from_numpy(frames).cuda()
+    xf_pinned = torch.from_numpy(frames).pin_memory()
+    G.build(xf_build)
+    out = torch.zeros((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    G.profile(True)
+    for i in range(W):
+        G.refit(xf_dev[i])
+        G.render(cam, lights, out=out)
+    torch.cuda.synchronize()
+    build_stats = G.profile_read()
+    assert G.sync_status() == 0
+
+    # --- timed region: K frames, inputs resident in HBM -----------------------------
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(K):
+            G.refit(xf_dev[W + i])
+            G.render(cam, lights, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    stages = G.profile_read()
+    launches = sum(n for (_, n) in stages.values())
+    assert G.sync_status() == 0
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    ms_frame_rank = t_ms / K
+    value = t_ms / (K * world)
+
+    # --- end to end through the public API with host buffers ----------------------
+    host_img = torch.empty((cam.height, cam.width, 4), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(K):
+        G.refit(xf_pinned[W + K + i].numpy())
+        G.render(cam, lights, out=out)
+        host_img.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    G.profile_read()
+    e2e = {"value": t_e2e / (K * world), "unit": UNIT, "h2d_bytes_per_step": int(frames[0].nbytes),
+           "d2h_bytes_per_step": int(host_img.numel() * 4)}
+
+    # --- rays traced per frame (shadow rays counted from the G-buffer) ------------
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, lights, out=out, gbuf=gb)
+    vis = gb[:, 2].to(torch.int64)
+    shadow_rays = int(sum(((vis >> (8 + j)) & 1).sum().item() for j in range(len(lights))))
+    primary_rays = cam.width * cam.height * cam.spp
+    hits = int((gb[:, 0] >= 0).sum().item())
+    del gb
+
+    prim_ms = stages["primary"][0] / max(1, stages["primary"][1])
+    shade_ms = stages["shade"][0] / max(1, stages["shade"][1])
+    refit_ms = stages["refit"][0] / max(1, stages["refit"][1])
+    grays = (primary_rays + shadow_rays) / ((prim_ms + shade_ms) * 1e-3) / 1e9
+    grays_frame = (primary_rays + shadow_rays) / (ms_frame_rank * 1e-3) / 1e9
+    alg = algorithmic_bytes(w.scene.nt, w.scene.nv, primary_rays, cam.width * cam.height)
+    per = {"refit": refit_ms, "primary": prim_ms, "shade": shade_ms}
+    dom = max(per, key=per.get)
+    peak, peak_kind = load_peaks()
+    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get(dom)
+    roofline = {"bound": "hbm", "kernel": {"refit": "k_refit", "primary": "k_primary", "shade": "k_shade"}[dom],
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": alg[dom]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_frame_rank, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded icospheres + value-noise terrain, random rigid motion)",
+            "config": workload_config(w, K), "gpu_launches": int(launches),
+            "grays_per_s": grays, "grays_per_s_frame": grays_frame,
+            "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
+            "stages_ms": {"refit": refit_ms, "primary": prim_ms, "shade_shadow_resolve": shade_ms,
+                          "build_once": build_stats["build"][0]},
+            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e}
+
+    if rank == 0 and not args.no_side:
+        line["batched"] = batch_ratio(fb, torch)
+        line["backward"] = backward_ratio(fb, torch)
+    if rank == 0:
+        ms_cpu, info = cpu_oracle_frame(w, xf_build, frames[0], args.cpu_samples)
+        line["cpu_baseline"] = {"value": ms_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": (f"oracle refit of one frame + {info['samples']} random samples of "
+                                           f"its {primary_rays:,}, scaled to the frame; single thread")}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

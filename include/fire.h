@@ -1,0 +1,257 @@
+/*
+ * fire.h -- C ABI of the B300 renderer hot path (libfire.so).
+ *
+ * The per-frame data-parallel path of the FIRE-3DV renderer (arXiv 2410.05095)
+ * restated as CUDA for one B300 (sm_103a): an LBVH over a triangle scene
+ * rebuilt or refit from per-body rigid transforms (§IV-B-3 acceleration
+ * structure; §IV-C per-body world matrices every frame), supersampled primary
+ * visibility (§IV-B-2 multisampling), any-hit shadow rays per light (§IV-B-3),
+ * Cook-Torrance GGX shading (§IV-B-1) and a box-filter resolve into a linear
+ * HDR image.  No graphics API is involved.
+ *
+ * Conventions for every call:
+ *  - Return FIRE_OK (0) or a negative FIRE_ERR_* code; fire_last_error()
+ *    gives a thread-local message for the last failure.
+ *  - "device" pointers are CUDA device memory of the current device (for
+ *    example a torch tensor's data_ptr()); "host" pointers are ordinary host
+ *    memory.  The caller owns every buffer it passes in; the library never
+ *    frees or retains caller pointers beyond the call, except that device
+ *    work enqueued by the call reads/writes them asynchronously on `stream`.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work and return without synchronising, except where stated.
+ *  - Errors found on the device (traversal stack overflow, iteration cap) set
+ *    a sticky per-scene error word that fire_sync_status() reports; bad input
+ *    is rejected on the host (or by a counting kernel) and never traps on the
+ *    device.
+ *  - A scene handle must not be used from two host threads at once.
+ */
+#ifndef FIRE_H
+#define FIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIRE_OK 0
+#define FIRE_ERR_INVALID_ARG (-1)
+#define FIRE_ERR_OOM (-2)
+#define FIRE_ERR_CUDA (-3)
+#define FIRE_ERR_STACK_OVERFLOW (-4)
+#define FIRE_ERR_TIMEOUT (-5)
+#define FIRE_ERR_NOT_BUILT (-6)
+
+typedef struct fire_scene_s* fire_scene; /* opaque, library-owned */
+
+/* glTF metallic-roughness material (§IV-B-1): linear albedo in [0,1],
+ * roughness in (0,1] (alpha = roughness^2 in the GGX term), metallic in [0,1]. */
+typedef struct {
+  float albedo[3];
+  float roughness;
+  float metallic;
+} fire_material;
+
+/* Pinhole camera: forward = normalize(target - pos), right = normalize(forward x up),
+ * true up = right x forward; vfov_deg is the vertical field of view; image row 0
+ * is the top.  spp is 1 (pixel centre) or 4 (rotated grid, offsets
+ * (-1/8,-3/8), (3/8,-1/8), (-3/8,1/8), (1/8,3/8) pixels). */
+typedef struct {
+  float pos[3];
+  float target[3];
+  float up[3];
+  float vfov_deg;
+  int32_t width;
+  int32_t height;
+  int32_t spp;
+} fire_camera;
+
+/* Light (§IV-B-3 Fig. 5: several omnidirectional lights).  type 0: point light
+ * at v with irradiance I/d^2; type 1: directional light, v = direction towards
+ * the light (normalised by the library), irradiance I. */
+typedef struct {
+  int32_t type;
+  float v[3];
+  float intensity;
+} fire_light;
+
+/* Render options; a zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+  int32_t row_begin;     /* render rows [row_begin, row_end) only; 0,0 = all rows.
+                            Other rows of out_rgba are left untouched. */
+  int32_t row_end;
+  int32_t block_threads; /* threads per block of the trace kernels (0 = default) */
+  int32_t blocks_per_sm; /* persistent grid = SMs x blocks_per_sm (0 = default) */
+  int32_t stack_depth;   /* traversal stack entries (0 = sufficient for the tree) */
+  int32_t flags;         /* FIRE_RENDER_* bits, 0 by default */
+} fire_render_opts;
+
+/* Test hook: accept a stack_depth below the tree height.  A ray whose stack
+ * would overflow drops the deepest pending subtree (its result may then be
+ * wrong) and sets FIRE_ERR_STACK_OVERFLOW in the scene's error word; no
+ * access ever leaves the stack. */
+#define FIRE_RENDER_ALLOW_SHALLOW_STACK 1
+
+/* One G-buffer record per sample, sample id = (y*W + x)*spp + k:
+ * prim = original triangle index of the nearest hit (-1 = miss), t = hit
+ * distance along the unit ray, vis = bit j set if light j was cast
+ * (n.l > 0) and unoccluded, bit 8+j set if light j was cast. */
+typedef struct {
+  int32_t prim;
+  float t;
+  uint32_t vis;
+  uint32_t pad;
+} fire_gbuffer_rec;
+
+/* ---------------------------------------------------------------- scenes */
+
+/* Create a scene from a rest-pose triangle mesh (§IV-A-1 resource containers;
+ * vertex pulling: flat vertex and index buffers).
+ *   verts_xyzw [nv*4] device float  rest positions (w ignored)
+ *   tri_idx    [nt*3] device uint32 vertex indices, each < nv
+ *   tri_mat    [nt]   device uint32 material index, each < nmat
+ *   vert_body  [nv]   device uint16 rigid body of each vertex, each < nbody
+ *   mats       [nmat] host fire_material
+ * The library copies all geometry (the caller may free its buffers after the
+ * call returns; the copy is ordered on `stream`).  Out-of-range indices or
+ * non-finite positions -> FIRE_ERR_INVALID_ARG (checked by a counting kernel;
+ * this call synchronises `stream` once).  nt = 0 is a valid empty scene. */
+int fire_scene_create(const float* verts_xyzw, int64_t nv, const uint32_t* tri_idx, int64_t nt,
+                      const uint32_t* tri_mat, const uint16_t* vert_body,
+                      const fire_material* mats, int32_t nmat, int32_t nbody, void* stream,
+                      fire_scene* out);
+
+/* Release all device memory of the scene (synchronises the device). */
+int fire_scene_destroy(fire_scene s);
+
+/* Replace the materials (host array of the same length nmat). */
+int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nmat);
+
+/* Scene sizes: out[0] = nv, out[1] = nt, out[2] = nmat, out[3] = nbody,
+ * out[4] = tree depth (after a build), out[5] = device bytes held. */
+int fire_scene_info(fire_scene s, int64_t* out6);
+
+/* ------------------------------------------------------------------ LBVH */
+
+/* Build the LBVH (§IV-B-3 acceleration-structure build, restated as Karras
+ * 2012): transform every vertex by its body's row-major 3x4 world matrix
+ * (x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row), 63-bit Morton codes of
+ * triangle-box centroids over the centroid bounds, stable radix sort,
+ * radix-tree topology, bottom-up boxes.
+ *   body_xforms [nbody*12] float, device if xforms_on_device else host
+ * Non-finite matrices -> FIRE_ERR_INVALID_ARG (host check only for host
+ * matrices; device matrices are the caller's responsibility). */
+int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream);
+
+/* Refit with the topology of the last build (§IV-B-3 step 4: new transforms
+ * each frame): re-transform the vertices and recompute every box bottom-up.
+ * Before any build -> FIRE_ERR_NOT_BUILT. */
+int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream);
+
+/* ---------------------------------------------------------------- render */
+
+/* Render one frame: primary rays (spp per pixel), any-hit shadow rays per
+ * light from the hit point lifted by eps = 1e-4 x scene-box diagonal along the
+ * normal (§IV-B-3), Cook-Torrance GGX + Lambert shading with E = I/d^2 (point)
+ * or I (directional) (§IV-B-1), box-filter mean of the samples (§IV-B-2).
+ *   cam         host fire_camera
+ *   lights      host fire_light[nlights], 0 <= nlights <= 8
+ *   opts        host, or NULL for defaults
+ *   out_rgba    device float [H*W*4]: rgb = linear radiance, a = hit fraction
+ *   gbuf        device fire_gbuffer_rec [H*W*spp] or NULL (written if given)
+ * Before any build -> FIRE_ERR_NOT_BUILT. */
+int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, int32_t nlights,
+                const fire_render_opts* opts, float* out_rgba, fire_gbuffer_rec* gbuf,
+                void* stream);
+
+/* Render many cameras over many scenes in one persistent launch, replayed as
+ * a CUDA graph when the same batch is rendered again (scenes, cameras, lights,
+ * outputs and options unchanged).
+ *   scenes     host fire_scene[nscenes] (each built)
+ *   cams       host fire_camera[ncams]; cam_scene host int32[ncams] (< nscenes)
+ *   lights     host fire_light[light_off[nscenes]]; light_off host int32[nscenes+1]
+ *              (scene i uses lights[light_off[i] .. light_off[i+1]), at most 8)
+ *   outs       host array of ncams device float pointers, [H_i*W_i*4] each
+ *   opts       host or NULL; block_threads/blocks_per_sm/stack_depth of 0 are
+ *              chosen by the library's autotuner (timed once per batch shape)
+ * Results equal ncams separate fire_render calls bit for bit. */
+int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_camera* cams,
+                      const int32_t* cam_scene, int32_t ncams, const fire_light* lights,
+                      const int32_t* light_off, float* const* outs, const fire_render_opts* opts,
+                      void* stream);
+
+/* ------------------------------------------------------- differentiable */
+
+/* Shade a G-buffer (from fire_render) with device-side parameters, holding
+ * visibility fixed: params [nmat*5] device float (albedo rgb, roughness,
+ * metallic per material), inten [nlights] device float (replaces the lights'
+ * intensities).  Writes out_rgba like fire_render. */
+int fire_shade(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam,
+               const fire_light* lights, int32_t nlights, const float* params, const float* inten,
+               float* out_rgba, void* stream);
+
+/* Backward of fire_shade: given dL/d(out_rgba) [H*W*4] device float (alpha
+ * ignored), ACCUMULATE dL/dparams into dparams [nmat*5] and dL/dinten into
+ * dinten [nlights] (device float; zero them first for a plain gradient).
+ * Recomputes every shading input from the G-buffer (no stored intermediates). */
+int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam,
+                        const fire_light* lights, int32_t nlights, const float* params,
+                        const float* inten, const float* dL_drgba, float* dparams, float* dinten,
+                        void* stream);
+
+/* ------------------------------------------------------------- utilities */
+
+/* Copy internal state to host memory for checks (synchronises `stream` = the
+ * library's last used stream of this scene).  what:
+ *  0 morton codes by original triangle  uint64[nt]
+ *  1 sorted order (position -> triangle) uint32[nt]
+ *  2 children in Karras numbering       int32[(nt-1)*2] (internal i < nt-1,
+ *                                       leaf at sorted position p = nt-1+p)
+ *  3 parent by Karras code              int32[2nt-1] (root -1)
+ *  4 node boxes by Karras code          float[(2nt-1)*6] (lo xyz, hi xyz)
+ *  5 triangle records in sorted order  float[nt*12]: v0 xyz, original index
+ *                                       (bits), e1 = v1-v0 xyz, material (bits),
+ *                                       e2 = v2-v0 xyz, 0
+ *  6 centroid bounds                    float[6]
+ * bytes must equal the exact size; otherwise FIRE_ERR_INVALID_ARG. */
+int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes);
+
+/* Synchronise `stream`, then return and clear the scene's sticky device error
+ * (FIRE_OK, FIRE_ERR_STACK_OVERFLOW or FIRE_ERR_TIMEOUT). */
+int fire_sync_status(fire_scene s, void* stream);
+
+/* Test hook: cap traversal loop iterations per ray (0 = no cap beyond the
+ * library's safety bound).  A ray that hits the cap stops early and sets
+ * FIRE_ERR_TIMEOUT in the scene's error word. */
+int fire_debug_set_iteration_cap(fire_scene s, int64_t cap);
+
+/* Test hook: make the next device allocation of this thread fail (n-th
+ * allocation from now, 1 = next), to exercise FIRE_ERR_OOM paths. 0 = off. */
+int fire_debug_fail_alloc(int32_t nth);
+
+/* Stage timing with CUDA events recorded on the launching stream around each
+ * kernel of the scene's calls (off by default; negligible cost when on).
+ * Stages: 0 refit, 1 primary rays, 2 shadow rays + shading + resolve,
+ * 3 build (whole), 4 G-buffer shading, 5 shading backward.
+ * fire_profile_read synchronises the pending events and returns, per stage,
+ * the summed milliseconds and the number of launches since the last read
+ * (then resets). */
+int fire_profile_enable(fire_scene s, int32_t enable);
+int fire_profile_read(fire_scene s, double* ms8, int64_t* launches8);
+
+/* Configuration of the last fire_render_batch launch: out4 = threads per
+ * block, blocks per SM (0 = occupancy limit), stack depth, 1 if the autotuner
+ * ran during that call. */
+int fire_batch_last_config(int32_t* out4);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* fire_last_error(void);
+
+/* Library version string. */
+const char* fire_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIRE_H */

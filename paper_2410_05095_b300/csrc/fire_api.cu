@@ -1,0 +1,621 @@
+// C ABI of libfire: handles, validation, device memory, error codes.
+// Every entry point checks its arguments on the host, enqueues work on the
+// caller's stream and returns without synchronising unless fire.h says so.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fire_internal.cuh"
+
+namespace fire {
+
+namespace {
+thread_local std::string g_err;
+thread_local int g_fail_alloc = 0;
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FIRE_OK;
+  cudaGetLastError();  // clear a non-sticky error
+  if (e == cudaErrorMemoryAllocation) return set_error(FIRE_ERR_OOM, std::string(what) + ": out of device memory");
+  return set_error(FIRE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, size_t* counter) {
+  *p = nullptr;
+  if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess && counter) *counter += bytes;
+  return e;
+}
+
+int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  });
+  return n;
+}
+
+namespace {
+// Host FP32 vector helpers in the same operation order as the device ones
+// (the host compiler runs with -ffp-contract=off).
+struct H3 { float x, y, z; };
+H3 hsub(H3 a, H3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+float hdot(H3 a, H3 b) { return std::fmaf(a.x, b.x, std::fmaf(a.y, b.y, a.z * b.z)); }
+H3 hcross(H3 a, H3 b) {
+  return {std::fmaf(a.y, b.z, -(a.z * b.y)), std::fmaf(a.z, b.x, -(a.x * b.z)), std::fmaf(a.x, b.y, -(a.y * b.x))};
+}
+H3 hnorm(H3 v) {
+  float len = std::sqrt(hdot(v, v));
+  return {v.x / len, v.y / len, v.z / len};
+}
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+}  // namespace
+
+// forward = normalize(target - pos), right = normalize(forward x up),
+// up' = right x forward, sys = float(tan(vfov/2)) (double tan), sxs = sys * (W/H).
+CamParams make_cam(const fire_camera& c) {
+  CamParams p;
+  H3 pos{c.pos[0], c.pos[1], c.pos[2]}, tgt{c.target[0], c.target[1], c.target[2]}, up{c.up[0], c.up[1], c.up[2]};
+  H3 f = hnorm(hsub(tgt, pos));
+  H3 r = hnorm(hcross(f, up));
+  H3 u = hcross(r, f);
+  p.ox = pos.x; p.oy = pos.y; p.oz = pos.z;
+  p.fx = f.x; p.fy = f.y; p.fz = f.z;
+  p.rx = r.x; p.ry = r.y; p.rz = r.z;
+  p.ux = u.x; p.uy = u.y; p.uz = u.z;
+  p.sys = (float)std::tan((double)c.vfov_deg * 3.14159265358979323846 / 360.0);
+  p.sxs = p.sys * ((float)c.width / (float)c.height);
+  p.W = c.width;
+  p.H = c.height;
+  p.spp = c.spp;
+  return p;
+}
+
+int make_lights(const fire_light* lights, int n, LightParams* out) {
+  if (n < 0 || n > kMaxLights) return set_error(FIRE_ERR_INVALID_ARG, "nlights must be in [0, 8]");
+  if (n > 0 && !lights) return set_error(FIRE_ERR_INVALID_ARG, "lights is NULL");
+  memset(out, 0, sizeof(*out));
+  out->n = n;
+  for (int j = 0; j < n; ++j) {
+    const fire_light& L = lights[j];
+    if ((L.type != 0 && L.type != 1) || !finite3(L.v) || !std::isfinite(L.intensity) || L.intensity < 0)
+      return set_error(FIRE_ERR_INVALID_ARG, "invalid light " + std::to_string(j));
+    H3 v{L.v[0], L.v[1], L.v[2]};
+    if (L.type == 1) {
+      if (hdot(v, v) == 0.0f) return set_error(FIRE_ERR_INVALID_ARG, "directional light with zero direction");
+      v = hnorm(v);
+    }
+    out->type[j] = L.type;
+    out->x[j] = v.x;
+    out->y[j] = v.y;
+    out->z[j] = v.z;
+    out->I[j] = L.intensity;
+  }
+  return FIRE_OK;
+}
+
+namespace {
+
+int check_cam(const fire_camera* c) {
+  if (!c) return set_error(FIRE_ERR_INVALID_ARG, "camera is NULL");
+  if (c->width <= 0 || c->height <= 0 || (int64_t)c->width * c->height > (int64_t)1 << 28)
+    return set_error(FIRE_ERR_INVALID_ARG, "camera size out of range");
+  if (c->spp != 1 && c->spp != 4) return set_error(FIRE_ERR_INVALID_ARG, "spp must be 1 or 4");
+  if (!finite3(c->pos) || !finite3(c->target) || !finite3(c->up) || !(c->vfov_deg > 0 && c->vfov_deg < 180))
+    return set_error(FIRE_ERR_INVALID_ARG, "camera parameters not finite / fov out of (0,180)");
+  H3 f = hsub(H3{c->target[0], c->target[1], c->target[2]}, H3{c->pos[0], c->pos[1], c->pos[2]});
+  H3 r = hcross(f, H3{c->up[0], c->up[1], c->up[2]});
+  if (hdot(f, f) == 0.0f || hdot(r, r) == 0.0f) return set_error(FIRE_ERR_INVALID_ARG, "degenerate camera basis");
+  return FIRE_OK;
+}
+
+int check_mats(const fire_material* m, int n) {
+  if (n < 1 || !m) return set_error(FIRE_ERR_INVALID_ARG, "need at least one material");
+  for (int i = 0; i < n; ++i) {
+    bool ok = finite3(m[i].albedo) && std::isfinite(m[i].roughness) && std::isfinite(m[i].metallic) &&
+              m[i].roughness > 0.0f && m[i].roughness <= 1.0f && m[i].metallic >= 0.0f && m[i].metallic <= 1.0f;
+    for (int c = 0; c < 3; ++c) ok = ok && m[i].albedo[c] >= 0.0f && m[i].albedo[c] <= 1.0f;
+    if (!ok) return set_error(FIRE_ERR_INVALID_ARG, "material " + std::to_string(i) + " out of range");
+  }
+  return FIRE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Stage profiler: an event pair per kernel launch, resolved lazily (the
+// oldest pairs are synchronised only when many are pending or on read).
+// ---------------------------------------------------------------------------
+struct Profiler {
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::deque<Pending> pending;
+  cudaEvent_t open[kStages] = {};
+  double ms[kStages] = {};
+  int64_t n[kStages] = {};
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  void drain(size_t keep) {
+    while (pending.size() > keep) {
+      Pending p = pending.front();
+      pending.pop_front();
+      float t = 0.0f;
+      cudaEventSynchronize(p.b);
+      cudaEventElapsedTime(&t, p.a, p.b);
+      ms[p.stage] += t;
+      n[p.stage] += 1;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+  }
+  ~Profiler() {
+    drain(0);
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : open)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+void prof_begin(fire_scene_s* s, int stage, cudaStream_t st) {
+  if (!s->prof) return;
+  Profiler* P = static_cast<Profiler*>(s->prof);
+  if (P->open[stage]) P->pool.push_back(P->open[stage]);
+  P->open[stage] = P->get();
+  cudaEventRecord(P->open[stage], st);
+}
+
+void prof_end(fire_scene_s* s, int stage, cudaStream_t st) {
+  if (!s->prof) return;
+  Profiler* P = static_cast<Profiler*>(s->prof);
+  if (!P->open[stage]) return;
+  cudaEvent_t e = P->get();
+  cudaEventRecord(e, st);
+  P->pending.push_back({stage, P->open[stage], e});
+  P->open[stage] = nullptr;
+  if (P->pending.size() > 1024) P->drain(512);
+}
+
+namespace {
+
+void free_scene(fire_scene_s* s) {
+  delete static_cast<Profiler*>(s->prof);
+  s->prof = nullptr;
+  void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
+                  s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
+                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int upload_mats(fire_scene_s* s, const fire_material* m, cudaStream_t st) {
+  std::vector<float> h(5 * (size_t)s->nmat);
+  for (int i = 0; i < s->nmat; ++i) {
+    h[5 * i] = m[i].albedo[0];
+    h[5 * i + 1] = m[i].albedo[1];
+    h[5 * i + 2] = m[i].albedo[2];
+    h[5 * i + 3] = m[i].roughness;
+    h[5 * i + 4] = m[i].metallic;
+  }
+  s->h_mats.assign(m, m + s->nmat);
+  int e = cuda_check(cudaMemcpyAsync(s->mats, h.data(), h.size() * 4, cudaMemcpyHostToDevice, st), "materials");
+  if (e) return e;
+  return cuda_check(cudaStreamSynchronize(st), "materials");  // h is a stack buffer
+}
+
+int load_xforms(fire_scene_s* s, const float* xf, int on_device, cudaStream_t st) {
+  if (!xf) return set_error(FIRE_ERR_INVALID_ARG, "body_xforms is NULL");
+  size_t n = 12 * (size_t)s->nbody;
+  if (on_device) {
+    return cuda_check(cudaMemcpyAsync(s->xf, xf, n * 4, cudaMemcpyDeviceToDevice, st), "xforms");
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(xf[i])) return set_error(FIRE_ERR_INVALID_ARG, "non-finite body transform");
+  return cuda_check(cudaMemcpyAsync(s->xf, xf, n * 4, cudaMemcpyHostToDevice, st), "xforms");
+}
+
+int alloc_lbvh(fire_scene_s* s) {
+  const int64_t T = s->nt;
+  if (T == 0 || s->keys) return FIRE_OK;
+  const int64_t ntiles = (T + kSortTile - 1) / kSortTile;
+  struct A { void** p; size_t b; } list[] = {
+      {(void**)&s->keys, 8 * (size_t)T},          {(void**)&s->keys_orig, 8 * (size_t)T},
+      {(void**)&s->order, 4 * (size_t)T},         {(void**)&s->sidx, 16 * (size_t)T},
+      {(void**)&s->smat, 4 * (size_t)T},          {(void**)&s->nodes, 64 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->leaf_slot, 4 * (size_t)T},     {(void**)&s->node_slot, 4 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris, 48 * (size_t)T},
+      {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
+      {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
+  };
+  for (auto& a : list)
+    if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "LBVH buffers");
+  return FIRE_OK;
+}
+
+cudaStream_t as_stream(void* st) { return reinterpret_cast<cudaStream_t>(st); }
+
+}  // namespace
+}  // namespace fire
+
+using namespace fire;
+
+extern "C" {
+
+const char* fire_last_error(void) { return g_err.c_str(); }
+const char* fire_version(void) { return "fire-b300 1.0 (sm_103a)"; }
+
+int fire_debug_fail_alloc(int32_t nth) {
+  g_fail_alloc = nth > 0 ? nth : 0;
+  return FIRE_OK;
+}
+
+int fire_scene_create(const float* verts_xyzw, int64_t nv, const uint32_t* tri_idx, int64_t nt,
+                      const uint32_t* tri_mat, const uint16_t* vert_body, const fire_material* mats, int32_t nmat,
+                      int32_t nbody, void* stream, fire_scene* out) {
+  g_err.clear();
+  if (!out) return set_error(FIRE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nv < 0 || nt < 0 || nbody < 1 || nbody > 65536 || nt >= ((int64_t)1 << 31) - 1 || nv >= ((int64_t)1 << 32))
+    return set_error(FIRE_ERR_INVALID_ARG, "sizes out of range");
+  if ((nv > 0 && (!verts_xyzw || !vert_body)) || (nt > 0 && (!tri_idx || !tri_mat)))
+    return set_error(FIRE_ERR_INVALID_ARG, "NULL geometry pointer");
+  if (int e = check_mats(mats, nmat)) return e;
+  cudaStream_t st = as_stream(stream);
+  fire_scene_s* s = new fire_scene_s();
+  cudaGetDevice(&s->device);
+  s->nv = nv;
+  s->nt = nt;
+  s->nmat = nmat;
+  s->nbody = nbody;
+  s->last_stream = st;
+  struct A { void** p; size_t b; } list[] = {
+      {(void**)&s->rest, 16 * (size_t)nv}, {(void**)&s->idx, 12 * (size_t)nt}, {(void**)&s->tmat, 4 * (size_t)nt},
+      {(void**)&s->vbody, 2 * (size_t)nv}, {(void**)&s->mats, 20 * (size_t)nmat},
+      {(void**)&s->xf, 48 * (size_t)nbody}, {(void**)&s->ctrl, 64}};
+  for (auto& a : list) {
+    if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) {
+      int rc = cuda_check(e, "scene buffers");
+      free_scene(s);
+      delete s;
+      return rc;
+    }
+  }
+  int rc = FIRE_OK;
+  if (nv > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->rest, verts_xyzw, 16 * nv, cudaMemcpyDefault, st), "copy");
+  if (nv > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->vbody, vert_body, 2 * nv, cudaMemcpyDefault, st), "copy");
+  if (nt > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->idx, tri_idx, 12 * nt, cudaMemcpyDefault, st), "copy");
+  if (nt > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->tmat, tri_mat, 4 * nt, cudaMemcpyDefault, st), "copy");
+  rc = rc ? rc : cuda_check(cudaMemsetAsync(s->ctrl, 0, 64, st), "memset");
+  rc = rc ? rc : upload_mats(s, mats, st);
+  uint32_t bad = 0;
+  rc = rc ? rc : lbvh_validate(s, st, &bad);
+  if (!rc && bad) rc = set_error(FIRE_ERR_INVALID_ARG, "out-of-range index or non-finite vertex (" + std::to_string(bad) + ")");
+  if (rc) {
+    free_scene(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return FIRE_OK;
+}
+
+int fire_scene_destroy(fire_scene s) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  cudaDeviceSynchronize();
+  free_scene(s);
+  delete s;
+  return FIRE_OK;
+}
+
+int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nmat) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  if (nmat != s->nmat) return set_error(FIRE_ERR_INVALID_ARG, "material count differs from the scene's");
+  if (int e = check_mats(mats, nmat)) return e;
+  return upload_mats(s, mats, s->last_stream);
+}
+
+int fire_scene_info(fire_scene s, int64_t* out6) {
+  g_err.clear();
+  if (!s || !out6) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  out6[0] = s->nv;
+  out6[1] = s->nt;
+  out6[2] = s->nmat;
+  out6[3] = s->nbody;
+  out6[4] = s->height;
+  out6[5] = (int64_t)s->bytes;
+  return FIRE_OK;
+}
+
+int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  cudaStream_t st = as_stream(stream);
+  s->last_stream = st;
+  if (int e = load_xforms(s, body_xforms, xforms_on_device, st)) return e;
+  if (int e = alloc_lbvh(s)) return e;
+  return lbvh_build(s, st);
+}
+
+int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "refit before build");
+  cudaStream_t st = as_stream(stream);
+  s->last_stream = st;
+  if (int e = load_xforms(s, body_xforms, xforms_on_device, st)) return e;
+  return lbvh_refit(s, st);
+}
+
+static int fill_args(fire_scene s, const fire_camera* cam, const fire_light* lights, int32_t nlights,
+                     RenderArgs* a) {
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "render before build");
+  if (int e = check_cam(cam)) return e;
+  memset(a, 0, sizeof(*a));
+  if (int e = make_lights(lights, nlights, &a->lights)) return e;
+  a->nodes = s->nodes;
+  a->tris = s->tris;
+  a->nt = s->nt;
+  a->cam = make_cam(*cam);
+  a->mats.p = s->mats;
+  a->mats.n = s->nmat;
+  a->row_begin = 0;
+  a->row_end = cam->height;
+  a->iter_cap = s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64;
+  a->ctrl = s->ctrl;
+  return FIRE_OK;
+}
+
+static int ensure_scratch(fire_scene s, size_t n) {
+  if (s->gscratch_n >= n) return FIRE_OK;
+  if (s->gscratch) {
+    cudaFree(s->gscratch);
+    s->bytes -= s->gscratch_n * sizeof(fire_gbuffer_rec);
+  }
+  s->gscratch = nullptr;
+  s->gscratch_n = 0;
+  if (cudaError_t e = dev_alloc((void**)&s->gscratch, n * sizeof(fire_gbuffer_rec), &s->bytes))
+    return cuda_check(e, "G-buffer scratch");
+  s->gscratch_n = n;
+  return FIRE_OK;
+}
+
+int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, int32_t nlights,
+                const fire_render_opts* opts, float* out_rgba, fire_gbuffer_rec* gbuf, void* stream) {
+  g_err.clear();
+  RenderArgs a;
+  if (int e = fill_args(s, cam, lights, nlights, &a)) return e;
+  if (!out_rgba) return set_error(FIRE_ERR_INVALID_ARG, "out_rgba is NULL");
+  fire_render_opts o{};
+  if (opts) o = *opts;
+  if (o.row_begin != 0 || o.row_end != 0) {
+    if (o.row_begin < 0 || o.row_end > cam->height || o.row_begin >= o.row_end)
+      return set_error(FIRE_ERR_INVALID_ARG, "row range out of the image");
+    a.row_begin = o.row_begin;
+    a.row_end = o.row_end;
+  }
+  if (o.stack_depth < 0 || o.stack_depth > 128 || o.blocks_per_sm < 0 ||
+      (o.flags & ~FIRE_RENDER_ALLOW_SHALLOW_STACK) != 0)
+    return set_error(FIRE_ERR_INVALID_ARG, "invalid render options");
+  if (o.stack_depth > 0 && o.stack_depth < s->height && !(o.flags & FIRE_RENDER_ALLOW_SHALLOW_STACK))
+    return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below the tree height " + std::to_string(s->height));
+  cudaStream_t st = as_stream(stream);
+  s->last_stream = st;
+  size_t nsamp = (size_t)cam->width * cam->height * cam->spp;
+  if (gbuf) {
+    a.g = gbuf;
+    a.write_vis = 1;
+  } else {
+    if (int e = ensure_scratch(s, nsamp)) return e;
+    a.g = s->gscratch;
+    a.write_vis = 0;
+  }
+  a.out = out_rgba;
+  return render_frame(s, a, o, st);
+}
+
+int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_camera* cams, const int32_t* cam_scene,
+                      int32_t ncams, const fire_light* lights, const int32_t* light_off, float* const* outs,
+                      const fire_render_opts* opts, void* stream) {
+  g_err.clear();
+  if (nscenes < 1 || ncams < 0 || !scenes || (ncams > 0 && (!cams || !cam_scene || !outs)) || !light_off)
+    return set_error(FIRE_ERR_INVALID_ARG, "invalid batch arguments");
+  for (int i = 0; i < nscenes; ++i) {
+    if (!scenes[i]) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene in batch");
+    if (!scenes[i]->built) return set_error(FIRE_ERR_NOT_BUILT, "batch scene not built");
+    if (light_off[i + 1] < light_off[i] || light_off[i + 1] - light_off[i] > kMaxLights)
+      return set_error(FIRE_ERR_INVALID_ARG, "light_off not ascending or > 8 lights");
+  }
+  if (light_off[0] != 0 || (light_off[nscenes] > 0 && !lights))
+    return set_error(FIRE_ERR_INVALID_ARG, "light_off[0] must be 0");
+  for (int i = 0; i < ncams; ++i) {
+    if (cam_scene[i] < 0 || cam_scene[i] >= nscenes) return set_error(FIRE_ERR_INVALID_ARG, "cam_scene out of range");
+    if (int e = check_cam(&cams[i])) return e;
+    if (!outs[i]) return set_error(FIRE_ERR_INVALID_ARG, "NULL output");
+  }
+  if (opts && (opts->row_begin || opts->row_end || opts->flags || opts->stack_depth < 0 || opts->stack_depth > 128 ||
+               opts->blocks_per_sm < 0 || opts->block_threads < 0 || opts->block_threads > 256 ||
+               (opts->block_threads % 32) != 0))
+    return set_error(FIRE_ERR_INVALID_ARG, "invalid batch options");
+  return render_batch(scenes, nscenes, cams, cam_scene, ncams, lights, light_off, outs, opts, as_stream(stream));
+}
+
+int fire_shade(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam, const fire_light* lights,
+               int32_t nlights, const float* params, const float* inten, float* out_rgba, void* stream) {
+  g_err.clear();
+  RenderArgs a;
+  if (int e = fill_args(s, cam, lights, nlights, &a)) return e;
+  if (!gbuf || !params || (!inten && nlights > 0) || !out_rgba) return set_error(FIRE_ERR_INVALID_ARG, "NULL buffer");
+  a.g = const_cast<fire_gbuffer_rec*>(gbuf);
+  a.mats.p = params;
+  a.out = out_rgba;
+  cudaStream_t st = as_stream(stream);
+  s->last_stream = st;
+  return shade_from_gbuffer(s, a, inten, st);
+}
+
+int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam, const fire_light* lights,
+                        int32_t nlights, const float* params, const float* inten, const float* dL_drgba,
+                        float* dparams, float* dinten, void* stream) {
+  g_err.clear();
+  RenderArgs a;
+  if (int e = fill_args(s, cam, lights, nlights, &a)) return e;
+  if (!gbuf || !params || (nlights > 0 && (!inten || !dinten)) || !dL_drgba || !dparams)
+    return set_error(FIRE_ERR_INVALID_ARG, "NULL buffer");
+  if (s->nmat * 5 + nlights > 16384) return set_error(FIRE_ERR_INVALID_ARG, "too many materials for the backward");
+  a.g = const_cast<fire_gbuffer_rec*>(gbuf);
+  a.mats.p = params;
+  cudaStream_t st = as_stream(stream);
+  s->last_stream = st;
+  return shade_backward(s, a, inten, dL_drgba, dparams, dinten, st);
+}
+
+int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
+  g_err.clear();
+  if (!s || !host_dst) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "dump before build");
+  const int64_t T = s->nt;
+  cudaStream_t st = s->last_stream;
+  if (cudaError_t e = cudaStreamSynchronize(st)) return cuda_check(e, "sync");
+  auto need = [&](size_t n) { return bytes == n; };
+  auto get = [&](void* dst, const void* src, size_t n) {
+    return cuda_check(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost), "dump copy");
+  };
+  switch (what) {
+    case 0: if (!need(8 * T)) break; return T ? get(host_dst, s->keys_orig, 8 * T) : FIRE_OK;
+    case 1: if (!need(4 * T)) break; return T ? get(host_dst, s->order, 4 * T) : FIRE_OK;
+    case 2:
+    case 3:
+    case 4: {
+      int64_t ni = T > 1 ? T - 1 : 0;
+      size_t want = what == 2 ? 8 * ni : what == 3 ? 4 * (size_t)(T ? 2 * T - 1 : 0) : 24 * (size_t)(T ? 2 * T - 1 : 0);
+      if (!need(want)) break;
+      if (T == 0) return FIRE_OK;
+      std::vector<Node> nodes(std::max<int64_t>(ni, 1));
+      if (int e = get(nodes.data(), s->nodes, 64 * nodes.size())) return e;
+      auto code = [&](int c) { return c >= 0 ? c : (int)(T - 1) + ~c; };
+      if (what == 2) {
+        int32_t* o = (int32_t*)host_dst;
+        for (int64_t i = 0; i < ni; ++i) { o[2 * i] = code(nodes[i].d.x); o[2 * i + 1] = code(nodes[i].d.y); }
+      } else if (what == 3) {
+        int32_t* o = (int32_t*)host_dst;
+        o[0] = -1;
+        for (int64_t i = 0; i < ni; ++i) { o[code(nodes[i].d.x)] = (int32_t)i; o[code(nodes[i].d.y)] = (int32_t)i; }
+      } else {
+        float* o = (float*)host_dst;
+        auto put = [&](int c, const float* b) { memcpy(o + 6 * (int64_t)c, b, 24); };
+        if (T == 1) {
+          put(0, reinterpret_cast<const float*>(&nodes[0]));
+        } else {
+          for (int64_t i = 0; i < ni; ++i) {
+            const float* f = reinterpret_cast<const float*>(&nodes[i]);
+            put(code(nodes[i].d.x), f);
+            put(code(nodes[i].d.y), f + 6);
+          }
+          float root[6];
+          const float* f = reinterpret_cast<const float*>(&nodes[0]);
+          for (int k = 0; k < 3; ++k) {
+            root[k] = std::fmin(f[k], f[6 + k]);
+            root[3 + k] = std::fmax(f[3 + k], f[9 + k]);
+          }
+          put(0, root);
+        }
+      }
+      return FIRE_OK;
+    }
+    case 5: {
+      if (!need(48 * (size_t)T)) break;
+      return T ? get(host_dst, s->tris, 48 * T) : FIRE_OK;
+    }
+    case 6: {
+      if (!need(24)) break;
+      uint32_t u[6];
+      if (int e = get(u, s->ctrl + 9, 24)) return e;
+      float* o = (float*)host_dst;
+      for (int k = 0; k < 6; ++k) o[k] = ord2f(u[k]);
+      return FIRE_OK;
+    }
+    default:
+      return set_error(FIRE_ERR_INVALID_ARG, "unknown dump selector");
+  }
+  return set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+}
+
+int fire_sync_status(fire_scene s, void* stream) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  cudaStream_t st = as_stream(stream);
+  uint32_t w = 0;
+  if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
+  if (int e = cuda_check(cudaMemcpy(&w, s->ctrl + 8, 4, cudaMemcpyDeviceToHost), "status")) return e;
+  if (int e = cuda_check(cudaMemset(s->ctrl + 8, 0, 4), "status")) return e;
+  if (w & kErrStack) return set_error(FIRE_ERR_STACK_OVERFLOW, "traversal stack overflow");
+  if (w & kErrTimeout) return set_error(FIRE_ERR_TIMEOUT, "traversal iteration cap reached");
+  return FIRE_OK;
+}
+
+int fire_debug_set_iteration_cap(fire_scene s, int64_t cap) {
+  g_err.clear();
+  if (!s || cap < 0) return set_error(FIRE_ERR_INVALID_ARG, "invalid argument");
+  s->iter_cap = cap;
+  return FIRE_OK;
+}
+
+int fire_profile_enable(fire_scene s, int32_t enable) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  if (enable && !s->prof) s->prof = new Profiler();
+  if (!enable && s->prof) {
+    delete static_cast<Profiler*>(s->prof);
+    s->prof = nullptr;
+  }
+  return FIRE_OK;
+}
+
+int fire_profile_read(fire_scene s, double* ms8, int64_t* launches8) {
+  g_err.clear();
+  if (!s || !ms8 || !launches8) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < kStages; ++i) { ms8[i] = 0.0; launches8[i] = 0; }
+  if (!s->prof) return FIRE_OK;
+  Profiler* P = static_cast<Profiler*>(s->prof);
+  P->drain(0);
+  for (int i = 0; i < kStages; ++i) {
+    ms8[i] = P->ms[i];
+    launches8[i] = P->n[i];
+    P->ms[i] = 0.0;
+    P->n[i] = 0;
+  }
+  return FIRE_OK;
+}
+
+int fire_batch_last_config(int32_t* out4) {
+  g_err.clear();
+  if (!out4) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  return batch_last_info(out4);
+}
+
+}  // extern "C"

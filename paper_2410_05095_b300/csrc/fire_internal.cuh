@@ -1,0 +1,213 @@
+// Internal declarations of libfire (B300 / sm_103a).
+//
+// Compiled with -fmad=false: no multiply-add is fused unless written as
+// fmaf(), and '/' and sqrtf() are IEEE correctly rounded (nvcc defaults), so
+// every FP32 expression below has one fixed rounding sequence.  The integer
+// decisions of the method (Morton codes, nearest-hit argmin, shadow
+// visibility) depend on that sequence.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fire.h"
+
+namespace fire {
+
+// ---------------------------------------------------------------------------
+// Device data layout
+// ---------------------------------------------------------------------------
+// Internal node of the binary LBVH, 64 B = two 32-B sectors: the boxes of
+// BOTH children plus the child links, so one node fetch decides which
+// children a ray enters (no separate fetch of the child's own box).
+//   a = lo0.x lo0.y lo0.z hi0.x
+//   b = hi0.y hi0.z lo1.x lo1.y
+//   c = lo1.z hi1.x hi1.y hi1.z
+//   d = child0, child1, height0, height1   (child >= 0: internal node index,
+//                                           child < 0: leaf at sorted position ~child)
+struct __align__(16) Node {
+  float4 a, b, c;
+  int4 d;
+};
+static_assert(sizeof(Node) == 64, "node must be 64 bytes");
+
+// Triangle record in leaf (sorted) order, 48 B:
+//   v0.xyz, w = original triangle index (bits)
+//   e1 = v1 - v0, w = material index (bits)
+//   e2 = v2 - v0, w = 0
+// e1/e2 are the same FP32 differences the ray/triangle test and the normal use.
+
+constexpr int kMaxLights = 8;
+constexpr int kSortBits = 9;                 // 7 passes x 9 bits = 63-bit keys
+constexpr int kSortBins = 1 << kSortBits;
+constexpr int kSortPasses = 7;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Device error word bits
+constexpr uint32_t kErrStack = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+struct CamParams {
+  float ox, oy, oz;     // position
+  float fx, fy, fz;     // forward
+  float rx, ry, rz;     // right
+  float ux, uy, uz;     // true up
+  float sxs, sys;       // tan(vfov/2) * aspect, tan(vfov/2)
+  int W, H, spp;
+};
+
+struct LightParams {
+  int n;
+  int type[kMaxLights];
+  float x[kMaxLights], y[kMaxLights], z[kMaxLights];  // position or unit direction
+  float I[kMaxLights];
+};
+
+struct MatParams {  // device pointer to [nmat*5] (albedo rgb, roughness, metallic)
+  const float* p;
+  int n;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side scene object
+// ---------------------------------------------------------------------------
+}  // namespace fire
+
+struct fire_scene_s {
+  int device = 0;
+  int64_t nv = 0, nt = 0;
+  int32_t nmat = 0, nbody = 0;
+  // rest-pose inputs (library copies)
+  float4* rest = nullptr;       // [nv]
+  uint32_t* idx = nullptr;      // [nt*3] original order
+  uint32_t* tmat = nullptr;     // [nt]   original order
+  uint16_t* vbody = nullptr;    // [nv]
+  float* mats = nullptr;        // [nmat*5] device copy
+  std::vector<fire_material> h_mats;
+  float* xf = nullptr;          // [nbody*12]
+  // LBVH
+  bool built = false;
+  int height = 0;               // internal levels on the longest root-leaf path
+  uint64_t* keys = nullptr;     // sorted keys [nt]
+  uint64_t* keys_orig = nullptr;// keys by original triangle [nt] (debug dump)
+  uint32_t* order = nullptr;    // [nt] sorted position -> original triangle
+  uint4* sidx = nullptr;        // [nt] (i0, i1, i2, orig) in sorted order
+  uint32_t* smat = nullptr;     // [nt] material in sorted order
+  fire::Node* nodes = nullptr;  // [max(nt-1, 1)]
+  int32_t* leaf_slot = nullptr; // [nt]   2*parent + side
+  int32_t* node_slot = nullptr; // [nt-1] 2*parent + side (root -1)
+  uint32_t* counters = nullptr; // [nt-1] arrival counters (parity per refit)
+  float4* tris = nullptr;       // [nt*3]
+  // build scratch
+  float4* cen = nullptr;        // [nt]
+  uint64_t* keys_alt = nullptr; // [nt]
+  uint32_t* vals_alt = nullptr; // [nt]
+  uint32_t* hist = nullptr;     // [kSortBins * nblocks]
+  uint32_t* ctrl = nullptr;     // [16]: [0..7] task counters, [8] error word, [9..14] bounds
+  // render scratch
+  fire_gbuffer_rec* gscratch = nullptr;
+  size_t gscratch_n = 0;
+  // batch cache (see batch.cu)
+  void* batch = nullptr;
+  int64_t iter_cap = 0;
+  size_t bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  void* prof = nullptr;         // fire::Profiler when enabled
+};
+
+namespace fire {
+
+// ---------------------------------------------------------------------------
+// Host helpers (fire_api.cu)
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+cudaError_t dev_alloc(void** p, size_t bytes, size_t* counter);
+int sm_count();
+CamParams make_cam(const fire_camera& c);
+int make_lights(const fire_light* lights, int n, LightParams* out);
+
+// Stage profiler (fire_api.cu): event pairs around kernels, read lazily.
+enum Stage { kStageRefit = 0, kStagePrimary = 1, kStageShade = 2, kStageBuild = 3, kStageShadeGbuf = 4,
+             kStageBackward = 5, kStages = 8 };
+void prof_begin(fire_scene_s* s, int stage, cudaStream_t st);
+void prof_end(fire_scene_s* s, int stage, cudaStream_t st);
+
+// lbvh.cu
+int lbvh_build(fire_scene_s* s, cudaStream_t st);
+int lbvh_refit(fire_scene_s* s, cudaStream_t st);
+int lbvh_validate(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host);
+
+// trace.cu
+struct RenderArgs {
+  const Node* nodes;
+  const float4* tris;
+  int64_t nt;
+  CamParams cam;
+  LightParams lights;
+  MatParams mats;
+  int row_begin, row_end;
+  int64_t iter_cap;
+  uint32_t* ctrl;               // counters + error word
+  fire_gbuffer_rec* g;          // per-sample records
+  int write_vis;                // store vis bits into g
+  float* out;                   // [H*W*4]
+};
+int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o, cudaStream_t st);
+int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten, cudaStream_t st);
+int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,
+                   float* dparams, float* dinten, cudaStream_t st);
+int stack_for_height(int height, int requested);
+
+// batch.cu
+int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
+                 const int32_t* cam_scene, int ncams, const fire_light* lights,
+                 const int32_t* light_off, float* const* outs, const fire_render_opts* opts,
+                 cudaStream_t st);
+void batch_free(fire_scene_s* s);
+int batch_last_info(int32_t* out4);
+
+// ---------------------------------------------------------------------------
+// Device math with the fixed operation order
+//   dot(a,b)   = fma(ax,bx, fma(ay,by, az*bz))
+//   cross(a,b) = (fma(ay,bz, -(az*by)), fma(az,bx, -(ax*bz)), fma(ax,by, -(ay*bx)))
+//   normalize(v) = v / sqrt(dot(v,v))
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 add3(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 neg3(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x)));
+}
+__device__ __forceinline__ float3 normalize3(float3 v) {
+  float len = sqrtf(dot3(v, v));
+  return f3(v.x / len, v.y / len, v.z / len);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+
+// Ordered-integer image of a float (monotone), for exact atomic min/max.
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ord2f(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+#else
+  uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+
+}  // namespace fire

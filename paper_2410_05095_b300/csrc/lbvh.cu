@@ -1,0 +1,451 @@
+// LBVH build and refit (§IV-B-3 acceleration-structure build; §IV-C per-body
+// world matrices each frame), restated as a Karras (2012) linear BVH:
+//   transform -> centroid bounds -> 63-bit Morton codes -> stable LSD radix
+//   sort -> radix-tree topology -> bottom-up boxes.
+// The refit re-runs only the transform and the bottom-up boxes with the
+// topology of the last build.
+#include <algorithm>
+#include <cstdio>
+
+#include "fire_internal.cuh"
+
+namespace fire {
+namespace {
+
+// x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row of the 3x4 matrix.
+__device__ __forceinline__ float3 xform(const float* __restrict__ m, float4 v) {
+  return f3(fmaf(m[0], v.x, fmaf(m[1], v.y, fmaf(m[2], v.z, m[3]))),
+            fmaf(m[4], v.x, fmaf(m[5], v.y, fmaf(m[6], v.z, m[7]))),
+            fmaf(m[8], v.x, fmaf(m[9], v.y, fmaf(m[10], v.z, m[11]))));
+}
+
+__device__ __forceinline__ float3 fmin3(float3 a, float3 b) { return f3(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z)); }
+__device__ __forceinline__ float3 fmax3(float3 a, float3 b) { return f3(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z)); }
+
+// ----------------------------------------------------------------------------
+// Validation of the inputs of fire_scene_create: count out-of-range indices
+// and non-finite positions (the host turns a non-zero count into an error).
+// ----------------------------------------------------------------------------
+__global__ void k_validate(const float4* __restrict__ rest, int64_t nv, const uint32_t* __restrict__ idx,
+                           const uint32_t* __restrict__ tmat, int64_t nt, const uint16_t* __restrict__ vb,
+                           int nmat, int nbody, uint32_t* bad) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t n = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv || i < nt; i += stride) {
+    if (i < nv) {
+      float4 v = rest[i];
+      n += !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+      n += vb[i] >= (uint32_t)nbody;
+    }
+    if (i < nt) {
+      n += idx[3 * i] >= (uint64_t)nv;
+      n += idx[3 * i + 1] >= (uint64_t)nv;
+      n += idx[3 * i + 2] >= (uint64_t)nv;
+      n += tmat[i] >= (uint32_t)nmat;
+    }
+  }
+  if (n) atomicAdd(bad, n);
+}
+
+// ----------------------------------------------------------------------------
+// Build step 1: transform, triangle boxes, centroids, exact centroid bounds.
+// centroid c = 0.5 * (min + max) per axis.
+// ----------------------------------------------------------------------------
+__global__ void k_centroids(const float4* __restrict__ rest, const uint32_t* __restrict__ idx,
+                            const uint16_t* __restrict__ vb, const float* __restrict__ xf, int64_t nt,
+                            float4* __restrict__ cen, uint32_t* __restrict__ bounds) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float3 c = f3(__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000));
+  float3 cmax = f3(-c.x, -c.y, -c.z);
+  float3 cmin = c;
+  if (i < nt) {
+    uint32_t a = idx[3 * i], b = idx[3 * i + 1], d = idx[3 * i + 2];
+    float3 w0 = xform(xf + 12 * vb[a], rest[a]);
+    float3 w1 = xform(xf + 12 * vb[b], rest[b]);
+    float3 w2 = xform(xf + 12 * vb[d], rest[d]);
+    float3 mn = fmin3(w0, fmin3(w1, w2)), mx = fmax3(w0, fmax3(w1, w2));
+    c = f3(0.5f * (mn.x + mx.x), 0.5f * (mn.y + mx.y), 0.5f * (mn.z + mx.z));
+    cen[i] = make_float4(c.x, c.y, c.z, 0.0f);
+    cmin = c;
+    cmax = c;
+  }
+  uint32_t lo[3] = {f2ord(cmin.x), f2ord(cmin.y), f2ord(cmin.z)};
+  uint32_t hi[3] = {f2ord(cmax.x), f2ord(cmax.y), f2ord(cmax.z)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    for (int off = 16; off; off >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(bounds + k, lo[k]);
+      atomicMax(bounds + 3 + k, hi[k]);
+    }
+  }
+}
+
+// Spread the low 21 bits of x to every third bit (bit k -> bit 3k).
+__device__ __forceinline__ uint64_t spread3(uint32_t x) {
+  uint64_t v = x & 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// q = min(floor((c - lo) * s), 2^21 - 1) with s = 2^21 / (hi - lo) (0 if
+// hi == lo): FP32 subtract, FP32 multiply, truncation.
+__device__ __forceinline__ uint32_t quantise(float c, float lo, float s) {
+  float f = (c - lo) * s;
+  if (!(f > 0.0f)) return 0u;
+  if (f >= 2097151.0f) return 2097151u;
+  return (uint32_t)f;
+}
+
+// Build step 2: 63-bit Morton code (x -> bit 3k+2, y -> 3k+1, z -> 3k).
+__global__ void k_morton(const float4* __restrict__ cen, int64_t nt, const uint32_t* __restrict__ bounds,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         uint64_t* __restrict__ keys_orig) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  float lo[3], s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = ord2f(bounds[k]);
+    float hi = ord2f(bounds[3 + k]);
+    s[k] = (hi > lo[k]) ? 2097152.0f / (hi - lo[k]) : 0.0f;
+  }
+  float4 c = cen[i];
+  uint64_t code = (spread3(quantise(c.x, lo[0], s[0])) << 2) | (spread3(quantise(c.y, lo[1], s[1])) << 1) |
+                  spread3(quantise(c.z, lo[2], s[2]));
+  keys[i] = code;
+  keys_orig[i] = code;
+  vals[i] = (uint32_t)i;
+}
+
+// ----------------------------------------------------------------------------
+// Stable LSD radix sort of (63-bit key, u32 value): 7 passes of 9 bits.
+//   upsweep   : per-tile digit histogram -> hist[digit * ntiles + tile]
+//   scan      : per digit, exclusive scan over tiles; digit totals
+//   downsweep : per tile, stable local ranks (warp match + per-warp counts),
+//               scatter to digit_start + tile_prefix + warp_prefix + rank
+// Tile = 256 threads x 16 items; item order inside a tile is warp-major,
+// then round, then lane, which equals global order (stability).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & (kSortBins - 1); }
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                                                               uint32_t* __restrict__ hist, int ntiles) {
+  __shared__ uint32_t h[kSortBins];
+  for (int d = threadIdx.x; d < kSortBins; d += kSortThreads) h[d] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[digit_of(keys[i], shift)], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kSortBins; d += kSortThreads) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// One block per digit: exclusive scan of hist[d][0..ntiles) in place; total -> totals[d].
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, int ntiles, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  uint32_t* row = hist + (int64_t)blockIdx.x * ntiles;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < ntiles; base += 1024) {
+    int i = base + threadIdx.x;
+    uint32_t v = i < ntiles ? row[i] : 0u;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t s = wsum[lane];
+      for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
+        if (lane >= off) s += y;
+      }
+      wsum[lane] = s;  // inclusive warp sums
+    }
+    __syncthreads();
+    uint32_t excl = carry + (w ? wsum[w - 1] : 0u) + x - v;
+    if (i < ntiles) row[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                                 int64_t n, int shift, const uint32_t* __restrict__ hist,
+                                                                 int ntiles, const uint32_t* __restrict__ totals) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t wcnt[W][kSortBins];
+  __shared__ uint32_t dbase[kSortBins];
+  __shared__ uint32_t scan_tmp[kSortThreads];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kSortBins; d += kSortThreads)
+#pragma unroll
+    for (int k = 0; k < W; ++k) wcnt[k][d] = 0;
+  // digit start = exclusive scan of totals (each thread owns 2 consecutive digits)
+  {
+    uint32_t t0 = totals[2 * threadIdx.x], t1 = totals[2 * threadIdx.x + 1];
+    uint32_t s = t0 + t1, x = s;
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) scan_tmp[w] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int k = 0; k < w; ++k) wpre += scan_tmp[k];
+    uint32_t excl = wpre + x - s;
+    dbase[2 * threadIdx.x] = excl + hist[(int64_t)(2 * threadIdx.x) * ntiles + blockIdx.x];
+    dbase[2 * threadIdx.x + 1] = excl + t0 + hist[(int64_t)(2 * threadIdx.x + 1) * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * (kSortItems * 32);
+  uint64_t key[kSortItems];
+  uint32_t val[kSortItems], pre[kSortItems];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * 32 + lane;
+    bool ok = i < n;
+    key[r] = ok ? kin[i] : 0;
+    val[r] = ok ? vin[i] : 0;
+    uint32_t d = ok ? digit_of(key[r], shift) : 0xffffffffu;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = ok ? wcnt[w][d] : 0u;
+    __syncwarp();
+    if (ok && (peers & lt) == 0) wcnt[w][d] = before + __popc(peers);
+    __syncwarp();
+    pre[r] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kSortBins; d += kSortThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      uint32_t c = wcnt[k][d];
+      wcnt[k][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * 32 + lane;
+    if (i < n) {
+      uint32_t d = digit_of(key[r], shift);
+      uint32_t pos = dbase[d] + wcnt[w][d] + pre[r];
+      kout[pos] = key[r];
+      vout[pos] = val[r];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Topology (Karras 2012): one thread per internal node i in [0, T-2].
+// delta(i, j) = clz64(k_i ^ k_j), or 64 + clz32(i ^ j) for equal keys,
+// -1 outside [0, T-1].
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int kdelta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = k[i], b = k[j];
+  if (a != b) return __clzll((long long)(a ^ b));
+  return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, Node* __restrict__ nodes,
+                         int32_t* __restrict__ leaf_slot, int32_t* __restrict__ node_slot) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (kdelta(k, n, i, i + 1) - kdelta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = kdelta(k, n, i, i - d);
+  int64_t lmax = 2;
+  while (kdelta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (kdelta(k, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = kdelta(k, n, i, j);
+  int64_t s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (kdelta(k, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+  int32_t c0, c1;
+  if (lo == gamma) { c0 = ~(int32_t)gamma; leaf_slot[gamma] = (int32_t)(2 * i); }
+  else { c0 = (int32_t)gamma; node_slot[gamma] = (int32_t)(2 * i); }
+  if (hi == gamma + 1) { c1 = ~(int32_t)(gamma + 1); leaf_slot[gamma + 1] = (int32_t)(2 * i + 1); }
+  else { c1 = (int32_t)(gamma + 1); node_slot[gamma + 1] = (int32_t)(2 * i + 1); }
+  nodes[i].d = make_int4(c0, c1, 0, 0);
+  if (i == 0) node_slot[0] = -1;
+}
+
+// Permute the index buffer and materials into leaf (sorted) order.
+__global__ void k_gather_sorted(const uint32_t* __restrict__ order, const uint32_t* __restrict__ idx,
+                                const uint32_t* __restrict__ tmat, int64_t nt, uint4* __restrict__ sidx,
+                                uint32_t* __restrict__ smat) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  uint32_t o = order[i];
+  sidx[i] = make_uint4(idx[3 * (int64_t)o], idx[3 * (int64_t)o + 1], idx[3 * (int64_t)o + 2], o);
+  smat[i] = tmat[o];
+}
+
+__device__ __forceinline__ void store_box(Node* node, int side, float3 lo, float3 hi) {
+  float* f = reinterpret_cast<float*>(node);
+  if (side == 0) {
+    *reinterpret_cast<float4*>(f) = make_float4(lo.x, lo.y, lo.z, hi.x);
+    *reinterpret_cast<float2*>(f + 4) = make_float2(hi.y, hi.z);
+  } else {
+    *reinterpret_cast<float2*>(f + 6) = make_float2(lo.x, lo.y);
+    *reinterpret_cast<float4*>(f + 8) = make_float4(lo.z, hi.x, hi.y, hi.z);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Refit: one thread per leaf (sorted position).  Transform the triangle,
+// write its 48-B record, store its box in the parent's slot; then climb:
+// the second thread to arrive at a node (odd counter value -- every refit
+// adds exactly 2 per node, so no reset is needed) unions the node's two
+// child boxes into the grandparent's slot.  Min/max are exact, so the boxes
+// do not depend on the arrival order.  HEIGHT also records subtree heights
+// (build only).
+// ----------------------------------------------------------------------------
+template <bool HEIGHT>
+__global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                        const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                        const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
+                        Node* nodes, const int32_t* __restrict__ leaf_slot,
+                        const int32_t* __restrict__ node_slot, uint32_t* counters) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  uint4 id = sidx[i];
+  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
+  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
+  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
+  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
+  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
+  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
+  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
+  if (nt == 1) {  // single leaf: node 0 holds it on both sides
+    store_box(nodes, 0, lo, hi);
+    store_box(nodes, 1, lo, hi);
+    if (HEIGHT) nodes[0].d = make_int4(~0, ~0, 0, 0);
+    return;
+  }
+  int32_t slot = leaf_slot[i];
+  int h = 0;
+  while (true) {
+    int32_t p = slot >> 1;
+    Node* node = nodes + p;
+    store_box(node, slot & 1, lo, hi);
+    if (HEIGHT) reinterpret_cast<int*>(&node->d)[2 + (slot & 1)] = h;
+    __threadfence();
+    uint32_t old = atomicAdd(counters + p, 1u);
+    if ((old & 1u) == 0) return;  // first arrival: the sibling finishes this node
+    __threadfence();
+    float4 a = __ldcg(&node->a), b = __ldcg(&node->b), c = __ldcg(&node->c);
+    lo = f3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
+    hi = f3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
+    if (HEIGHT) {
+      int4 d = __ldcg(&node->d);
+      h = 1 + max(d.z, d.w);
+    }
+    slot = node_slot[p];
+    if (slot < 0) return;  // root done
+  }
+}
+
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace
+
+int lbvh_validate(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host) {
+  uint32_t* bad = s->ctrl + 8;
+  if (int e = cuda_check(cudaMemsetAsync(bad, 0, 4, st), "memset")) return e;
+  int64_t n = std::max(s->nv, s->nt);
+  if (n > 0) {
+    int g = (int)std::min<int64_t>(grid_for(n, 256), 4 * 148 * 8);
+    k_validate<<<g, 256, 0, st>>>(s->rest, s->nv, s->idx, s->tmat, s->nt, s->vbody, s->nmat, s->nbody, bad);
+    if (int e = cuda_check(cudaGetLastError(), "k_validate")) return e;
+  }
+  if (int e = cuda_check(cudaMemcpyAsync(bad_host, bad, 4, cudaMemcpyDeviceToHost, st), "copy")) return e;
+  if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
+  return cuda_check(cudaMemsetAsync(bad, 0, 4, st), "memset");
+}
+
+int lbvh_build(fire_scene_s* s, cudaStream_t st) {
+  const int64_t T = s->nt;
+  if (T == 0) { s->built = true; s->height = 0; return FIRE_OK; }
+  // bounds live in ctrl[9..14]: lo = +inf ordered, hi = -inf ordered
+  uint32_t init[6];
+  for (int k = 0; k < 3; ++k) { init[k] = 0xffffffffu; init[3 + k] = 0u; }
+  if (int e = cuda_check(cudaMemcpyAsync(s->ctrl + 9, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
+  uint32_t* bounds = s->ctrl + 9;
+  prof_begin(s, kStageBuild, st);
+  k_centroids<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->idx, s->vbody, s->xf, T, s->cen, bounds);
+  k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->keys, s->order, s->keys_orig);
+  // sort (keys, order) with ping-pong through (keys_alt, vals_alt); 7 passes
+  const int ntiles = (int)((T + kSortTile - 1) / kSortTile);
+  uint32_t* totals = s->hist + (int64_t)kSortBins * ntiles;
+  uint64_t* ka = s->keys; uint32_t* va = s->order;
+  uint64_t* kb = s->keys_alt; uint32_t* vb = s->vals_alt;
+  for (int p = 0; p < kSortPasses; ++p) {
+    int shift = p * kSortBits;
+    k_sort_upsweep<<<ntiles, kSortThreads, 0, st>>>(ka, T, shift, s->hist, ntiles);
+    k_sort_scan<<<kSortBins, 1024, 0, st>>>(s->hist, ntiles, totals);
+    k_sort_downsweep<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, T, shift, s->hist, ntiles, totals);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // odd pass count: results are in the alt buffers; swap ownership
+  if (ka != s->keys) { std::swap(s->keys, s->keys_alt); std::swap(s->order, s->vals_alt); }
+  if (T > 1) k_karras<<<grid_for(T - 1, 256), 256, 0, st>>>(s->keys, T, s->nodes, s->leaf_slot, s->node_slot);
+  k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat);
+  if (T > 1)
+    if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;
+  k_refit<true><<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+                                                  s->nodes, s->leaf_slot, s->node_slot, s->counters);
+  prof_end(s, kStageBuild, st);
+  if (int e = cuda_check(cudaGetLastError(), "build kernels")) return e;
+  int4 d0;
+  if (int e = cuda_check(cudaMemcpyAsync(&d0, &s->nodes[0].d, sizeof(int4), cudaMemcpyDeviceToHost, st), "copy")) return e;
+  if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
+  s->height = T > 1 ? 1 + std::max(d0.z, d0.w) : 1;
+  s->built = true;
+  return FIRE_OK;
+}
+
+int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
+  const int64_t T = s->nt;
+  if (T == 0) return FIRE_OK;
+  prof_begin(s, kStageRefit, st);
+  k_refit<false><<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+                                                   s->nodes, s->leaf_slot, s->node_slot, s->counters);
+  prof_end(s, kStageRefit, st);
+  return cuda_check(cudaGetLastError(), "k_refit");
+}
+
+}  // namespace fire

@@ -1,0 +1,137 @@
+"""Differentiable shading on the GPU: the hand-written backward kernel
+against the oracle's FP64 analytic gradient (1e-4) and FP64 central finite
+differences (1e-3), both with |delta| <= tol * max(|g_ref|, 1e-3 ||g_ref||_inf),
+and the torch.autograd.Function wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from gpu_common import build_pair, compare_samples, gbuf_of, torch_cuda, THREADS
+
+pytestmark = pytest.mark.gpu
+
+
+def _close(g, ref, tol):
+    g, ref = np.asarray(g, np.float64).ravel(), np.asarray(ref, np.float64).ravel()
+    floor = 1e-3 * np.abs(ref).max()
+    err = np.abs(g - ref) / np.maximum(np.abs(ref), floor)
+    return float(err.max())
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = torch_cuda()
+    import paper_2410_05095_b300 as fb
+    w = sg.workload_grad500k(192, 192)
+    cam, lights = w.camera, w.lights
+    G, S = build_pair(w.scene)
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, lights, gbuf=gb)
+    g = gbuf_of(gb)
+    ref = S.render_all_samples(cam, lights, threads=THREADS)
+    _, bad = compare_samples(g, ref)
+    assert not bad.any(), "gradient test needs identical visibility"
+    P0 = oracle.params_of(w.scene.mats)
+    I0 = np.array([l.intensity for l in lights], np.float64)
+    tm, ti = sg.perturbed_params(w.scene.mats, I0)
+    Pt = oracle.params_of(tm)
+    target = S.shade_f64(cam, lights, ref, Pt, ti.astype(np.float64))
+    return dict(torch=torch, fb=fb, w=w, cam=cam, lights=lights, G=G, S=S, gb=gb, ref=ref, P0=P0, I0=I0,
+                target=target)
+
+
+def _gpu_grad(s, P, I):
+    torch = s["torch"]
+    cam = s["cam"]
+    params = torch.from_numpy(P.astype(np.float32)).cuda()
+    inten = torch.from_numpy(I.astype(np.float32)).cuda()
+    img = s["G"].shade(s["gb"], cam, s["lights"], params, inten)
+    npx = cam.width * cam.height * 3
+    tgt = torch.from_numpy(s["target"].astype(np.float32)).cuda()
+    dimg = torch.zeros_like(img)
+    dimg[..., :3] = 2.0 * (img[..., :3] - tgt) / npx
+    dP = torch.zeros_like(params)
+    dI = torch.zeros_like(inten)
+    s["G"].shade_backward(s["gb"], cam, s["lights"], params, inten, dimg, dP, dI)
+    return img, dimg, dP.cpu().numpy().astype(np.float64), dI.cpu().numpy().astype(np.float64)
+
+
+def test_backward_matches_oracle_analytic(setup):
+    s = setup
+    img, dimg, gP, gI = _gpu_grad(s, s["P0"], s["I0"])
+    # oracle analytic gradient at the same upstream (FP64 forward image)
+    img64 = s["S"].shade_f64(s["cam"], s["lights"], s["ref"], s["P0"], s["I0"])
+    npx = s["cam"].width * s["cam"].height * 3
+    d64 = 2.0 * (img64 - s["target"]) / npx
+    rP, rI = s["S"].grad_f64(s["cam"], s["lights"], s["ref"], s["P0"], s["I0"], d64)
+    err = _close(np.concatenate([gP.ravel(), gI]), np.concatenate([rP.ravel(), rI]), 1e-4)
+    assert err <= 1e-4, err
+    # the forward image agrees with the FP64 twin too
+    a = img.cpu().numpy()[..., :3].astype(np.float64)
+    assert np.max(np.abs(a - img64) / np.maximum(np.abs(img64), 1e-6)) < 2e-3
+
+
+def test_backward_matches_finite_differences(setup):
+    s = setup
+    _, _, gP, gI = _gpu_grad(s, s["P0"], s["I0"])
+    S, cam, lights, ref = s["S"], s["cam"], s["lights"], s["ref"]
+    npx = cam.width * cam.height * 3
+
+    def loss(P, I):
+        return float(np.sum((S.shade_f64(cam, lights, ref, P, I) - s["target"]) ** 2) / npx)
+
+    used = np.unique(s["w"].scene.tri_mat[ref["prim"][ref["prim"] >= 0]])
+    fd, g = [], []
+    for m in used[:12]:
+        for j in range(5):
+            h = max(1e-4 * abs(s["P0"][m, j]), 1e-6)
+            Pp, Pm = s["P0"].copy(), s["P0"].copy()
+            Pp[m, j] += h
+            Pm[m, j] -= h
+            fd.append((loss(Pp, s["I0"]) - loss(Pm, s["I0"])) / (2 * h))
+            g.append(gP[m, j])
+    for j in range(len(s["I0"])):
+        h = 1e-4 * s["I0"][j]
+        Ip, Im = s["I0"].copy(), s["I0"].copy()
+        Ip[j] += h
+        Im[j] -= h
+        fd.append((loss(s["P0"], Ip) - loss(s["P0"], Im)) / (2 * h))
+        g.append(gI[j])
+    err = _close(g, fd, 1e-3)
+    assert err <= 1e-3, err
+
+
+def test_autograd_function_and_descent(setup):
+    """FireShade.apply gives the kernel's gradient; a few steps of gradient
+    descent on the perturbed start reduce the loss."""
+    s = setup
+    torch = s["torch"]
+    from paper_2410_05095_b300.autograd import FireShade
+    P = torch.from_numpy(s["P0"].astype(np.float32)).cuda().requires_grad_(True)
+    I = torch.from_numpy(s["I0"].astype(np.float32)).cuda().requires_grad_(True)
+    tgt = torch.from_numpy(s["target"].astype(np.float32)).cuda()
+    img = FireShade.apply(P, I, s["G"], s["gb"], s["cam"], s["lights"])
+    loss = ((img[..., :3] - tgt) ** 2).mean()
+    loss.backward()
+    _, _, gP, gI = _gpu_grad(s, s["P0"], s["I0"])
+    assert np.allclose(P.grad.cpu().numpy(), gP, rtol=1e-5, atol=1e-12)
+    assert np.allclose(I.grad.cpu().numpy(), gI, rtol=1e-5, atol=1e-12)
+    # descent from the perturbed parameters towards the target
+    tm, ti = sg.perturbed_params(s["w"].scene.mats, s["I0"])
+    P = torch.from_numpy(oracle.params_of(s["w"].scene.mats).astype(np.float32)).cuda().requires_grad_(True)
+    I = torch.from_numpy(s["I0"].astype(np.float32)).cuda().requires_grad_(True)
+    opt = torch.optim.Adam([P, I], lr=1e-2)
+    losses = []
+    for _ in range(20):
+        opt.zero_grad()
+        img = FireShade.apply(P, I, s["G"], s["gb"], s["cam"], s["lights"])
+        l = ((img[..., :3] - tgt) ** 2).mean()
+        l.backward()
+        opt.step()
+        with torch.no_grad():
+            P[:, :3].clamp_(0.01, 0.99)
+            P[:, 3].clamp_(0.05, 1.0)
+            I.clamp_(min=1e-3)
+        losses.append(float(l))
+    assert losses[-1] < 0.5 * losses[0]

@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the oracle on
+the same seeded inputs, at sizes the oracle finishes in seconds, spanning
+several tiles and ragged tails, plus the edge cases of the method."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from gpu_common import (assert_lbvh_equal, assert_radiance_close, assert_tris_equal, build_pair,
+                        compare_samples, gbuf_of, pixel_ok_mask, torch_cuda, THREADS)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fb():
+    import paper_2410_05095_b300 as fb
+    torch_cuda()
+    return fb
+
+
+def _gbuf(cam):
+    torch = torch_cuda()
+    return torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+
+
+def _render(G, cam, lights, **opts):
+    import paper_2410_05095_b300 as fb
+    torch = torch_cuda()
+    gb = _gbuf(cam)
+    out = torch.zeros((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
+    G.render(cam, lights, out=out, gbuf=gb, opts=fb.fire.make_opts(**opts) if opts else None)
+    assert G.sync_status() == 0
+    return out.cpu().numpy(), gbuf_of(gb)
+
+
+# ----------------------------------------------------------------------------- LBVH
+@pytest.mark.parametrize("name", ["tiny41k", "mid1m"])
+def test_lbvh_bitexact(fb, name):
+    w = sg.WORKLOADS[name]()
+    G, S = build_pair(w.scene)
+    assert_lbvh_equal(G, S, w.scene)
+    assert G.info()["height"] >= 2
+
+
+def test_lbvh_duplicate_keys_and_tiny_counts(fb):
+    """Many equal Morton codes (index-augmented topology); 1, 2 and 3 triangles."""
+    rng = sg.Rng(77)
+    for n in (1, 2, 3, 5000):
+        tris = []
+        for _ in range(n):
+            c = np.array([float(int(rng.u() * 4)) for _ in range(3)])
+            tris.append(np.stack([c - 0.1, c, c + np.array([0.1, -0.05, 0.1])]))
+        sc = sg.assemble([(np.concatenate(tris), np.arange(3 * n).reshape(n, 3))], 1,
+                         sg.random_materials(rng, 1))
+        G, S = build_pair(sc)
+        assert_lbvh_equal(G, S, sc)
+
+
+def test_refit_frames_bitexact(fb):
+    w = sg.workload_frame7m(nspheres=120, cells=64)
+    sc = w.scene
+    G, S = build_pair(sc, w.motion.xforms())
+    order = G.dump("order")
+    for frame in range(3):
+        xf = w.motion.step()
+        G.refit(xf)
+        S.update(xf, rebuild=False)
+        assert np.array_equal(G.dump("order"), order)
+        assert np.array_equal(G.dump("boxes"), S.get("boxes"))
+        assert_tris_equal(G, S, sc)
+    # device-resident transforms give the same result
+    torch = torch_cuda()
+    xf = w.motion.step()
+    G.refit(torch.from_numpy(xf).cuda())
+    S.update(xf, rebuild=False)
+    assert np.array_equal(G.dump("boxes"), S.get("boxes"))
+    # a rebuild after motion re-derives everything
+    G.build(xf)
+    S.update(xf, rebuild=True)
+    assert_lbvh_equal(G, S, sc)
+
+
+# --------------------------------------------------------------------------- render
+def test_render_tiny_full_image(fb):
+    w = sg.workload_tiny41k()
+    G, S = build_pair(w.scene)
+    img, g = _render(G, w.camera, w.lights)
+    ref = S.render_all_samples(w.camera, w.lights, threads=THREADS)
+    frac, bad = compare_samples(g, ref)
+    assert np.array_equal(g["t"][~bad], ref["t"][~bad])
+    img_ref = S.render_image(w.camera, w.lights, threads=THREADS)
+    ok = pixel_ok_mask(bad, w.camera.width, w.camera.height, 1)
+    assert_radiance_close(img, img_ref, ok)
+    assert np.array_equal(img[..., 3][ok], img_ref[..., 3][ok])
+    assert (g["prim"] >= 0).mean() > 0.5
+
+
+def test_render_mid_4spp_three_lights(fb):
+    w = sg.workload_mid1m(320, 180, 4)
+    G, S = build_pair(w.scene)
+    img, g = _render(G, w.camera, w.lights)
+    ref = S.render_all_samples(w.camera, w.lights, threads=THREADS)
+    frac, bad = compare_samples(g, ref)
+    img_ref = S.render_image(w.camera, w.lights, threads=THREADS)
+    assert_radiance_close(img, img_ref, pixel_ok_mask(bad, 320, 180, 4))
+    lit = (ref["vis"] & 0xFF) != 0
+    shadowed = ((ref["vis"] >> 8) & ~ref["vis"] & 0xFF) != 0
+    assert lit.mean() > 0.2 and shadowed.mean() > 0.01  # all three light kinds exercised
+
+
+@pytest.mark.parametrize("W,H,spp", [(37, 23, 4), (37, 23, 1), (8, 4, 1), (1, 1, 4), (129, 3, 1)])
+def test_render_ragged_sizes(fb, W, H, spp):
+    w = sg.workload_tiny41k()
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, W, H, spp)
+    G, S = build_pair(w.scene)
+    img, g = _render(G, cam, w.lights)
+    ref = S.render_all_samples(cam, w.lights)
+    _, bad = compare_samples(g, ref)
+    assert_radiance_close(img, S.render_image(cam, w.lights), pixel_ok_mask(bad, W, H, spp))
+
+
+def test_row_bands_equal_full_render(fb):
+    """Image partition by row bands (the replica split): two band renders
+    into one buffer equal the full render bit for bit."""
+    torch = torch_cuda()
+    w = sg.workload_tiny41k()
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 96, 61, 4)
+    G, _ = build_pair(w.scene)
+    full = G.render(cam, w.lights)
+    part = torch.full_like(full, -1.0)
+    G.render(cam, w.lights, out=part, opts=fb.fire.make_opts(row_begin=0, row_end=29))
+    G.render(cam, w.lights, out=part, opts=fb.fire.make_opts(row_begin=29, row_end=61))
+    assert torch.equal(full, part)
+
+
+def test_empty_scene_and_single_triangle(fb):
+    torch = torch_cuda()
+    mats = sg.random_materials(sg.Rng(1), 2)
+    empty = sg.Scene(verts=np.zeros((0, 4), np.float32), idx=np.zeros((0, 3), np.uint32),
+                     tri_mat=np.zeros(0, np.uint32), vert_body=np.zeros(0, np.uint16), mats=mats, nbody=1)
+    G = fb.Scene.from_numpy(empty)
+    G.build(empty.identity_xforms())
+    cam = sg.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 60.0, 16, 8, 4)
+    out = G.render(cam, [sg.LIGHTS_MAIN[0]])
+    assert torch.count_nonzero(out) == 0
+    one = sg.assemble([(np.array([[-1.0, -1, 0], [1, -1, 0], [0, 1, 0]]), np.array([[0, 1, 2]]))], 2, mats)
+    G1, S1 = build_pair(one)
+    assert_lbvh_equal(G1, S1, one)
+    cam = sg.Camera((0.1, 0.2, 5), (0, 0, 0), (0, 1, 0), 40.0, 33, 17, 4)
+    img, g = _render(G1, cam, [sg.Light(0, (0.0, 0.0, 4.0), 10.0)])
+    ref = S1.render_all_samples(cam, [sg.Light(0, (0.0, 0.0, 4.0), 10.0)])
+    _, bad = compare_samples(g, ref)
+    assert not bad.any()
+    assert_radiance_close(img, S1.render_image(cam, [sg.Light(0, (0.0, 0.0, 4.0), 10.0)]))
+
+
+# ---------------------------------------------------------------------- error paths
+def test_error_paths(fb):
+    torch = torch_cuda()
+    w = sg.workload_tiny41k()
+    sc = w.scene
+    G = fb.Scene.from_numpy(sc)
+    cam = w.camera
+    with pytest.raises(fb.FireError) as e:
+        G.refit(sc.identity_xforms())
+    assert e.value.code == -6                        # refit before build
+    with pytest.raises(fb.FireError) as e:
+        G.render(cam, w.lights)
+    assert e.value.code == -6
+    bad = sc.identity_xforms()
+    bad[0, 3] = np.nan
+    with pytest.raises(fb.FireError) as e:
+        G.build(bad)
+    assert e.value.code == -1                        # non-finite transform
+    G.build(sc.identity_xforms())
+    for bad_cam in (sg.Camera(cam.pos, cam.target, cam.up, 60.0, 16, 16, 2),
+                    sg.Camera(cam.pos, cam.pos, cam.up, 60.0, 16, 16, 1),
+                    sg.Camera(cam.pos, cam.target, cam.up, 180.0, 16, 16, 1)):
+        with pytest.raises(fb.FireError) as e:
+            G.render(bad_cam, w.lights)
+        assert e.value.code == -1
+    with pytest.raises(fb.FireError) as e:
+        G.render(cam, [sg.LIGHTS_MAIN[0]] * 9)
+    assert e.value.code == -1
+    with pytest.raises(fb.FireError):
+        G.render(cam, w.lights, opts=fb.fire.make_opts(row_begin=5, row_end=3))
+    with pytest.raises(fb.FireError):
+        G.render(cam, w.lights, opts=fb.fire.make_opts(stack_depth=2))  # below the tree height
+    # out-of-range index / material / body -> counted on the device, rejected
+    for field, val in (("idx", sc.nv), ("tri_mat", 9), ("vert_body", 3)):
+        bad_sc = sg.Scene(verts=sc.verts, idx=sc.idx.copy(), tri_mat=sc.tri_mat.copy(),
+                          vert_body=sc.vert_body.copy(), mats=sc.mats, nbody=1)
+        getattr(bad_sc, field).reshape(-1)[7] = val
+        with pytest.raises(fb.FireError) as e:
+            fb.Scene.from_numpy(bad_sc)
+        assert e.value.code == -1
+    # injected allocation failure -> OOM, and the next create works
+    fb.fire.fail_next_alloc(3)
+    with pytest.raises(fb.FireError) as e:
+        fb.Scene.from_numpy(sc)
+    assert e.value.code == -2
+    fb.Scene.from_numpy(sc).destroy()
+
+
+def test_device_error_flags(fb):
+    """Stack overflow and the iteration cap are reported through the sticky
+    device error word (no trap): a forced 8-entry stack on a deep tree, and
+    a cap of 3 node visits per ray."""
+    w = sg.workload_mid1m(64, 36, 1)
+    G, _ = build_pair(w.scene)
+    assert G.info()["height"] > 8
+    G.render(w.camera, w.lights, opts=fb.fire.make_opts(stack_depth=8, flags=1))
+    assert G.sync_status() == -4
+    assert G.sync_status() == 0                       # cleared by the read
+    G.set_iteration_cap(3)
+    G.render(w.camera, w.lights)
+    assert G.sync_status() == -5
+    G.set_iteration_cap(0)
+    G.render(w.camera, w.lights)
+    assert G.sync_status() == 0
+
+
+# ---------------------------------------------------------------------------- batch
+def test_batch_equals_sequential(fb):
+    torch = torch_cuda()
+    rng = sg.Rng(2024)
+    scenes, G = [], []
+    for s in range(3):
+        sc = sg.scene_icospheres_terrain(rng, 3 + 4 * s, 32, 32)
+        scenes.append(sc)
+        g = fb.Scene.from_numpy(sc)
+        g.build(sc.identity_xforms())
+        G.append(g)
+    res = [(64, 64, 1), (37, 23, 4), (128, 96, 1), (20, 11, 1), (33, 9, 4), (96, 64, 1)]
+    cams, cam_scene = [], []
+    for i, (W, H, spp) in enumerate(res):
+        c = sg.orbit_camera(rng, W, H, spp)
+        cams.append(c)
+        cam_scene.append(i % 3)
+    lights = [sg.LIGHTS_MAIN[:1], sg.LIGHTS_MAIN[:2], sg.LIGHTS_MAIN[:3]]
+    outs = [torch.zeros((c.height, c.width, 4), device="cuda") for c in cams]
+    fb.render_batch(G, cams, cam_scene, lights, outs)
+    cfg = fb.batch_last_config()
+    assert cfg["tuned"] == 1 and cfg["threads"] in (64, 128, 256)
+    for c, si, o in zip(cams, cam_scene, outs):
+        ref = G[si].render(c, lights[si])
+        assert torch.equal(o, ref)
+    # graph replay gives the same images
+    outs2 = [o.clone().fill_(-1) for o in outs]
+    fb.render_batch(G, cams, cam_scene, lights, outs2)
+    assert fb.batch_last_config()["tuned"] == 0
+    for a, b in zip(outs, outs2):
+        assert torch.equal(a, b)
+    # and after a refit of one scene (new poses, same buffers) the replay reflects it
+    xf = scenes[1].identity_xforms()
+    xf[0, 3] = 0.25
+    G[1].refit(xf)
+    fb.render_batch(G, cams, cam_scene, lights, outs2)
+    for c, si, o in zip(cams, cam_scene, outs2):
+        assert torch.equal(o, G[si].render(c, lights[si]))
+    for g in G:
+        assert g.sync_status() == 0
+
+
+# ------------------------------------------------------------------- differentiable
+def test_shade_gbuffer_equals_render(fb):
+    torch = torch_cuda()
+    w = sg.workload_tiny41k(64, 48)
+    cam = sg.Camera(**{**w.camera.__dict__, "spp": 4})
+    lights = [sg.LIGHTS_MAIN[0], sg.LIGHTS_MAIN[1]]
+    G, _ = build_pair(w.scene)
+    gb = _gbuf(cam)
+    img = G.render(cam, lights, gbuf=gb)
+    params = torch.from_numpy(oracle.params_of(w.scene.mats).astype(np.float32)).cuda()
+    inten = torch.tensor([l.intensity for l in lights], dtype=torch.float32, device="cuda")
+    img2 = G.shade(gb, cam, lights, params, inten)
+    assert torch.equal(img, img2)
