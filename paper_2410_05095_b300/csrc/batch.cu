@@ -162,7 +162,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
   std::vector<BatchCam> h(ncams);
   std::vector<int64_t> shape;
   int ntasks = 0, maxh = 0;
-  int64_t cap = INT64_MAX;
+  int64_t cap = 64;  // safety bound: a ray visits each node at most once
   for (int i = 0; i < ncams; ++i) {
     fire_scene_s* s = scenes[cam_scene[i]];
     BatchCam& b = h[i];
@@ -181,7 +181,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     TaskGrid g = make_grid(b.cam.W, 0, b.cam.H, b.cam.spp);
     ntasks += g.tiles_x * g.tiles_y;
     maxh = std::max(maxh, s->height);
-    if (s->iter_cap > 0) cap = std::min(cap, s->iter_cap);
+    cap = std::max(cap, 2 * s->nt + 64);
     shape.push_back(s->nt);
     shape.push_back(b.cam.W);
     shape.push_back(b.cam.H);

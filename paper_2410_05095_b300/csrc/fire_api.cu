@@ -575,6 +575,7 @@ int fire_sync_status(fire_scene s, void* stream) {
   if (int e = cuda_check(cudaMemset(s->ctrl + 8, 0, 4), "status")) return e;
   if (w & kErrStack) return set_error(FIRE_ERR_STACK_OVERFLOW, "traversal stack overflow");
   if (w & kErrTimeout) return set_error(FIRE_ERR_TIMEOUT, "traversal iteration cap reached");
+  if (w & kErrCorrupt) return set_error(FIRE_ERR_CUDA, "traversal met a link outside the tree");
   return FIRE_OK;
 }
 

@@ -51,6 +51,7 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // Device error word bits
 constexpr uint32_t kErrStack = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrCorrupt = 4u;  // a link outside the tree (never for a built tree)
 
 struct CamParams {
   float ox, oy, oz;     // position

@@ -254,8 +254,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(const uint64_t*
     if (i < n) {
       uint32_t d = digit_of(key[r], shift);
       uint32_t pos = dbase[d] + wcnt[w][d] + pre[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      if (pos < n) {  // always true for a consistent histogram; keeps stores in bounds regardless
+        kout[pos] = key[r];
+        vout[pos] = val[r];
+      }
     }
   }
 }
@@ -292,6 +294,7 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, Node* __rest
   } while (t > 1);
   int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
   int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+  if (gamma < lo || gamma >= hi) return;  // impossible for sorted keys; slots stay -1
   int32_t c0, c1;
   if (lo == gamma) { c0 = ~(int32_t)gamma; leaf_slot[gamma] = (int32_t)(2 * i); }
   else { c0 = (int32_t)gamma; node_slot[gamma] = (int32_t)(2 * i); }
@@ -358,6 +361,7 @@ __global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restr
   int32_t slot = leaf_slot[i];
   int h = 0;
   while (true) {
+    if (slot < 0 || (slot >> 1) >= nt - 1) return;  // never for a complete topology
     int32_t p = slot >> 1;
     Node* node = nodes + p;
     store_box(node, slot & 1, lo, hi);
@@ -422,7 +426,12 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   }
   // odd pass count: results are in the alt buffers; swap ownership
   if (ka != s->keys) { std::swap(s->keys, s->keys_alt); std::swap(s->order, s->vals_alt); }
-  if (T > 1) k_karras<<<grid_for(T - 1, 256), 256, 0, st>>>(s->keys, T, s->nodes, s->leaf_slot, s->node_slot);
+  if (T > 1) {
+    if (int e = cuda_check(cudaMemsetAsync(s->leaf_slot, 0xff, 4 * T, st), "memset")) return e;
+    if (int e = cuda_check(cudaMemsetAsync(s->node_slot, 0xff, 4 * (T - 1), st), "memset")) return e;
+    if (int e = cuda_check(cudaMemsetAsync(s->nodes, 0xff, 64 * (T - 1), st), "memset")) return e;
+    k_karras<<<grid_for(T - 1, 256), 256, 0, st>>>(s->keys, T, s->nodes, s->leaf_slot, s->node_slot);
+  }
   k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat);
   if (T > 1)
     if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;

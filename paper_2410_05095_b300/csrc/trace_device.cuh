@@ -112,6 +112,10 @@ __device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float
       atomicOr(c.err, kErrTimeout);
       return;
     }
+    if ((uint64_t)cur >= (uint64_t)(c.nt > 1 ? c.nt - 1 : 1)) {  // never for a built tree
+      atomicOr(c.err, kErrCorrupt);
+      break;
+    }
     const Node* n = c.nodes + cur;
     float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
     int4 dd = __ldg(&n->d);
@@ -121,6 +125,7 @@ __device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float
     if (h0 && dd.x < 0) {
       int p = ~dd.x;
       float t;
+      if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
       float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
              C = __ldg(c.tris + 3 * (int64_t)p + 2);
       if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f()) {
@@ -132,6 +137,7 @@ __device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float
     if (h1 && dd.y < 0) {
       int p = ~dd.y;
       float t;
+      if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
       float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
              C = __ldg(c.tris + 3 * (int64_t)p + 2);
       if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f()) {
@@ -171,6 +177,10 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
       atomicOr(c.err, kErrTimeout);
       return false;
     }
+    if ((uint64_t)cur >= (uint64_t)(c.nt > 1 ? c.nt - 1 : 1)) {  // never for a built tree
+      atomicOr(c.err, kErrCorrupt);
+      break;
+    }
     const Node* n = c.nodes + cur;
     float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
     int4 dd = __ldg(&n->d);
@@ -183,6 +193,7 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
       bool& h = side ? h1 : h0;
       if (h && ch < 0) {
         int p = ~ch;
+        if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
         float t;
         float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
                C = __ldg(c.tris + 3 * (int64_t)p + 2);
@@ -205,6 +216,7 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
       cur = stack[--sp];
     }
   }
+  return false;
 }
 
 // Shadow-ray lift: eps = 1e-4 * |hi - lo| of the scene box (union of the
