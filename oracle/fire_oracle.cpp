@@ -537,51 +537,55 @@ SampleOut shade_sample(const orc_scene& S, const Cam& K, const orc_light* L, int
 // ---------------------------------------------------------------------------
 // FP64 twin of the shading (fixed visibility), with its analytic gradient.
 // ---------------------------------------------------------------------------
-struct Geo64 { D3 n, v; int nlights; D3 l[8]; double g[8], ndl[8]; bool lit[8]; };
+// The gradient checks hold the geometry fixed at the frame the renderer
+// shades with: the FP32 hit frame and light vectors of the forward path
+// (hit_frame, light_vec, h = normalize(l + v)) give n.l, n.v, n.h, v.h and
+// the falloff g = 1/d^2 (1 for a directional light); everything that depends
+// on the material parameters and intensities is then evaluated in FP64.
+struct Cos64 { double nl, nv, nh, vh, g; bool lit; };
+struct Geo64 { int nlights; Cos64 c[8]; };
 
 bool geo64(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, int y, int s,
            int32_t prim, float t, uint16_t vis, Geo64& G) {
   if (prim < 0) return false;
-  V3 d32 = cam_dir(K, x, y, s);
-  D3 o = tod(K.o), d = tod(d32);
-  V3 a, b, c;
-  tri_verts(S, prim, a, b, c);
-  D3 n = dnorm(dcross(dsub(tod(b), tod(a)), dsub(tod(c), tod(a))));
-  if (ddot(n, d) > 0) n = dk(-n.x, -n.y, -n.z);
-  double eps = (double)scene_eps(S);
-  D3 p = dk(o.x + (double)t * d.x, o.y + (double)t * d.y, o.z + (double)t * d.z);
-  D3 po = dk(p.x + eps * n.x, p.y + eps * n.y, p.z + eps * n.z);
-  G.n = n;
-  G.v = dk(-d.x, -d.y, -d.z);
+  V3 o = K.o, d = cam_dir(K, x, y, s);
+  V3 n, po;
+  hit_frame(S, prim, o, d, t, scene_eps(S), n, po);
+  V3 v = neg3(d);
   G.nlights = nl;
   for (int j = 0; j < nl; ++j) {
-    G.lit[j] = (vis >> j) & 1u;
+    V3 l;
+    float E, tmax;
+    light_vec(L[j], po, l, E, tmax);
+    float d2 = 1.0f;
     if (L[j].type == 0) {
-      D3 lv = dsub(dk(L[j].v[0], L[j].v[1], L[j].v[2]), po);
-      double d2 = ddot(lv, lv);
-      G.l[j] = dnorm(lv);
-      G.g[j] = 1.0 / d2;
-    } else {
-      G.l[j] = dnorm(dk(L[j].v[0], L[j].v[1], L[j].v[2]));
-      G.g[j] = 1.0;
+      V3 lv = sub3(mk(L[j].v[0], L[j].v[1], L[j].v[2]), po);
+      d2 = dot3(lv, lv);
     }
-    G.ndl[j] = ddot(n, G.l[j]);
-    if (!(G.ndl[j] > 0)) G.lit[j] = false;
+    V3 h = normalize3(add3(l, v));
+    Cos64& c = G.c[j];
+    float ndl = dot3(n, l);
+    c.lit = ((vis >> j) & 1u) && ndl > 0.0f;
+    c.nl = std::max(ndl, 0.0f);
+    c.nv = std::max(dot3(n, v), 0.0f);
+    c.nh = std::max(dot3(n, h), 0.0f);
+    c.vh = std::max(dot3(v, h), 0.0f);
+    c.g = 1.0 / (double)d2;
   }
   return true;
 }
 
-// f_c and its derivatives d/d albedo_c, d/d rough, d/d metal (kmode 0).
+// f_c and its derivatives d/d albedo_c, d/d rough, d/d metal (kmode 0), FP64,
+// at fixed cosines.  dd is formed as (1-nh)(1+nh) + nh^2 a2 (no cancellation).
 struct Brdf64 { double f[3], dalb[3], dr[3], dm[3]; };
 
-Brdf64 brdf64(D3 n, D3 v, D3 l, const double* alb, double r, double m) {
-  D3 h = dnorm(dk(l.x + v.x, l.y + v.y, l.z + v.z));
-  double nl = std::max(ddot(n, l), 0.0), nv = std::max(ddot(n, v), 0.0);
-  double nh = std::max(ddot(n, h), 0.0), vh = std::max(ddot(v, h), 0.0);
+Brdf64 brdf64(const Cos64& cs, const double* alb, double r, double m) {
+  double nl = cs.nl, nv = cs.nv, nh = cs.nh, vh = cs.vh;
   double a = r * r, a2 = a * a;
-  double dd = nh * nh * (a2 - 1.0) + 1.0;
+  double s1 = (1.0 - nh) * (1.0 + nh);
+  double dd = s1 + nh * nh * a2;
   double D = a2 / (kPiD * dd * dd);
-  double dD_da2 = (dd - 2.0 * a2 * nh * nh) / (kPiD * dd * dd * dd);
+  double dD_da2 = (s1 - a2 * nh * nh) / (kPiD * dd * dd * dd);
   double dD_dr = dD_da2 * 4.0 * r * r * r;
   double k = (r + 1.0) * (r + 1.0) / 8.0, dk_dr = (r + 1.0) / 4.0;
   double gl = nl * (1.0 - k) + k, gv = nv * (1.0 - k) + k;
@@ -772,9 +776,9 @@ void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, 
         if (!geo64(*s, K, L, nl, x, y, k, prim[id], t[id], vis[id], G)) continue;
         const double* P = params + 5 * s->tri_mat[prim[id]];
         for (int j = 0; j < nl; ++j) {
-          if (!G.lit[j]) continue;
-          Brdf64 B = brdf64(G.n, G.v, G.l[j], P, P[3], P[4]);
-          for (int ch = 0; ch < 3; ++ch) acc[ch] += B.f[ch] * inten[j] * G.g[j] * G.ndl[j];
+          if (!G.c[j].lit) continue;
+          Brdf64 B = brdf64(G.c[j], P, P[3], P[4]);
+          for (int ch = 0; ch < 3; ++ch) acc[ch] += B.f[ch] * inten[j] * G.c[j].g * G.c[j].nl;
         }
       }
       for (int ch = 0; ch < 3; ++ch) img[3 * ((int64_t)y * K.W + x) + ch] = acc[ch] / K.spp;
@@ -799,9 +803,9 @@ void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, i
         const double* P = params + 5 * mat;
         double* dP = dparams + 5 * mat;
         for (int j = 0; j < nl; ++j) {
-          if (!G.lit[j]) continue;
-          Brdf64 B = brdf64(G.n, G.v, G.l[j], P, P[3], P[4]);
-          double w = G.g[j] * G.ndl[j] / K.spp;
+          if (!G.c[j].lit) continue;
+          Brdf64 B = brdf64(G.c[j], P, P[3], P[4]);
+          double w = G.c[j].g * G.c[j].nl / K.spp;
           for (int ch = 0; ch < 3; ++ch) {
             double up = gp[ch] * w;  // dL/d f_c, per unit intensity
             dP[ch] += up * inten[j] * B.dalb[ch];

@@ -205,7 +205,7 @@ void free_scene(fire_scene_s* s) {
   s->prof = nullptr;
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
-                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch};
+                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -486,7 +486,7 @@ int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_c
   if (int e = fill_args(s, cam, lights, nlights, &a)) return e;
   if (!gbuf || !params || (nlights > 0 && (!inten || !dinten)) || !dL_drgba || !dparams)
     return set_error(FIRE_ERR_INVALID_ARG, "NULL buffer");
-  if (s->nmat * 5 + nlights > 16384) return set_error(FIRE_ERR_INVALID_ARG, "too many materials for the backward");
+  if (s->nmat * 5 + nlights > 12288) return set_error(FIRE_ERR_INVALID_ARG, "too many materials for the backward");
   a.g = const_cast<fire_gbuffer_rec*>(gbuf);
   a.mats.p = params;
   cudaStream_t st = as_stream(stream);

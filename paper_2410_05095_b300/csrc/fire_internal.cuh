@@ -113,6 +113,8 @@ struct fire_scene_s {
   // render scratch
   fire_gbuffer_rec* gscratch = nullptr;
   size_t gscratch_n = 0;
+  double* bwd_partials = nullptr;  // per-block gradient partials of the backward
+  size_t bwd_partials_n = 0;
   // batch cache (see batch.cu)
   void* batch = nullptr;
   int64_t iter_cap = 0;

@@ -129,20 +129,26 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
 // Backward of k_shade<.., false> for L(image): per sample, the upstream
 // gradient of the pixel divided by spp, chained through
 //   rad_c = sum_j I_j g_j (n.l_j) f_c(albedo, r, m)
-// with g_j = 1/d^2 (point) or 1.  Derivatives of f_c (a = r^2, a2 = a^2):
-//   dD/dr   = (dd - 2 a2 nh^2) / (pi dd^3) * 4 r^3
+// with g_j = 1/d^2 (point) or 1.  Derivatives of f_c (a = r^2, a2 = a^2,
+// dd = (1-nh)(1+nh) + nh^2 a2, the form of nh^2 (a2-1) + 1 without
+// cancellation near the highlight peak):
+//   dD/dr   = ((1-nh)(1+nh) - a2 nh^2) / (pi dd^3) * 4 r^3
 //   dvis/dr = -vis ((1 - nl)/gl + (1 - nv)/gv) (r + 1)/4
 //   df/dalb = (1-F)(1-m)/pi + (D vis - (1-m) alb/pi)(1 - w5) m
 //   df/dm   = (D vis - (1-m) alb/pi)(1 - w5)(alb - 0.04) - (1-F) alb/pi
 //   df/dr   = F (dD/dr vis + D dvis/dr)
-// Gradients are summed per warp when all lanes share a material, then per
-// block in shared memory, then once per block into global memory.
+// Per-sample terms are FP32; sums are FP64: per warp (shuffles) when the
+// warp shares one material, else shared-memory atomics, then each block
+// stores its partials and the last block to finish adds them in block order
+// (deterministic) into the FP32 outputs.
 __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
-                                                   const float* dL, float* dparams, float* dinten) {
-  extern __shared__ float sacc[];  // [nmat*5 + nlights]
+                                                   const float* dL, float* dparams, float* dinten,
+                                                   double* partials) {
+  extern __shared__ double sacc[];  // [nmat*5 + nlights]
+  __shared__ bool last_block;
   const int nm5 = a.mats.n * 5;
   const int nacc = nm5 + a.lights.n;
-  for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0f;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const float eps = scene_eps(a.nodes, a.nt);
@@ -153,10 +159,10 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
     if (task >= ntasks) break;
     int x, y, k;
     bool valid = task_sample(g, task, lane, x, y, k);
-    float gm[5] = {0, 0, 0, 0, 0};
-    float gl[kMaxLights];
+    double gm[5] = {0, 0, 0, 0, 0};
+    double gl[kMaxLights];
 #pragma unroll
-    for (int j = 0; j < kMaxLights; ++j) gl[j] = 0.0f;
+    for (int j = 0; j < kMaxLights; ++j) gl[j] = 0.0;
     int mat = -1;
     if (valid) {
       int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
@@ -187,9 +193,10 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
           float nl = fmaxf(ndl, 0.0f), nv = fmaxf(dot3(n, v), 0.0f);
           float nh = fmaxf(dot3(n, h), 0.0f), vh = fmaxf(dot3(v, h), 0.0f);
           float aa = r * r, a2 = aa * aa;
-          float dd = fmaf(nh * nh, a2 - 1.0f, 1.0f);
+          float s1 = (1.0f - nh) * (1.0f + nh), nh2a2 = (nh * nh) * a2;
+          float dd = s1 + nh2a2;
           float D = a2 / ((kPi * dd) * dd);
-          float dD_dr = (dd - 2.0f * a2 * nh * nh) / (kPi * dd * dd * dd) * (4.0f * r * r * r);
+          float dD_dr = (s1 - nh2a2) / (kPi * dd * dd * dd) * (4.0f * r * r * r);
           float kk = (r + 1.0f) * (r + 1.0f) * 0.125f, dk_dr = (r + 1.0f) * 0.25f;
           float gL = fmaf(nl, 1.0f - kk, kk), gV = fmaf(nv, 1.0f - kk, kk);
           float vis = 0.25f / (gL * gV);
@@ -206,10 +213,10 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
             float dm = dfdF * (1.0f - w5) * (alb[ch] - 0.04f) - (1.0f - F) * alb[ch] * kInvPi;
             float dr = F * (dD_dr * vis + D * dvis_dr);
             float u = up[ch] * wI;
-            gm[ch] += u * I * dalb;
-            gm[3] += u * I * dr;
-            gm[4] += u * I * dm;
-            gl[j] += u * f;
+            gm[ch] += (double)(u * I * dalb);
+            gm[3] += (double)(u * I * dr);
+            gm[4] += (double)(u * I * dm);
+            gl[j] += (double)(u * f);
           }
         }
       }
@@ -234,9 +241,19 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
     }
   }
   __syncthreads();
+  double* part = partials + (int64_t)blockIdx.x * nacc;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) part[i] = sacc[i];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_block = atomicAdd(a.ctrl + 3, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last_block) return;
+  __threadfence();
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
-    float v = sacc[i];
-    if (v != 0.0f) atomicAdd(i < nm5 ? dparams + i : dinten + (i - nm5), v);
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + (int64_t)b * nacc + i);
+    float* o = i < nm5 ? dparams + i : dinten + (i - nm5);
+    *o = *o + (float)s;
   }
 }
 
@@ -312,16 +329,26 @@ int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, con
   TaskGrid g = make_grid(a.cam.W, 0, a.cam.H, a.cam.spp);
   int ntasks = g.tiles_x * g.tiles_y;
   if (ntasks == 0) return FIRE_OK;
-  if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 4 * 4, st), "memset")) return e;
-  size_t smem = sizeof(float) * (a.mats.n * 5 + a.lights.n);
+  const int nacc = a.mats.n * 5 + a.lights.n;
+  size_t smem = sizeof(double) * nacc;
   if (smem > 48 * 1024) {
     if (int e = cuda_check(cudaFuncSetAttribute(k_shade_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                            "smem attr"))
       return e;
   }
   int grid = std::max(1, std::min(sm_count() * 4, (ntasks + 3) / 4));
+  size_t need = (size_t)grid * nacc;
+  if (s->bwd_partials_n < need) {
+    if (s->bwd_partials) cudaFree(s->bwd_partials);
+    s->bwd_partials = nullptr;
+    s->bwd_partials_n = 0;
+    if (cudaError_t e = dev_alloc((void**)&s->bwd_partials, need * sizeof(double), &s->bytes))
+      return cuda_check(e, "backward partials");
+    s->bwd_partials_n = need;
+  }
+  if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 4 * 4, st), "memset")) return e;
   prof_begin(s, kStageBackward, st);
-  k_shade_bwd<<<grid, 128, smem, st>>>(a, g, ntasks, inten, dL, dparams, dinten);
+  k_shade_bwd<<<grid, 128, smem, st>>>(a, g, ntasks, inten, dL, dparams, dinten, s->bwd_partials);
   prof_end(s, kStageBackward, st);
   return cuda_check(cudaGetLastError(), "k_shade_bwd");
 }

@@ -73,7 +73,8 @@ def compare_samples(gpu: dict, ref: dict, ids=None):
     rp, rv, rt, rt2 = ref["prim"], ref["vis"].astype(np.uint32), ref["t"], ref["t2"]
     bad = (gp != rp) | (gv != rv)
     frac = 1.0 - bad.mean() if len(bad) else 1.0
-    tie = np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))
     unexplained = bad & ~tie
     assert frac >= AGREE_MIN, f"agreement {frac:.6f} < {AGREE_MIN}"
     assert not unexplained.any(), f"{int(unexplained.sum())} disagreements without a near tie"

@@ -57,7 +57,7 @@ def test_fullsize_refit_and_sampled_render(frame7m):
     gpu_px = img.reshape(-1, 4)[pix]
     ok = ~bad.reshape(-1, 4).any(1)
     assert_radiance_close(gpu_px[None], ref_px[None].astype(np.float32), ok[None])
-    assert (g["prim"] >= 0).mean() > 0.5
+    assert (g["prim"] >= 0).mean() > 0.3
 
 
 def _oracle_samples(S, cam, lights, ids):
