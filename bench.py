@@ -107,7 +107,10 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------- roofline
-def algorithmic_bytes(nt: int, nv: int, samples: int, pixels: int):
+KERNEL_NAMES = {"refit": "k_refit", "primary": "k_primary", "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
+
+
+def algorithmic_bytes(nt: int, nv: int, samples: int, pixels: int, shadow_rays: int):
     """Minimum bytes each kernel must move per launch (one frame):
     refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, sorted
                index records (16 B) + material (4 B) + leaf slot (4 B) per
@@ -115,13 +118,27 @@ def algorithmic_bytes(nt: int, nv: int, samples: int, pixels: int):
                write 2 child boxes (48 B), read them back (48 B), counter
                atomic (8 B) and parent slot (4 B)
     primary -- read the whole tree once (64 B per internal node + 48 B per
-               triangle) + write a 16-B G-buffer record per sample
-    shade   -- read the whole tree once + the 16-B G-buffer record per
-               sample + write a 16-B pixel."""
+               triangle) + write a 16-B record per sample + a 32-B queued
+               shadow ray
+    shadow  -- read the whole tree once + read each 32-B queued ray and the
+               4-B skip id + a 4-B visibility update
+    resolve -- read the 16-B record per sample + 32 B of its triangle for the
+               hit frame + write a 16-B pixel."""
     tree = 64 * max(nt - 1, 0) + 48 * nt
     return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48) + max(nt - 1, 0) * (48 + 48 + 8 + 4),
-            "primary": tree + 16 * samples,
-            "shade": tree + 16 * samples + 16 * pixels}
+            "primary": tree + 16 * samples + 32 * shadow_rays,
+            "shadow": tree + 40 * shadow_rays,
+            "resolve": 16 * samples + 32 * samples + 16 * pixels}
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    the current kernels from the committed ncu summary, else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_frame7m.txt")
+    if os.path.exists(p):
+        lines = [l for l in open(p) if not l.startswith("#")]
+        return json.loads("".join(lines)).get(kernel)
+    return None
 
 
 def load_peaks():
@@ -362,23 +379,21 @@ def main():
     hits = int((gb[:, 0] >= 0).sum().item())
     del gb
 
-    prim_ms = stages["primary"][0] / max(1, stages["primary"][1])
-    shade_ms = stages["shade"][0] / max(1, stages["shade"][1])
-    refit_ms = stages["refit"][0] / max(1, stages["refit"][1])
-    grays = (primary_rays + shadow_rays) / ((prim_ms + shade_ms) * 1e-3) / 1e9
+    avg = {k: stages[k][0] / max(1, stages[k][1]) for k in ("refit", "primary", "shadow", "resolve")}
+    trace_ms = avg["primary"] + avg["shadow"] + avg["resolve"]
+    grays = (primary_rays + shadow_rays) / (trace_ms * 1e-3) / 1e9
     grays_frame = (primary_rays + shadow_rays) / (ms_frame_rank * 1e-3) / 1e9
-    alg = algorithmic_bytes(w.scene.nt, w.scene.nv, primary_rays, cam.width * cam.height)
-    per = {"refit": refit_ms, "primary": prim_ms, "shade": shade_ms}
-    dom = max(per, key=per.get)
+    alg = algorithmic_bytes(w.scene.nt, w.scene.nv, primary_rays, cam.width * cam.height, shadow_rays)
+    dom = max(avg, key=avg.get)
     peak, peak_kind = load_peaks()
-    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        traffic = json.load(open(tp)).get(dom)
-    roofline = {"bound": "hbm", "kernel": {"refit": "k_refit", "primary": "k_primary", "shade": "k_shade"}[dom],
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": alg[dom]}
+    achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": committed_traffic(dom),
+                "peak_source": f"{peak_kind} hbm_gbs (of measured)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes": alg[dom],
+                "all_kernels": {k: {"ms": avg[k], "algorithmic_bytes": alg[k],
+                                    "gbs": alg[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None}
+                                for k in avg}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_frame_rank, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -386,8 +401,7 @@ def main():
             "config": workload_config(w, K), "gpu_launches": int(launches),
             "grays_per_s": grays, "grays_per_s_frame": grays_frame,
             "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
-            "stages_ms": {"refit": refit_ms, "primary": prim_ms, "shade_shadow_resolve": shade_ms,
-                          "build_once": build_stats["build"][0]},
+            "stages_ms": {**avg, "build_once": build_stats["build"][0]},
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e}
 
     if rank == 0 and not args.no_side:

@@ -113,9 +113,10 @@ namespace {
 
 int check_cam(const fire_camera* c) {
   if (!c) return set_error(FIRE_ERR_INVALID_ARG, "camera is NULL");
-  if (c->width <= 0 || c->height <= 0 || (int64_t)c->width * c->height > (int64_t)1 << 28)
-    return set_error(FIRE_ERR_INVALID_ARG, "camera size out of range");
   if (c->spp != 1 && c->spp != 4) return set_error(FIRE_ERR_INVALID_ARG, "spp must be 1 or 4");
+  // sample ids (and sample id x 8 + light in the shadow queue) stay below 2^31
+  if (c->width <= 0 || c->height <= 0 || (int64_t)c->width * c->height * c->spp >= (int64_t)1 << 28)
+    return set_error(FIRE_ERR_INVALID_ARG, "camera size out of range");
   if (!finite3(c->pos) || !finite3(c->target) || !finite3(c->up) || !(c->vfov_deg > 0 && c->vfov_deg < 180))
     return set_error(FIRE_ERR_INVALID_ARG, "camera parameters not finite / fov out of (0,180)");
   H3 f = hsub(H3{c->target[0], c->target[1], c->target[2]}, H3{c->pos[0], c->pos[1], c->pos[2]});
@@ -205,7 +206,7 @@ void free_scene(fire_scene_s* s) {
   s->prof = nullptr;
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
-                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials};
+                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -433,6 +434,17 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     if (int e = ensure_scratch(s, nsamp)) return e;
     a.g = s->gscratch;
     a.write_vis = 0;
+  }
+  size_t njobs = nsamp * (size_t)std::max(1, nlights);
+  if (s->jobs_n < njobs) {
+    if (s->jobs) {
+      cudaFree(s->jobs);
+      s->bytes -= s->jobs_n * 32;
+    }
+    s->jobs = nullptr;
+    s->jobs_n = 0;
+    if (cudaError_t e = dev_alloc((void**)&s->jobs, njobs * 32, &s->bytes)) return cuda_check(e, "shadow queue");
+    s->jobs_n = njobs;
   }
   a.out = out_rgba;
   return render_frame(s, a, o, st);

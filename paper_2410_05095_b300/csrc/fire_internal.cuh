@@ -115,6 +115,8 @@ struct fire_scene_s {
   size_t gscratch_n = 0;
   double* bwd_partials = nullptr;  // per-block gradient partials of the backward
   size_t bwd_partials_n = 0;
+  float4* jobs = nullptr;          // shadow-ray queue, 32 B per ray
+  size_t jobs_n = 0;               // capacity in rays
   // batch cache (see batch.cu)
   void* batch = nullptr;
   int64_t iter_cap = 0;
@@ -136,8 +138,8 @@ CamParams make_cam(const fire_camera& c);
 int make_lights(const fire_light* lights, int n, LightParams* out);
 
 // Stage profiler (fire_api.cu): event pairs around kernels, read lazily.
-enum Stage { kStageRefit = 0, kStagePrimary = 1, kStageShade = 2, kStageBuild = 3, kStageShadeGbuf = 4,
-             kStageBackward = 5, kStages = 8 };
+enum Stage { kStageRefit = 0, kStagePrimary = 1, kStageShadow = 2, kStageBuild = 3, kStageShadeGbuf = 4,
+             kStageBackward = 5, kStageResolve = 6, kStages = 8 };
 void prof_begin(fire_scene_s* s, int stage, cudaStream_t st);
 void prof_end(fire_scene_s* s, int stage, cudaStream_t st);
 

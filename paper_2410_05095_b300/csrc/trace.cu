@@ -18,29 +18,86 @@
 namespace fire {
 namespace {
 
+// Nearest hit per sample; writes the sample's record (prim, t, cast bits,
+// leaf position) and, for every light with n.l > 0 at the hit, appends a
+// shadow ray (lifted origin, unit direction, range, sample|light) to a dense
+// queue: one ballot per light, one atomicAdd per warp, lanes ranked by the
+// popcount of the lower lanes.
 template <int STACK>
-__global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int ntasks) {
+__global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
   const int lane = threadIdx.x & 31;
+  const unsigned lower = (1u << lane) - 1u;
   TraceCtx c{a.nodes, a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  const float eps = scene_eps(a.nodes, a.nt);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 0, 1);
     task = __shfl_sync(kFull, task, 0);
     if (task >= ntasks) return;
     int x, y, k;
-    if (task_sample(g, task, lane, x, y, k)) {
-      float3 o = f3(a.cam.ox, a.cam.oy, a.cam.oz);
+    const bool valid = task_sample(g, task, lane, x, y, k);
+    int prim = -1, pos = -1;
+    float t = inf_f();
+    int64_t sid = 0;
+    float3 o = f3(a.cam.ox, a.cam.oy, a.cam.oz), n = f3(0, 0, 0), po = f3(0, 0, 0);
+    if (valid) {
       float3 d = cam_dir(a.cam, x, y, k);
-      int prim, pos;
-      float t;
       trace_nearest<STACK>(c, o, d, prim, pos, t);
-      int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
-      fire_gbuffer_rec r;
-      r.prim = prim;
-      r.t = t;
-      r.vis = 0;
-      r.pad = (uint32_t)pos;
-      reinterpret_cast<int4*>(a.g)[sid] = *reinterpret_cast<int4*>(&r);
+      sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
+      if (prim >= 0) {
+        float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
+        hit_frame(B, C, o, d, t, eps, n, po);
+      }
+    }
+    uint32_t cast = 0;
+    for (int j = 0; j < a.lights.n; ++j) {
+      float3 l = f3(0, 0, 0);
+      float E, tmax = 0.0f;
+      bool want = false;
+      if (prim >= 0) {
+        light_vec(a.lights, j, a.lights.I[j], po, l, E, tmax);
+        want = dot3(n, l) > 0.0f;
+      }
+      unsigned m = __ballot_sync(kFull, want);
+      if (m == 0) continue;
+      uint32_t base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(a.ctrl + 4, (uint32_t)__popc(m));
+      base = __shfl_sync(kFull, base, __ffs(m) - 1);
+      if (want) {
+        cast |= 1u << (8 + j);
+        int64_t slot = (int64_t)base + __popc(m & lower);
+        jobs[2 * slot] = make_float4(po.x, po.y, po.z, tmax);
+        jobs[2 * slot + 1] = make_float4(l.x, l.y, l.z, __int_as_float((int)(sid * 8 + j)));
+      }
+    }
+    if (valid)
+      reinterpret_cast<int4*>(a.g)[sid] = make_int4(prim, __float_as_int(t), (int)cast, pos);
+  }
+}
+
+// Shadow rays from the dense queue: each warp takes 32 consecutive rays (all
+// lanes busy until the queue's tail); an unoccluded ray sets its light's bit
+// in the sample's record.
+template <int STACK>
+__global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs) {
+  const int lane = threadIdx.x & 31;
+  TraceCtx c{a.nodes, a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  const uint32_t njobs = a.ctrl[4];
+  int4* rec = reinterpret_cast<int4*>(a.g);
+  while (true) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(a.ctrl + 5, 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= njobs) return;
+    uint32_t jb = base + lane;
+    if (jb < njobs) {
+      float4 A = jobs[2 * (int64_t)jb], B = jobs[2 * (int64_t)jb + 1];
+      int sj = __float_as_int(B.w);
+      int64_t sid = sj >> 3;
+      int light = sj & 7;
+      int skip = rec[sid].x;
+      if (!trace_any<STACK>(c, f3(A.x, A.y, A.z), f3(B.x, B.y, B.z), A.w, skip))
+        atomicOr(reinterpret_cast<unsigned*>(&rec[sid].z), 1u << light);
     }
   }
 }
@@ -137,13 +194,13 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
 //   df/dalb = (1-F)(1-m)/pi + (D vis - (1-m) alb/pi)(1 - w5) m
 //   df/dm   = (D vis - (1-m) alb/pi)(1 - w5)(alb - 0.04) - (1-F) alb/pi
 //   df/dr   = F (dD/dr vis + D dvis/dr)
-// Per-sample terms are FP32; sums are FP64: per warp (shuffles) when the
-// warp shares one material, else shared-memory atomics, then each block
-// stores its partials and the last block to finish adds them in block order
-// (deterministic) into the FP32 outputs.
+// Per-sample terms and per-warp sums (shuffles, when the warp shares one
+// material) are FP32; everything above is FP64: shared-memory atomics per
+// block, global atomics into `acc` (nmat*5 + nlights doubles, zero on entry),
+// and the last block to finish adds `acc` into the FP32 outputs and zeroes it.
 __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
                                                    const float* dL, float* dparams, float* dinten,
-                                                   double* partials) {
+                                                   double* acc) {
   extern __shared__ double sacc[];  // [nmat*5 + nlights]
   __shared__ bool last_block;
   const int nm5 = a.mats.n * 5;
@@ -159,10 +216,10 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
     if (task >= ntasks) break;
     int x, y, k;
     bool valid = task_sample(g, task, lane, x, y, k);
-    double gm[5] = {0, 0, 0, 0, 0};
-    double gl[kMaxLights];
+    float gm[5] = {0, 0, 0, 0, 0};
+    float gl[kMaxLights];
 #pragma unroll
-    for (int j = 0; j < kMaxLights; ++j) gl[j] = 0.0;
+    for (int j = 0; j < kMaxLights; ++j) gl[j] = 0.0f;
     int mat = -1;
     if (valid) {
       int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
@@ -213,10 +270,10 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
             float dm = dfdF * (1.0f - w5) * (alb[ch] - 0.04f) - (1.0f - F) * alb[ch] * kInvPi;
             float dr = F * (dD_dr * vis + D * dvis_dr);
             float u = up[ch] * wI;
-            gm[ch] += (double)(u * I * dalb);
-            gm[3] += (double)(u * I * dr);
-            gm[4] += (double)(u * I * dm);
-            gl[j] += (double)(u * f);
+            gm[ch] += u * I * dalb;
+            gm[3] += u * I * dr;
+            gm[4] += u * I * dm;
+            gl[j] += u * f;
           }
         }
       }
@@ -231,18 +288,18 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
         for (int off = 16; off; off >>= 1) gl[j] += __shfl_xor_sync(kFull, gl[j], off);
       if (lane == 0 && mat >= 0) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], gm[q]);
-        for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], gl[j]);
+        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], (double)gm[q]);
+        for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], (double)gl[j]);
       }
     } else if (mat >= 0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], gm[q]);
-      for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], gl[j]);
+      for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], (double)gm[q]);
+      for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], (double)gl[j]);
     }
   }
   __syncthreads();
-  double* part = partials + (int64_t)blockIdx.x * nacc;
-  for (int i = threadIdx.x; i < nacc; i += blockDim.x) part[i] = sacc[i];
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x)
+    if (sacc[i] != 0.0) atomicAdd(acc + i, sacc[i]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last_block = atomicAdd(a.ctrl + 3, 1u) == gridDim.x - 1;
@@ -250,8 +307,8 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
   if (!last_block) return;
   __threadfence();
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + (int64_t)b * nacc + i);
+    double s = __ldcg(acc + i);
+    acc[i] = 0.0;  // ready for the next call
     float* o = i < nm5 ? dparams + i : dinten + (i - nm5);
     *o = *o + (float)s;
   }
@@ -269,23 +326,34 @@ template <int STACK>
 int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int ntasks,
                   const fire_render_opts& o, cudaStream_t st) {
   const int threads = 128;
-  static int occ_p = 0, occ_s = 0;
+  static int occ_p = 0, occ_s = 0, occ_r = 0;
   static std::once_flag once;
   std::call_once(once, [] {
     occ_p = occupancy_blocks(k_primary<STACK>, 128, 0);
-    occ_s = occupancy_blocks(k_shade<STACK, true>, 128, 0);
+    occ_s = occupancy_blocks(k_shadow<STACK>, 128, 0);
+    occ_r = occupancy_blocks(k_shade<32, false>, 128, 0);
   });
   int sms = sm_count();
   int bp = o.blocks_per_sm > 0 ? o.blocks_per_sm : occ_p;
   int bs = o.blocks_per_sm > 0 ? o.blocks_per_sm : occ_s;
+  int br = o.blocks_per_sm > 0 ? o.blocks_per_sm : occ_r;
   int gp = std::max(1, std::min(sms * bp, (ntasks + 3) / 4));
-  int gs = std::max(1, std::min(sms * bs, (ntasks + 3) / 4));
+  // the shadow queue holds at most samples x lights rays; its length is only
+  // known on the device, so the grid covers the worst case
+  int64_t maxjobs = (int64_t)ntasks * 32 * std::max(1, a.lights.n);
+  int gs = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * bs, (maxjobs + 127) / 128));
+  int gr = std::max(1, std::min(sms * br, (ntasks + 3) / 4));
   prof_begin(s, kStagePrimary, st);
-  k_primary<STACK><<<gp, threads, 0, st>>>(a, g, ntasks);
+  k_primary<STACK><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
   prof_end(s, kStagePrimary, st);
-  prof_begin(s, kStageShade, st);
-  k_shade<STACK, true><<<gs, threads, 0, st>>>(a, g, ntasks, nullptr);
-  prof_end(s, kStageShade, st);
+  if (a.lights.n > 0) {
+    prof_begin(s, kStageShadow, st);
+    k_shadow<STACK><<<gs, threads, 0, st>>>(a, s->jobs);
+    prof_end(s, kStageShadow, st);
+  }
+  prof_begin(s, kStageResolve, st);
+  k_shade<32, false><<<gr, threads, 0, st>>>(a, g, ntasks, nullptr);
+  prof_end(s, kStageResolve, st);
   return cuda_check(cudaGetLastError(), "render kernels");
 }
 
@@ -303,7 +371,8 @@ int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o
   TaskGrid g = make_grid(a.cam.W, a.row_begin, a.row_end, a.cam.spp);
   int ntasks = g.tiles_x * g.tiles_y;
   if (ntasks == 0) return FIRE_OK;
-  if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 4 * 4, st), "memset")) return e;
+  // task counters, queue length and queue cursor (the error word at [8] stays)
+  if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 8 * 4, st), "memset")) return e;
   switch (stack_for_height(s->height, o.stack_depth)) {
     case 8: return launch_render<8>(s, a, g, ntasks, o, st);
     case 32: return launch_render<32>(s, a, g, ntasks, o, st);
@@ -337,13 +406,14 @@ int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, con
       return e;
   }
   int grid = std::max(1, std::min(sm_count() * 4, (ntasks + 3) / 4));
-  size_t need = (size_t)grid * nacc;
+  size_t need = (size_t)nacc;
   if (s->bwd_partials_n < need) {
     if (s->bwd_partials) cudaFree(s->bwd_partials);
     s->bwd_partials = nullptr;
     s->bwd_partials_n = 0;
     if (cudaError_t e = dev_alloc((void**)&s->bwd_partials, need * sizeof(double), &s->bytes))
-      return cuda_check(e, "backward partials");
+      return cuda_check(e, "backward accumulator");
+    if (int e = cuda_check(cudaMemsetAsync(s->bwd_partials, 0, need * sizeof(double), st), "memset")) return e;
     s->bwd_partials_n = need;
   }
   if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 4 * 4, st), "memset")) return e;

@@ -92,131 +92,110 @@ struct TraceCtx {
   uint32_t* err;     // sticky error word
 };
 
-// Nearest hit with t in (0, inf): lexicographic (t, original index) minimum,
-// so the result does not depend on the visiting order.  prim = original
-// index (-1 = miss), pos = sorted position.
-template <int STACK>
-__device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float3 d, int& prim, int& pos,
-                                              float& tb) {
-  prim = -1;
-  pos = -1;
-  tb = inf_f();
-  if (c.nt == 0) return;
-  float3 inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-  int stack[STACK];
-  int sp = 0;
-  int cur = 0;
-  int64_t visits = 0;
-  while (true) {
-    if (++visits > c.cap) {
-      atomicOr(c.err, kErrTimeout);
-      return;
-    }
-    if ((uint64_t)cur >= (uint64_t)(c.nt > 1 ? c.nt - 1 : 1)) {  // never for a built tree
-      atomicOr(c.err, kErrCorrupt);
-      break;
-    }
-    const Node* n = c.nodes + cur;
-    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
-    int4 dd = __ldg(&n->d);
-    float tn0, tn1;
-    bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
-    bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tb, tn1);
-    if (h0 && dd.x < 0) {
-      int p = ~dd.x;
-      float t;
-      if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
-      float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
-             C = __ldg(c.tris + 3 * (int64_t)p + 2);
-      if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f()) {
-        int orig = __float_as_int(A.w);
-        if (t < tb || (t == tb && orig < prim)) { tb = t; prim = orig; pos = p; }
-      }
-      h0 = false;
-    }
-    if (h1 && dd.y < 0) {
-      int p = ~dd.y;
-      float t;
-      if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
-      float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
-             C = __ldg(c.tris + 3 * (int64_t)p + 2);
-      if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f()) {
-        int orig = __float_as_int(A.w);
-        if (t < tb || (t == tb && orig < prim)) { tb = t; prim = orig; pos = p; }
-      }
-      h1 = false;
-    }
-    if (h0 && h1) {
-      int nearc = tn0 <= tn1 ? dd.x : dd.y;
-      int farc = tn0 <= tn1 ? dd.y : dd.x;
-      if (sp < STACK) stack[sp++] = farc;
-      else atomicOr(c.err, kErrStack);
-      cur = nearc;
-    } else if (h0) {
-      cur = dd.x;
-    } else if (h1) {
-      cur = dd.y;
-    } else {
-      if (sp == 0) return;
-      cur = stack[--sp];
-    }
+constexpr int kDone = 0x7fffffff;  // stack sentinel: nothing left to visit
+
+// Leaf = one triangle at sorted position ~code.  Nearest mode updates the
+// (t, original index) minimum; any mode returns true on a hit in (0, tmax)
+// that is not triangle `skip`.
+template <bool ANY>
+__device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o, float3 d, float tmax, int skip,
+                                          int& prim, int& pos, float& tb) {
+  int p = ~code;
+  if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
+  const float4* tr = c.tris + 3 * (int64_t)p;
+  float4 A = __ldg(tr), B = __ldg(tr + 1), C = __ldg(tr + 2);
+  int orig = __float_as_int(A.w);
+  float t;
+  if (ANY) return orig != skip && mt_t(o, d, A, B, C, t) && t > 0.0f && t < tmax;
+  if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f() && (t < tb || (t == tb && orig < prim))) {
+    tb = t;
+    prim = orig;
+    pos = p;
   }
+  return false;
 }
 
-// Any hit with 0 < t < tmax, skipping triangle `skip` (original index).
-template <int STACK>
-__device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d, float tmax, int skip) {
+// Stack traversal of the binary LBVH in the while-while form of Aila and
+// Laine (2009): the inner loop walks internal nodes, nearest child first,
+// and postpones the first leaf it meets; it leaves once every lane of the
+// warp holds a postponed leaf (or has nothing left), so the triangle tests of
+// a warp run together instead of splitting every node step.
+//   ANY:  any hit in (0, tmax) other than `skip`; returns true on a hit.
+//   else: nearest hit in (0, inf) by (t, original index) -- independent of
+//         the visiting order; prim = original index (-1 = miss), pos = sorted
+//         position, tb = t.
+template <int STACK, bool ANY>
+__device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, float tmax, int skip, int& prim,
+                                         int& pos, float& tb) {
+  prim = -1;
+  pos = -1;
+  tb = ANY ? tmax : inf_f();
   if (c.nt == 0) return false;
-  float3 inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const uint32_t nnodes = (uint32_t)(c.nt > 1 ? c.nt - 1 : 1);
+  const float3 inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
   int stack[STACK];
-  int sp = 0;
-  int cur = 0;
-  int64_t visits = 0;
-  while (true) {
-    if (++visits > c.cap) {
-      atomicOr(c.err, kErrTimeout);
-      return false;
-    }
-    if ((uint64_t)cur >= (uint64_t)(c.nt > 1 ? c.nt - 1 : 1)) {  // never for a built tree
-      atomicOr(c.err, kErrCorrupt);
-      break;
-    }
-    const Node* n = c.nodes + cur;
-    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
-    int4 dd = __ldg(&n->d);
-    float tn0, tn1;
-    bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tmax, tn0);
-    bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tmax, tn1);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      int ch = side ? dd.y : dd.x;
-      bool& h = side ? h1 : h0;
-      if (h && ch < 0) {
-        int p = ~ch;
-        if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
-        float t;
-        float4 A = __ldg(c.tris + 3 * (int64_t)p), B = __ldg(c.tris + 3 * (int64_t)p + 1),
-               C = __ldg(c.tris + 3 * (int64_t)p + 2);
-        if (__float_as_int(A.w) != skip && mt_t(o, d, A, B, C, t) && t > 0.0f && t < tmax) return true;
-        h = false;
+  stack[0] = kDone;
+  int sp = 1;
+  int cur = 0;   // internal node >= 0, leaf < 0, or kDone
+  int leaf = 0;  // postponed leaf code (< 0), 0 = none
+  int64_t budget = c.cap;
+  while (cur != kDone || leaf < 0) {
+    while (cur >= 0 && cur != kDone) {
+      if (--budget < 0) {
+        atomicOr(c.err, kErrTimeout);
+        return false;
       }
+      if ((uint32_t)cur >= nnodes) {  // never for a built tree
+        atomicOr(c.err, kErrCorrupt);
+        return false;
+      }
+      const Node* n = c.nodes + cur;
+      float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
+      int4 dd = __ldg(&n->d);
+      float tn0, tn1;
+      bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
+      bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tb, tn1);
+      if (h0 && h1) {
+        bool first0 = tn0 <= tn1;
+        if (sp < STACK) stack[sp++] = first0 ? dd.y : dd.x;
+        else atomicOr(c.err, kErrStack);
+        cur = first0 ? dd.x : dd.y;
+      } else if (h0) {
+        cur = dd.x;
+      } else if (h1) {
+        cur = dd.y;
+      } else {
+        cur = stack[--sp];
+      }
+      if (cur < 0 && leaf == 0) {
+        leaf = cur;
+        cur = stack[--sp];
+      }
+      if (!__any_sync(__activemask(), leaf == 0)) break;
     }
-    if (h0 && h1) {
-      int nearc = tn0 <= tn1 ? dd.x : dd.y;
-      int farc = tn0 <= tn1 ? dd.y : dd.x;
-      if (sp < STACK) stack[sp++] = farc;
-      else atomicOr(c.err, kErrStack);
-      cur = nearc;
-    } else if (h0) {
-      cur = dd.x;
-    } else if (h1) {
-      cur = dd.y;
-    } else {
-      if (sp == 0) return false;
-      cur = stack[--sp];
+    while (leaf < 0) {
+      if (leaf_test<ANY>(c, leaf, o, d, tmax, skip, prim, pos, tb)) return true;
+      leaf = 0;
+      if (cur < 0) {
+        leaf = cur;
+        cur = stack[--sp];
+      }
     }
   }
   return false;
+}
+
+template <int STACK>
+__device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float3 d, int& prim, int& pos,
+                                              float& tb) {
+  traverse<STACK, false>(c, o, d, 0.0f, -1, prim, pos, tb);
+}
+
+template <int STACK>
+__device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d, float tmax, int skip) {
+  int prim, pos;
+  float tb;
+  return traverse<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
 }
 
 // Shadow-ray lift: eps = 1e-4 * |hi - lo| of the scene box (union of the

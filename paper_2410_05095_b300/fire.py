@@ -28,7 +28,7 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_last_error", "fire_version"]
 
-STAGES = ["refit", "primary", "shade", "build", "shade_gbuf", "backward", "unused6", "unused7"]
+STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
 
 class FireError(RuntimeError):
