@@ -368,7 +368,22 @@ def main():
     t_e2e = max_over_ranks(t_e2e, device="cuda")
     G.profile_read()
     e2e = {"value": t_e2e / (K * world), "unit": UNIT, "h2d_bytes_per_step": int(frames[0].nbytes),
-           "d2h_bytes_per_step": int(host_img.numel() * 4)}
+           "d2h_bytes_per_step": int(host_img.numel() * 4), "host_pinned": bool(host_img.is_pinned())}
+    # where the end-to-end time goes (a separate, untimed pass of 3 frames)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    parts = np.zeros(3)
+    for i in range(3):
+        ev[0].record(stream)
+        G.refit(xf_pinned[W + i].numpy())
+        ev[1].record(stream)
+        G.render(cam, lights, out=out)
+        ev[2].record(stream)
+        host_img.copy_(out, non_blocking=True)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        parts += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    e2e["breakdown_ms"] = dict(zip(["refit_from_host", "render", "d2h_image"], (parts / 3).tolist()))
+    G.profile_read()
 
     # --- rays traced per frame (shadow rays counted from the G-buffer) ------------
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")

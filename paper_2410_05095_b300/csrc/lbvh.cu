@@ -51,26 +51,29 @@ __global__ void k_validate(const float4* __restrict__ rest, int64_t nv, const ui
 // Build step 1: transform, triangle boxes, centroids, exact centroid bounds.
 // centroid c = 0.5 * (min + max) per axis.
 // ----------------------------------------------------------------------------
-__global__ void k_centroids(const float4* __restrict__ rest, const uint32_t* __restrict__ idx,
-                            const uint16_t* __restrict__ vb, const float* __restrict__ xf, int64_t nt,
-                            float4* __restrict__ cen, uint32_t* __restrict__ bounds) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float3 c = f3(__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000));
-  float3 cmax = f3(-c.x, -c.y, -c.z);
-  float3 cmin = c;
-  if (i < nt) {
+// Grid-stride over triangles; min/max are reduced per thread, per warp
+// (shuffles) and per block (shared memory) before one set of atomics per
+// block on the ordered-integer images (exact, order-independent).
+__global__ void __launch_bounds__(256) k_centroids(const float4* __restrict__ rest, const uint32_t* __restrict__ idx,
+                                                   const uint16_t* __restrict__ vb, const float* __restrict__ xf,
+                                                   int64_t nt, float4* __restrict__ cen, uint32_t* __restrict__ bounds) {
+  __shared__ uint32_t red[8][6];
+  uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t a = idx[3 * i], b = idx[3 * i + 1], d = idx[3 * i + 2];
     float3 w0 = xform(xf + 12 * vb[a], rest[a]);
     float3 w1 = xform(xf + 12 * vb[b], rest[b]);
     float3 w2 = xform(xf + 12 * vb[d], rest[d]);
     float3 mn = fmin3(w0, fmin3(w1, w2)), mx = fmax3(w0, fmax3(w1, w2));
-    c = f3(0.5f * (mn.x + mx.x), 0.5f * (mn.y + mx.y), 0.5f * (mn.z + mx.z));
+    float3 c = f3(0.5f * (mn.x + mx.x), 0.5f * (mn.y + mx.y), 0.5f * (mn.z + mx.z));
     cen[i] = make_float4(c.x, c.y, c.z, 0.0f);
-    cmin = c;
-    cmax = c;
+    uint32_t o[3] = {f2ord(c.x), f2ord(c.y), f2ord(c.z)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], o[k]);
+      hi[k] = max(hi[k], o[k]);
+    }
   }
-  uint32_t lo[3] = {f2ord(cmin.x), f2ord(cmin.y), f2ord(cmin.z)};
-  uint32_t hi[3] = {f2ord(cmax.x), f2ord(cmax.y), f2ord(cmax.z)};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     for (int off = 16; off; off >>= 1) {
@@ -78,12 +81,21 @@ __global__ void k_centroids(const float4* __restrict__ rest, const uint32_t* __r
       hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
     }
   }
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      atomicMin(bounds + k, lo[k]);
-      atomicMax(bounds + 3 + k, hi[k]);
+      red[w][k] = lo[k];
+      red[w][3 + k] = hi[k];
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    uint32_t v = red[0][k];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? min(v, red[q][k]) : max(v, red[q][k]);
+    if (k < 3) atomicMin(bounds + k, v);
+    else atomicMax(bounds + k, v);
   }
 }
 
@@ -341,35 +353,73 @@ __global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restr
                         const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
                         Node* nodes, const int32_t* __restrict__ leaf_slot,
                         const int32_t* __restrict__ node_slot, uint32_t* counters) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nt) return;
-  uint4 id = sidx[i];
-  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
-  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
-  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
-  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
-  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
-  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
-  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
-  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool valid = i < nt;
+  float3 lo = f3(0, 0, 0), hi = f3(0, 0, 0);
+  int32_t slot = -1;
+  if (valid) {
+    uint4 id = sidx[i];
+    float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
+    float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
+    float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
+    float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
+    tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
+    tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
+    tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+    lo = fmin3(w0, fmin3(w1, w2));
+    hi = fmax3(w0, fmax3(w1, w2));
+    slot = nt > 1 ? leaf_slot[i] : 0;
+  }
   if (nt == 1) {  // single leaf: node 0 holds it on both sides
-    store_box(nodes, 0, lo, hi);
-    store_box(nodes, 1, lo, hi);
-    if (HEIGHT) nodes[0].d = make_int4(~0, ~0, 0, 0);
+    if (valid) {
+      store_box(nodes, 0, lo, hi);
+      store_box(nodes, 1, lo, hi);
+      if (HEIGHT) nodes[0].d = make_int4(~0, ~0, 0, 0);
+    }
     return;
   }
-  int32_t slot = leaf_slot[i];
+  // Two sibling leaves in neighbouring lanes (leaf i on side 0, leaf i+1 on
+  // side 1 of the same node) finish their node inside the warp: the side-0
+  // lane stores both boxes and climbs on; that node's counter is never used
+  // (the same pairs occur in every refit of the topology).
+  const int32_t s_next = __shfl_down_sync(0xffffffffu, slot, 1);
+  const int32_t s_prev = __shfl_up_sync(0xffffffffu, slot, 1);
+  const float3 nlo = f3(__shfl_down_sync(0xffffffffu, lo.x, 1), __shfl_down_sync(0xffffffffu, lo.y, 1),
+                        __shfl_down_sync(0xffffffffu, lo.z, 1));
+  const float3 nhi = f3(__shfl_down_sync(0xffffffffu, hi.x, 1), __shfl_down_sync(0xffffffffu, hi.y, 1),
+                        __shfl_down_sync(0xffffffffu, hi.z, 1));
+  if (!valid) return;
+  const bool pair_lo = slot >= 0 && (slot & 1) == 0 && lane < 31 && i + 1 < nt && s_next == slot + 1;
+  const bool pair_hi = slot >= 0 && (slot & 1) == 1 && lane > 0 && s_prev == slot - 1;
+  if (pair_hi) return;
   int h = 0;
+  if (pair_lo) {
+    if ((slot >> 1) >= nt - 1) return;  // never for a complete topology
+    Node* node = nodes + (slot >> 1);
+    store_box(node, 0, lo, hi);
+    store_box(node, 1, nlo, nhi);
+    if (HEIGHT) {
+      reinterpret_cast<int*>(&node->d)[2] = 0;
+      reinterpret_cast<int*>(&node->d)[3] = 0;
+    }
+    lo = fmin3(lo, nlo);
+    hi = fmax3(hi, nhi);
+    h = 1;
+    slot = node_slot[slot >> 1];
+    if (slot < 0) return;  // the pair was the root
+  }
   while (true) {
     if (slot < 0 || (slot >> 1) >= nt - 1) return;  // never for a complete topology
     int32_t p = slot >> 1;
     Node* node = nodes + p;
     store_box(node, slot & 1, lo, hi);
     if (HEIGHT) reinterpret_cast<int*>(&node->d)[2 + (slot & 1)] = h;
-    __threadfence();
+    // release the box to the sibling's thread / acquire the sibling's box
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     uint32_t old = atomicAdd(counters + p, 1u);
     if ((old & 1u) == 0) return;  // first arrival: the sibling finishes this node
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     float4 a = __ldcg(&node->a), b = __ldcg(&node->b), c = __ldcg(&node->c);
     lo = f3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
     hi = f3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
@@ -409,7 +459,8 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   if (int e = cuda_check(cudaMemcpyAsync(s->ctrl + 9, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
   uint32_t* bounds = s->ctrl + 9;
   prof_begin(s, kStageBuild, st);
-  k_centroids<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->idx, s->vbody, s->xf, T, s->cen, bounds);
+  k_centroids<<<(int)std::min<int64_t>(grid_for(T, 256), (int64_t)sm_count() * 8), 256, 0, st>>>(
+      s->rest, s->idx, s->vbody, s->xf, T, s->cen, bounds);
   k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->keys, s->order, s->keys_orig);
   // sort (keys, order) with ping-pong through (keys_alt, vals_alt); 7 passes
   const int ntiles = (int)((T + kSortTile - 1) / kSortTile);

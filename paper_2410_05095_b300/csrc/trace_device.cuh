@@ -115,11 +115,12 @@ __device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o,
   return false;
 }
 
-// Stack traversal of the binary LBVH in the while-while form of Aila and
-// Laine (2009): the inner loop walks internal nodes, nearest child first,
-// and postpones the first leaf it meets; it leaves once every lane of the
-// warp holds a postponed leaf (or has nothing left), so the triangle tests of
-// a warp run together instead of splitting every node step.
+// Stack traversal of the binary LBVH, nearest child first.  A leaf child
+// (one triangle) is tested as soon as its box is hit, so the nearest-hit
+// bound tightens early; only internal children go on the stack.
+// (Postponing leaves until the whole warp holds one -- the while-while form
+// of Aila and Laine -- measured 2x slower here: with one triangle per leaf the
+// delayed bound lets rays wander into far subtrees.)
 //   ANY:  any hit in (0, tmax) other than `skip`; returns true on a hit.
 //   else: nearest hit in (0, inf) by (t, original index) -- independent of
 //         the visiting order; prim = original index (-1 = miss), pos = sorted
@@ -136,50 +137,42 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
   int stack[STACK];
   stack[0] = kDone;
   int sp = 1;
-  int cur = 0;   // internal node >= 0, leaf < 0, or kDone
-  int leaf = 0;  // postponed leaf code (< 0), 0 = none
+  int cur = 0;  // internal node, or kDone
   int64_t budget = c.cap;
-  while (cur != kDone || leaf < 0) {
-    while (cur >= 0 && cur != kDone) {
-      if (--budget < 0) {
-        atomicOr(c.err, kErrTimeout);
-        return false;
-      }
-      if ((uint32_t)cur >= nnodes) {  // never for a built tree
-        atomicOr(c.err, kErrCorrupt);
-        return false;
-      }
-      const Node* n = c.nodes + cur;
-      float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
-      int4 dd = __ldg(&n->d);
-      float tn0, tn1;
-      bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
-      bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tb, tn1);
-      if (h0 && h1) {
-        bool first0 = tn0 <= tn1;
-        if (sp < STACK) stack[sp++] = first0 ? dd.y : dd.x;
-        else atomicOr(c.err, kErrStack);
-        cur = first0 ? dd.x : dd.y;
-      } else if (h0) {
-        cur = dd.x;
-      } else if (h1) {
-        cur = dd.y;
-      } else {
-        cur = stack[--sp];
-      }
-      if (cur < 0 && leaf == 0) {
-        leaf = cur;
-        cur = stack[--sp];
-      }
-      if (!__any_sync(__activemask(), leaf == 0)) break;
+  while (cur != kDone) {
+    if (--budget < 0) {
+      atomicOr(c.err, kErrTimeout);
+      return false;
     }
-    while (leaf < 0) {
-      if (leaf_test<ANY>(c, leaf, o, d, tmax, skip, prim, pos, tb)) return true;
-      leaf = 0;
-      if (cur < 0) {
-        leaf = cur;
-        cur = stack[--sp];
-      }
+    if ((uint32_t)cur >= nnodes) {  // never for a built tree
+      atomicOr(c.err, kErrCorrupt);
+      return false;
+    }
+    const Node* n = c.nodes + cur;
+    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
+    int4 dd = __ldg(&n->d);
+    float tn0, tn1;
+    bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
+    bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tb, tn1);
+    if (h0 && dd.x < 0) {
+      if (leaf_test<ANY>(c, dd.x, o, d, tmax, skip, prim, pos, tb)) return true;
+      h0 = false;
+    }
+    if (h1 && dd.y < 0) {
+      if (leaf_test<ANY>(c, dd.y, o, d, tmax, skip, prim, pos, tb)) return true;
+      h1 = false;
+    }
+    if (h0 && h1) {
+      bool first0 = tn0 <= tn1;
+      if (sp < STACK) stack[sp++] = first0 ? dd.y : dd.x;
+      else atomicOr(c.err, kErrStack);
+      cur = first0 ? dd.x : dd.y;
+    } else if (h0) {
+      cur = dd.x;
+    } else if (h1) {
+      cur = dd.y;
+    } else {
+      cur = stack[--sp];
     }
   }
   return false;

@@ -234,14 +234,41 @@ def assemble(meshes, nmat: int, mats: np.ndarray, mesh_body=None, nbody: int = 1
                  mats=mats, nbody=nbody, mesh_tri_start=starts)
 
 
-def _spheres(rng: Rng, n: int, cxz: float, cy: tuple, radius: tuple, level: int = 4):
+def _kd_labels(cs, nbody: int):
+    """Order sphere ids so that the runs of ids forming body b (ids i with
+    floor(nbody*i/n) == b) are spatially compact: recursive median splits of
+    the (x, z) centres along the longer extent, with the split counts taken
+    from the body boundaries."""
+    n = len(cs)
+    start = [(b * n + nbody - 1) // nbody for b in range(nbody + 1)]  # first id of body b
+
+    def rec(ids, b0, b1):
+        if b1 - b0 <= 1:
+            return list(ids)
+        mid = (b0 + b1) // 2
+        cnt = start[mid] - start[b0]
+        pts = np.array([cs[i] for i in ids])
+        ax = 0 if np.ptp(pts[:, 0]) >= np.ptp(pts[:, 2]) else 2
+        srt = sorted(ids, key=lambda i: (cs[i][ax], i))
+        return rec(srt[:cnt], b0, mid) + rec(srt[cnt:], mid, b1)
+
+    return rec(list(range(n)), 0, nbody)
+
+
+def _spheres(rng: Rng, n: int, cxz: float, cy: tuple, radius: tuple, level: int = 4,
+             nbody: int = 0):
+    """n icospheres with centres uniform in [-cxz,cxz]^2 (x,z) x cy (y) and
+    radii uniform in `radius`.  nbody > 0: number the spheres so that each
+    run of consecutive ids that forms one rigid body (sphere i -> body
+    floor(nbody*i/n)) is a spatially compact cluster (the draws themselves
+    are unchanged)."""
     uv, uf = icosphere(level)
-    out = []
+    cs, rs = [], []
     for _ in range(n):
-        c = np.array([rng.uniform(-cxz, cxz), rng.uniform(*cy), rng.uniform(-cxz, cxz)])
-        r = rng.uniform(*radius)
-        out.append((uv * r + c, uf))
-    return out
+        cs.append(np.array([rng.uniform(-cxz, cxz), rng.uniform(*cy), rng.uniform(-cxz, cxz)]))
+        rs.append(rng.uniform(*radius))
+    order = _kd_labels(cs, nbody) if nbody else range(n)
+    return [(uv * rs[i] + cs[i], uf) for i in order]
 
 
 # ----------------------------------------------------------------------------
@@ -294,7 +321,7 @@ def scene_icospheres_terrain(rng: Rng, nspheres: int, cells: int, nmat: int,
                              nbody_spheres: int = 0) -> Scene:
     mats = random_materials(rng, nmat)
     tv, tf = terrain(rng, cells)
-    sph = _spheres(rng, nspheres, 10.0, (0.5, 3.0), (0.3, 1.0))
+    sph = _spheres(rng, nspheres, 10.0, (0.5, 3.0), (0.3, 1.0), nbody=nbody_spheres)
     meshes = [(tv, tf)] + sph
     if nbody_spheres:
         mesh_body = [nbody_spheres] + [(nbody_spheres * i) // nspheres for i in range(nspheres)]
@@ -360,7 +387,9 @@ def batch16(nscenes: int = 16, ncams_per: int = 4, tmin: float = 20e3, tmax: flo
 # Rigid-body motion (the simulator's per-step world matrices, §IV-C)
 # ----------------------------------------------------------------------------
 class RigidMotion:
-    """Per frame, body b < nbody-1 gets a random delta: axis uniform on S^2,
+    """Bodies are runs of consecutive spheres, numbered by a k-d partition of
+    their centres (compact clusters, like the rigid parts of a simulated
+    scene).  Per frame, body b < nbody-1 gets a random delta: axis uniform on S^2,
     angle uniform in [0, 2 deg], translation of uniform direction and
     magnitude uniform in [0, 0.05].  The delta rotates about the body's
     current pivot (its rest-pose AABB centre mapped by the current matrix).
