@@ -206,7 +206,8 @@ void free_scene(fire_scene_s* s) {
   s->prof = nullptr;
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
-                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs};
+                  s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
+                  s->lvl_nodes, s->lvl_aux};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -249,6 +250,8 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris, 48 * (size_t)T},
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
+      {(void**)&s->lvl_nodes, 4 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->lvl_aux, 12 * (size_t)(kMaxHeight + 2) + 16},
   };
   for (auto& a : list)
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "LBVH buffers");
@@ -529,14 +532,26 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
       if (T == 0) return FIRE_OK;
       std::vector<Node> nodes(std::max<int64_t>(ni, 1));
       if (int e = get(nodes.data(), s->nodes, 64 * nodes.size())) return e;
+      // node = 16 floats: child 0 box [0..5], link [6], height [7]; child 1 at [8..15]
+      auto link = [&](const Node& n, int side) {
+        int v;
+        memcpy(&v, reinterpret_cast<const float*>(&n) + 8 * side + 6, 4);
+        return v;
+      };
       auto code = [&](int c) { return c >= 0 ? c : (int)(T - 1) + ~c; };
       if (what == 2) {
         int32_t* o = (int32_t*)host_dst;
-        for (int64_t i = 0; i < ni; ++i) { o[2 * i] = code(nodes[i].d.x); o[2 * i + 1] = code(nodes[i].d.y); }
+        for (int64_t i = 0; i < ni; ++i) {
+          o[2 * i] = code(link(nodes[i], 0));
+          o[2 * i + 1] = code(link(nodes[i], 1));
+        }
       } else if (what == 3) {
         int32_t* o = (int32_t*)host_dst;
         o[0] = -1;
-        for (int64_t i = 0; i < ni; ++i) { o[code(nodes[i].d.x)] = (int32_t)i; o[code(nodes[i].d.y)] = (int32_t)i; }
+        for (int64_t i = 0; i < ni; ++i) {
+          o[code(link(nodes[i], 0))] = (int32_t)i;
+          o[code(link(nodes[i], 1))] = (int32_t)i;
+        }
       } else {
         float* o = (float*)host_dst;
         auto put = [&](int c, const float* b) { memcpy(o + 6 * (int64_t)c, b, 24); };
@@ -545,14 +560,14 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
         } else {
           for (int64_t i = 0; i < ni; ++i) {
             const float* f = reinterpret_cast<const float*>(&nodes[i]);
-            put(code(nodes[i].d.x), f);
-            put(code(nodes[i].d.y), f + 6);
+            put(code(link(nodes[i], 0)), f);
+            put(code(link(nodes[i], 1)), f + 8);
           }
           float root[6];
           const float* f = reinterpret_cast<const float*>(&nodes[0]);
           for (int k = 0; k < 3; ++k) {
-            root[k] = std::fmin(f[k], f[6 + k]);
-            root[3 + k] = std::fmax(f[3 + k], f[9 + k]);
+            root[k] = std::fmin(f[k], f[8 + k]);
+            root[3 + k] = std::fmax(f[3 + k], f[11 + k]);
           }
           put(0, root);
         }

@@ -20,17 +20,19 @@ namespace fire {
 // ---------------------------------------------------------------------------
 // Device data layout
 // ---------------------------------------------------------------------------
-// Internal node of the binary LBVH, 64 B = two 32-B sectors: the boxes of
-// BOTH children plus the child links, so one node fetch decides which
-// children a ray enters (no separate fetch of the child's own box).
-//   a = lo0.x lo0.y lo0.z hi0.x
-//   b = hi0.y hi0.z lo1.x lo1.y
-//   c = lo1.z hi1.x hi1.y hi1.z
-//   d = child0, child1, height0, height1   (child >= 0: internal node index,
-//                                           child < 0: leaf at sorted position ~child)
+// Internal node of the binary LBVH, 64 B = two 32-B sectors, one per child:
+// the child's box, its link and its subtree height.  One node fetch decides
+// which children a ray enters (no separate fetch of the child's own box),
+// and a refit writes each child as one whole sector (no partial-sector
+// read-modify-write in L2/DRAM).
+//   a = lo0.x lo0.y lo0.z hi0.x      sector 0 (child 0)
+//   b = hi0.y hi0.z link0 height0
+//   c = lo1.x lo1.y lo1.z hi1.x      sector 1 (child 1)
+//   d = hi1.y hi1.z link1 height1
+// link >= 0: internal node index; link < 0: leaf at sorted position ~link
+// (links and heights are stored as the bits of the float lanes).
 struct __align__(16) Node {
-  float4 a, b, c;
-  int4 d;
+  float4 a, b, c, d;
 };
 static_assert(sizeof(Node) == 64, "node must be 64 bytes");
 
@@ -41,6 +43,7 @@ static_assert(sizeof(Node) == 64, "node must be 64 bytes");
 // e1/e2 are the same FP32 differences the ray/triangle test and the normal use.
 
 constexpr int kMaxLights = 8;
+constexpr int kMaxHeight = 128;              // tree height is at most 97 (64 + 32 prefix bits + 1)
 constexpr int kSortBits = 9;                 // 7 passes x 9 bits = 63-bit keys
 constexpr int kSortBins = 1 << kSortBits;
 constexpr int kSortPasses = 7;
@@ -102,7 +105,10 @@ struct fire_scene_s {
   fire::Node* nodes = nullptr;  // [max(nt-1, 1)]
   int32_t* leaf_slot = nullptr; // [nt]   2*parent + side
   int32_t* node_slot = nullptr; // [nt-1] 2*parent + side (root -1)
-  uint32_t* counters = nullptr; // [nt-1] arrival counters (parity per refit)
+  uint32_t* counters = nullptr; // [nt-1] arrival counters of the build's refit
+  int32_t* lvl_nodes = nullptr; // [nt-1] internal nodes grouped by height (per-frame refit)
+  uint8_t* lvl_aux = nullptr;   // level histogram / cursor (u32) + level offsets (i64) on the device
+  std::vector<int64_t> lvl_off; // host copy: level h = lvl_nodes[lvl_off[h] .. lvl_off[h+1])
   float4* tris = nullptr;       // [nt*3]
   // build scratch
   float4* cen = nullptr;        // [nt]

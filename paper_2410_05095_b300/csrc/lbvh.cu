@@ -6,6 +6,7 @@
 // topology of the last build.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 
 #include "fire_internal.cuh"
 
@@ -312,7 +313,8 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, Node* __rest
   else { c0 = (int32_t)gamma; node_slot[gamma] = (int32_t)(2 * i); }
   if (hi == gamma + 1) { c1 = ~(int32_t)(gamma + 1); leaf_slot[gamma + 1] = (int32_t)(2 * i + 1); }
   else { c1 = (int32_t)(gamma + 1); node_slot[gamma + 1] = (int32_t)(2 * i + 1); }
-  nodes[i].d = make_int4(c0, c1, 0, 0);
+  nodes[i].b.z = __int_as_float(c0);
+  nodes[i].d.z = __int_as_float(c1);
   if (i == 0) node_slot[0] = -1;
 }
 
@@ -327,32 +329,35 @@ __global__ void k_gather_sorted(const uint32_t* __restrict__ order, const uint32
   smat[i] = tmat[o];
 }
 
-__device__ __forceinline__ void store_box(Node* node, int side, float3 lo, float3 hi) {
-  float* f = reinterpret_cast<float*>(node);
-  if (side == 0) {
-    *reinterpret_cast<float4*>(f) = make_float4(lo.x, lo.y, lo.z, hi.x);
-    *reinterpret_cast<float2*>(f + 4) = make_float2(hi.y, hi.z);
-  } else {
-    *reinterpret_cast<float2*>(f + 6) = make_float2(lo.x, lo.y);
-    *reinterpret_cast<float4*>(f + 8) = make_float4(lo.z, hi.x, hi.y, hi.z);
-  }
+// Write one child sector of a node: box, link and subtree height (a whole
+// 32-B sector, two 16-B stores).
+__device__ __forceinline__ void store_child(Node* node, int side, float3 lo, float3 hi, int link, int height) {
+  float4* s = side == 0 ? &node->a : &node->c;
+  s[0] = make_float4(lo.x, lo.y, lo.z, hi.x);
+  s[1] = make_float4(hi.y, hi.z, __int_as_float(link), __int_as_float(height));
+}
+
+// Box (union of both children) and height of a node, read through L2.
+__device__ __forceinline__ void load_node_box(const Node* nd, float3& lo, float3& hi, int& height) {
+  float4 a = __ldcg(&nd->a), b = __ldcg(&nd->b), c = __ldcg(&nd->c), d = __ldcg(&nd->d);
+  lo = f3(fminf(a.x, c.x), fminf(a.y, c.y), fminf(a.z, c.z));
+  hi = f3(fmaxf(a.w, c.w), fmaxf(b.x, d.x), fmaxf(b.y, d.y));
+  height = 1 + max(__float_as_int(b.w), __float_as_int(d.w));
 }
 
 // ----------------------------------------------------------------------------
-// Refit: one thread per leaf (sorted position).  Transform the triangle,
-// write its 48-B record, store its box in the parent's slot; then climb:
-// the second thread to arrive at a node (odd counter value -- every refit
-// adds exactly 2 per node, so no reset is needed) unions the node's two
-// child boxes into the grandparent's slot.  Min/max are exact, so the boxes
-// do not depend on the arrival order.  HEIGHT also records subtree heights
-// (build only).
+// Build refit: one thread per leaf (sorted position).  Transform the
+// triangle, write its 48-B record, store its box in the parent's slot; then
+// climb: the second thread to arrive at a node (odd counter value) unions
+// the node's two child boxes into the grandparent's slot and records the
+// node's height there.  Min/max are exact, so the boxes do not depend on the
+// arrival order.  (Per frame, the level-synchronous refit below is used.)
 // ----------------------------------------------------------------------------
-template <bool HEIGHT>
-__global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
-                        const float* __restrict__ xf, const uint4* __restrict__ sidx,
-                        const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
-                        Node* nodes, const int32_t* __restrict__ leaf_slot,
-                        const int32_t* __restrict__ node_slot, uint32_t* counters) {
+__global__ void k_refit_build(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                              const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                              const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
+                              Node* nodes, const int32_t* __restrict__ leaf_slot,
+                              const int32_t* __restrict__ node_slot, uint32_t* counters) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < nt;
@@ -373,9 +378,8 @@ __global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restr
   }
   if (nt == 1) {  // single leaf: node 0 holds it on both sides
     if (valid) {
-      store_box(nodes, 0, lo, hi);
-      store_box(nodes, 1, lo, hi);
-      if (HEIGHT) nodes[0].d = make_int4(~0, ~0, 0, 0);
+      store_child(nodes, 0, lo, hi, ~0, 0);
+      store_child(nodes, 1, lo, hi, ~0, 0);
     }
     return;
   }
@@ -394,18 +398,16 @@ __global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restr
   const bool pair_hi = slot >= 0 && (slot & 1) == 1 && lane > 0 && s_prev == slot - 1;
   if (pair_hi) return;
   int h = 0;
+  int link = (int)~i;
   if (pair_lo) {
     if ((slot >> 1) >= nt - 1) return;  // never for a complete topology
     Node* node = nodes + (slot >> 1);
-    store_box(node, 0, lo, hi);
-    store_box(node, 1, nlo, nhi);
-    if (HEIGHT) {
-      reinterpret_cast<int*>(&node->d)[2] = 0;
-      reinterpret_cast<int*>(&node->d)[3] = 0;
-    }
+    store_child(node, 0, lo, hi, (int)~i, 0);
+    store_child(node, 1, nlo, nhi, (int)~(i + 1), 0);
     lo = fmin3(lo, nlo);
     hi = fmax3(hi, nhi);
     h = 1;
+    link = slot >> 1;
     slot = node_slot[slot >> 1];
     if (slot < 0) return;  // the pair was the root
   }
@@ -413,23 +415,107 @@ __global__ void k_refit(const float4* __restrict__ rest, const uint16_t* __restr
     if (slot < 0 || (slot >> 1) >= nt - 1) return;  // never for a complete topology
     int32_t p = slot >> 1;
     Node* node = nodes + p;
-    store_box(node, slot & 1, lo, hi);
-    if (HEIGHT) reinterpret_cast<int*>(&node->d)[2 + (slot & 1)] = h;
+    store_child(node, slot & 1, lo, hi, link, h);
     // release the box to the sibling's thread / acquire the sibling's box
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     uint32_t old = atomicAdd(counters + p, 1u);
     if ((old & 1u) == 0) return;  // first arrival: the sibling finishes this node
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    float4 a = __ldcg(&node->a), b = __ldcg(&node->b), c = __ldcg(&node->c);
-    lo = f3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
-    hi = f3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
-    if (HEIGHT) {
-      int4 d = __ldcg(&node->d);
-      h = 1 + max(d.z, d.w);
-    }
+    load_node_box(node, lo, hi, h);
+    link = p;
     slot = node_slot[p];
     if (slot < 0) return;  // root done
   }
+}
+
+// ----------------------------------------------------------------------------
+// Per-frame refit, level-synchronous and without fences: the build groups
+// the internal nodes by height (leaves = 0, node = 1 + max over children);
+// each frame then runs
+//   k_refit_leaves  one thread per leaf: transform, 48-B record, leaf box
+//                   into the parent's slot (no atomics);
+//   k_refit_level   one launch per large level: node box = union of its two
+//                   slots, stored into its parent's slot;
+//   k_refit_top     one block for the small top levels, __syncthreads()
+//                   between levels.
+// Kernel boundaries (and the block barrier) order every read after the
+// writes of the level below; min/max are exact, so the boxes equal the
+// atomic-climb boxes of the build bit for bit.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_refit_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                                                      const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                                                      const uint32_t* __restrict__ smat, int64_t nt,
+                                                      float4* __restrict__ tris, Node* __restrict__ nodes,
+                                                      const int32_t* __restrict__ leaf_slot) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  uint4 id = sidx[i];
+  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
+  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
+  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
+  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
+  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
+  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
+  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
+  if (nt == 1) {
+    store_child(nodes, 0, lo, hi, ~0, 0);
+    store_child(nodes, 1, lo, hi, ~0, 0);
+    return;
+  }
+  int32_t slot = leaf_slot[i];
+  if (slot < 0 || (slot >> 1) >= nt - 1) return;  // never for a complete topology
+  store_child(nodes + (slot >> 1), slot & 1, lo, hi, (int)~i, 0);
+}
+
+__device__ __forceinline__ void refit_node(Node* nodes, const int32_t* __restrict__ node_slot, int32_t n,
+                                           int64_t nt) {
+  if (n < 0 || n >= nt - 1) return;  // never for a complete topology
+  int32_t slot = node_slot[n];
+  if (slot < 0 || (slot >> 1) >= nt - 1) return;  // root: its box is the two slots themselves
+  float3 lo, hi;
+  int h;
+  load_node_box(nodes + n, lo, hi, h);
+  store_child(nodes + (slot >> 1), slot & 1, lo, hi, n, h);
+}
+
+__global__ void __launch_bounds__(256) k_refit_level(Node* nodes, const int32_t* __restrict__ node_slot,
+                                                     const int32_t* __restrict__ lvl_nodes, int64_t begin,
+                                                     int64_t end, int64_t nt) {
+  const int64_t j = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < end) refit_node(nodes, node_slot, lvl_nodes[j], nt);
+}
+
+__global__ void __launch_bounds__(1024) k_refit_top(Node* nodes, const int32_t* __restrict__ node_slot,
+                                                    const int32_t* __restrict__ lvl_nodes,
+                                                    const int64_t* __restrict__ lvl_off, int h0, int h1,
+                                                    int64_t nt) {
+  for (int h = h0; h <= h1; ++h) {
+    for (int64_t j = lvl_off[h] + threadIdx.x; j < lvl_off[h + 1]; j += blockDim.x)
+      refit_node(nodes, node_slot, lvl_nodes[j], nt);
+    __syncthreads();
+  }
+}
+
+// Build: height of every internal node (from the child heights the build's
+// refit stored in d.z / d.w) and its level histogram.
+__global__ void k_heights(const Node* __restrict__ nodes, int64_t ni, int32_t* __restrict__ height,
+                          uint32_t* __restrict__ hist, int hmax) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= ni) return;
+  int h = 1 + max(__float_as_int(nodes[n].b.w), __float_as_int(nodes[n].d.w));
+  h = min(max(h, 1), hmax);
+  height[n] = h;
+  atomicAdd(hist + h, 1u);
+}
+
+__global__ void k_scatter_levels(const int32_t* __restrict__ height, int64_t ni, const int64_t* __restrict__ lvl_off,
+                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ lvl_nodes) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= ni) return;
+  int h = height[n];
+  uint32_t p = atomicAdd(cursor + h, 1u);
+  lvl_nodes[lvl_off[h] + p] = (int32_t)n;
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -486,14 +572,39 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat);
   if (T > 1)
     if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;
-  k_refit<true><<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
-                                                  s->nodes, s->leaf_slot, s->node_slot, s->counters);
+  k_refit_build<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+                                                   s->nodes, s->leaf_slot, s->node_slot, s->counters);
   prof_end(s, kStageBuild, st);
   if (int e = cuda_check(cudaGetLastError(), "build kernels")) return e;
-  int4 d0;
-  if (int e = cuda_check(cudaMemcpyAsync(&d0, &s->nodes[0].d, sizeof(int4), cudaMemcpyDeviceToHost, st), "copy")) return e;
+  Node n0;
+  if (int e = cuda_check(cudaMemcpyAsync(&n0, &s->nodes[0], sizeof(Node), cudaMemcpyDeviceToHost, st), "copy")) return e;
   if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
-  s->height = T > 1 ? 1 + std::max(d0.z, d0.w) : 1;
+  int h0, h1;
+  memcpy(&h0, &n0.b.w, 4);
+  memcpy(&h1, &n0.d.w, 4);
+  s->height = T > 1 ? 1 + std::max(h0, h1) : 1;
+  s->lvl_off.clear();
+  if (T > 1) {
+    // level lists for the per-frame refit (heights 1..H)
+    const int H = std::min(s->height, kMaxHeight);
+    const int64_t ni = T - 1;
+    int32_t* height = reinterpret_cast<int32_t*>(s->counters);  // the counters are free after the build
+    uint32_t* hist = reinterpret_cast<uint32_t*>(s->lvl_aux);
+    if (int e = cuda_check(cudaMemsetAsync(hist, 0, 4 * (kMaxHeight + 2), st), "memset")) return e;
+    k_heights<<<grid_for(ni, 256), 256, 0, st>>>(s->nodes, ni, height, hist, H);
+    std::vector<uint32_t> hh(kMaxHeight + 2);
+    if (int e = cuda_check(cudaMemcpyAsync(hh.data(), hist, 4 * hh.size(), cudaMemcpyDeviceToHost, st), "copy")) return e;
+    if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
+    s->lvl_off.assign(H + 2, 0);
+    for (int h = 1; h <= H; ++h) s->lvl_off[h + 1] = s->lvl_off[h] + hh[h];
+    int64_t* off_dev = reinterpret_cast<int64_t*>(s->lvl_aux + 4 * (kMaxHeight + 2));
+    uint32_t* cursor = hist;
+    if (int e = cuda_check(cudaMemcpyAsync(off_dev, s->lvl_off.data(), 8 * s->lvl_off.size(), cudaMemcpyHostToDevice, st), "copy")) return e;
+    if (int e = cuda_check(cudaMemsetAsync(cursor, 0, 4 * (kMaxHeight + 2), st), "memset")) return e;
+    k_scatter_levels<<<grid_for(ni, 256), 256, 0, st>>>(height, ni, off_dev, cursor, s->lvl_nodes);
+    if (int e = cuda_check(cudaGetLastError(), "level lists")) return e;
+    if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // off_dev/hist reuse, host vector
+  }
   s->built = true;
   return FIRE_OK;
 }
@@ -502,10 +613,22 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) return FIRE_OK;
   prof_begin(s, kStageRefit, st);
-  k_refit<false><<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
-                                                   s->nodes, s->leaf_slot, s->node_slot, s->counters);
+  k_refit_leaves<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+                                                   s->nodes, s->leaf_slot);
+  if (T > 1) {
+    const int H = (int)s->lvl_off.size() - 2;
+    const int64_t* off_dev = reinterpret_cast<const int64_t*>(s->lvl_aux + 4 * (kMaxHeight + 2));
+    int h = 1;
+    for (; h <= H; ++h) {
+      int64_t n = s->lvl_off[h + 1] - s->lvl_off[h];
+      if (n <= 4096) break;  // the rest is cheaper in one block
+      k_refit_level<<<grid_for(n, 256), 256, 0, st>>>(s->nodes, s->node_slot, s->lvl_nodes, s->lvl_off[h],
+                                                      s->lvl_off[h + 1], T);
+    }
+    if (h <= H) k_refit_top<<<1, 1024, 0, st>>>(s->nodes, s->node_slot, s->lvl_nodes, off_dev, h, H, T);
+  }
   prof_end(s, kStageRefit, st);
-  return cuda_check(cudaGetLastError(), "k_refit");
+  return cuda_check(cudaGetLastError(), "refit kernels");
 }
 
 }  // namespace fire

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int n
 
 // Shadow rays from the dense queue: each warp takes 32 consecutive rays (all
 // lanes busy until the queue's tail); an unoccluded ray sets its light's bit
-// in the sample's record.
+// in the sample's record.  (A lane-level ray pool -- refilling idle lanes
+// every 16 node visits -- measured 7% slower: the idle lanes come from the
+// branches inside each node step, not from rays of different lengths.)
 template <int STACK>
 __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs) {
   const int lane = threadIdx.x & 31;

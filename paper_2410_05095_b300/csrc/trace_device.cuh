@@ -149,11 +149,11 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
       return false;
     }
     const Node* n = c.nodes + cur;
-    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c);
-    int4 dd = __ldg(&n->d);
+    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c), dq = __ldg(&n->d);
+    const int2 dd = make_int2(__float_as_int(b.z), __float_as_int(dq.z));  // child links
     float tn0, tn1;
     bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
-    bool h1 = slab(o, inv, b.z, b.w, cc.x, cc.y, cc.z, cc.w, tb, tn1);
+    bool h1 = slab(o, inv, cc.x, cc.y, cc.z, cc.w, dq.x, dq.y, tb, tn1);
     if (h0 && dd.x < 0) {
       if (leaf_test<ANY>(c, dd.x, o, d, tmax, skip, prim, pos, tb)) return true;
       h0 = false;
@@ -195,9 +195,9 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
 // root's two child boxes).
 __device__ __forceinline__ float scene_eps(const Node* nodes, int64_t nt) {
   if (nt == 0) return 0.0f;
-  float4 a = __ldg(&nodes[0].a), b = __ldg(&nodes[0].b), c = __ldg(&nodes[0].c);
-  float3 lo = f3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
-  float3 hi = f3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
+  float4 a = __ldg(&nodes[0].a), b = __ldg(&nodes[0].b), c = __ldg(&nodes[0].c), d = __ldg(&nodes[0].d);
+  float3 lo = f3(fminf(a.x, c.x), fminf(a.y, c.y), fminf(a.z, c.z));
+  float3 hi = f3(fmaxf(a.w, c.w), fmaxf(b.x, d.x), fmaxf(b.y, d.y));
   float3 ext = sub3(hi, lo);
   return 1e-4f * sqrtf(dot3(ext, ext));
 }
