@@ -200,6 +200,24 @@ int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_c
                         const float* inten, const float* dL_drgba, float* dparams, float* dinten,
                         void* stream);
 
+/* Allocation-free variant of fire_shade_backward (the paper has no
+ * counterpart; it is a service for callers that cannot call cudaMalloc while
+ * they run, e.g. a frame loop whose device memory is fixed at start-up, or a
+ * host that must not pay the device synchronisation an allocation can cause).
+ * Same arguments, results and accumulate-into-outputs behaviour as
+ * fire_shade_backward, within the same tolerance.  Its scratch (counters and
+ * the FP64 accumulator) is a fixed array inside the library image, 33,024 B
+ * per GPU that loads the library, held until the process exits.
+ *  - nmat*5 + nlights must be <= 4096, else FIRE_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the one array and clears it on `stream` before use:
+ *    calls whose GPU work overlaps (other streams or host threads) race. */
+int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam,
+                                const fire_light* lights, int32_t nlights, const float* params,
+                                const float* inten, const float* dL_drgba, float* dparams, float* dinten,
+                                void* stream);
+
 /* ------------------------------------------------------------- utilities */
 
 /* Copy internal state to host memory for checks (synchronises `stream` = the

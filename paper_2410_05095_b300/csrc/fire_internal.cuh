@@ -174,6 +174,8 @@ int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten,
 int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,
                    float* dparams, float* dinten, cudaStream_t st);
 int stack_for_height(int height, int requested);
+int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, float* dparams, float* dinten,
+                      double* acc, cudaStream_t st);
 
 // batch.cu
 int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,

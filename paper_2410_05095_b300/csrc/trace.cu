@@ -425,4 +425,20 @@ int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, con
   return cuda_check(cudaGetLastError(), "k_shade_bwd");
 }
 
+// The same backward kernel on caller-provided scratch: `acc` holds
+// nmat*5 + nlights doubles (at most 6144, so the block's copy fits the
+// default shared memory) and a.ctrl at least 4 counter words, all zero on
+// entry.  Nothing is allocated here.
+int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, float* dparams, float* dinten,
+                      double* acc, cudaStream_t st) {
+  TaskGrid g = make_grid(a.cam.W, 0, a.cam.H, a.cam.spp);
+  int ntasks = g.tiles_x * g.tiles_y;
+  if (ntasks == 0) return FIRE_OK;
+  const int nacc = a.mats.n * 5 + a.lights.n;
+  if (nacc > 6144) return set_error(FIRE_ERR_INVALID_ARG, "too many parameters for the scratch backward");
+  int grid = std::max(1, std::min(sm_count() * 4, (ntasks + 3) / 4));
+  k_shade_bwd<<<grid, 128, sizeof(double) * nacc, st>>>(a, g, ntasks, inten, dL, dparams, dinten, acc);
+  return cuda_check(cudaGetLastError(), "k_shade_bwd");
+}
+
 }  // namespace fire

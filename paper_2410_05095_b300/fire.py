@@ -26,7 +26,8 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_bvh_build", "fire_bvh_refit", "fire_render", "fire_render_batch", "fire_shade",
            "fire_shade_backward", "fire_debug_dump", "fire_sync_status",
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
-           "fire_profile_enable", "fire_profile_read", "fire_last_error", "fire_version"]
+           "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_last_error",
+           "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -86,6 +87,7 @@ def lib():
             "fire_batch_last_config": [P],
             "fire_profile_enable": [P, i32],
             "fire_profile_read": [P, P, P],
+            "fire_shade_backward_noalloc": [P, P, P, P, i32, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -234,6 +236,14 @@ class Scene:
         _check(lib().fire_shade_backward(self.h, _ptr(gbuf), C.byref(c), C.cast(L, C.c_void_p), len(lights),
                                          _ptr(params), _ptr(inten), _ptr(dL), _ptr(dparams), _ptr(dinten),
                                          _stream(stream)))
+
+    def shade_backward_noalloc(self, gbuf, cam, lights, params, inten, dL, dparams, dinten, stream=None):
+        """fire_shade_backward without any allocation (scratch in a fixed
+        library array; see include/fire.h)."""
+        c, L = make_camera(cam), make_lights(lights)
+        _check(lib().fire_shade_backward_noalloc(self.h, _ptr(gbuf), C.byref(c), C.cast(L, C.c_void_p),
+                                                 len(lights), _ptr(params), _ptr(inten), _ptr(dL),
+                                                 _ptr(dparams), _ptr(dinten), _stream(stream)))
 
     def dump(self, what: str) -> np.ndarray:
         T = self.nt
