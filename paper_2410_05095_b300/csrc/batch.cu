@@ -19,7 +19,8 @@ namespace fire {
 namespace {
 
 struct BatchCam {
-  const Node* nodes;
+  const Node4* nodes4;
+  int64_t n4;
   const float4* tris;
   int64_t nt;
   const float* mats;
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchCam* __restrict__ cams
     TaskGrid g = make_grid(bc.cam.W, 0, bc.cam.H, bc.cam.spp);
     int x, y, k;
     bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
-    TraceCtx c{bc.nodes, bc.tris, bc.nt, cap, bc.err};
+    TraceCtx c{bc.nodes4, bc.n4, scene_span(bc.nodes4, bc.nt), bc.tris, bc.nt, cap, bc.err};
     float3 rad = f3(0.0f, 0.0f, 0.0f);
     int hit = 0;
     if (valid) {
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchCam* __restrict__ cams
       trace_nearest<STACK>(c, o, d, prim, pos, t);
       if (prim >= 0) {
         hit = 1;
-        const float eps = scene_eps(bc.nodes, bc.nt);
+        const float eps = scene_eps(bc.nodes4, bc.nt);
         float4 B = __ldg(bc.tris + 3 * (int64_t)pos + 1), C = __ldg(bc.tris + 3 * (int64_t)pos + 2);
         float3 n, po;
         hit_frame(B, C, o, d, t, eps, n, po);
@@ -167,7 +168,8 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     fire_scene_s* s = scenes[cam_scene[i]];
     BatchCam& b = h[i];
     memset(&b, 0, sizeof(b));
-    b.nodes = s->nodes;
+    b.nodes4 = s->nodes4;
+    b.n4 = s->n4;
     b.tris = s->tris;
     b.nt = s->nt;
     b.mats = s->mats;
@@ -180,7 +182,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     b.task_begin = ntasks;
     TaskGrid g = make_grid(b.cam.W, 0, b.cam.H, b.cam.spp);
     ntasks += g.tiles_x * g.tiles_y;
-    maxh = std::max(maxh, s->height);
+    maxh = std::max(maxh, stack_need(s));
     cap = std::max(cap, 2 * s->nt + 64);
     shape.push_back(s->nt);
     shape.push_back(b.cam.W);

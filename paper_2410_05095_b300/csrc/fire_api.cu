@@ -207,7 +207,7 @@ void free_scene(fire_scene_s* s) {
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->lvl_nodes, s->lvl_aux};
+                  s->lvl_nodes, s->lvl_aux, s->nodes4, s->q4};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -252,6 +252,8 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
       {(void**)&s->lvl_nodes, 4 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->lvl_aux, 12 * (size_t)(kMaxHeight + 2) + 16},
+      {(void**)&s->nodes4, 128 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},
   };
   for (auto& a : list)
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "LBVH buffers");
@@ -381,7 +383,8 @@ static int fill_args(fire_scene s, const fire_camera* cam, const fire_light* lig
   if (int e = check_cam(cam)) return e;
   memset(a, 0, sizeof(*a));
   if (int e = make_lights(lights, nlights, &a->lights)) return e;
-  a->nodes = s->nodes;
+  a->nodes4 = s->nodes4;
+  a->n4 = s->n4;
   a->tris = s->tris;
   a->nt = s->nt;
   a->cam = make_cam(*cam);
@@ -425,8 +428,10 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
   if (o.stack_depth < 0 || o.stack_depth > 128 || o.blocks_per_sm < 0 ||
       (o.flags & ~FIRE_RENDER_ALLOW_SHALLOW_STACK) != 0)
     return set_error(FIRE_ERR_INVALID_ARG, "invalid render options");
-  if (o.stack_depth > 0 && o.stack_depth < s->height && !(o.flags & FIRE_RENDER_ALLOW_SHALLOW_STACK))
-    return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below the tree height " + std::to_string(s->height));
+  if (o.stack_depth > 0 && o.stack_depth < std::min(stack_need(s), 128) &&
+      !(o.flags & FIRE_RENDER_ALLOW_SHALLOW_STACK))
+    return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below the " + std::to_string(stack_need(s)) +
+                                               " entries the tree can need");
   cudaStream_t st = as_stream(stream);
   s->last_stream = st;
   size_t nsamp = (size_t)cam->width * cam->height * cam->spp;

@@ -36,6 +36,19 @@ struct __align__(16) Node {
 };
 static_assert(sizeof(Node) == 64, "node must be 64 bytes");
 
+// 4-wide node collapsed from the binary tree (build), 128 B = 4 sectors:
+// child boxes as structure-of-arrays (one float4 per coordinate, lane c =
+// child c), the four child links (>= 0: 4-wide node, < 0: leaf ~position,
+// kEmptyLink: unused slot) and, per child, the binary slot (2*parent + side)
+// whose box the per-frame fill copies (-1: unused).
+struct __align__(16) Node4 {
+  float4 lox, loy, loz, hix, hiy, hiz;
+  int4 link;
+  int4 src;
+};
+static_assert(sizeof(Node4) == 128, "4-wide node must be 128 bytes");
+constexpr int kEmptyLink = (int)0x80000000;
+
 // Triangle record in leaf (sorted) order, 48 B:
 //   v0.xyz, w = original triangle index (bits)
 //   e1 = v1 - v0, w = material index (bits)
@@ -109,6 +122,10 @@ struct fire_scene_s {
   int32_t* lvl_nodes = nullptr; // [nt-1] internal nodes grouped by height (per-frame refit)
   uint8_t* lvl_aux = nullptr;   // level histogram / cursor (u32) + level offsets (i64) on the device
   std::vector<int64_t> lvl_off; // host copy: level h = lvl_nodes[lvl_off[h] .. lvl_off[h+1])
+  fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree
+  int64_t n4 = 0;               // 4-wide nodes in use
+  int height4 = 0;              // 4-wide levels
+  int32_t* q4 = nullptr;        // build queue: 2 x [nt] (binary node, 4-wide node) pairs
   float4* tris = nullptr;       // [nt*3]
   // build scratch
   float4* cen = nullptr;        // [nt]
@@ -156,7 +173,8 @@ int lbvh_validate(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host);
 
 // trace.cu
 struct RenderArgs {
-  const Node* nodes;
+  const Node4* nodes4;
+  int64_t n4;
   const float4* tris;
   int64_t nt;
   CamParams cam;
@@ -174,6 +192,8 @@ int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten,
 int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,
                    float* dparams, float* dinten, cudaStream_t st);
 int stack_for_height(int height, int requested);
+// stack entries the 4-wide traversal of this scene can need: 3 per level + sentinel
+inline int stack_need(const fire_scene_s* s) { return 3 * s->height4 + 1; }
 int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, float* dparams, float* dinten,
                       double* acc, cudaStream_t st);
 

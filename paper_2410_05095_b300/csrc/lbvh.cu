@@ -518,6 +518,98 @@ __global__ void k_scatter_levels(const int32_t* __restrict__ height, int64_t ni,
   lvl_nodes[lvl_off[h] + p] = (int32_t)n;
 }
 
+// ----------------------------------------------------------------------------
+// 4-wide traversal tree, collapsed from the binary tree at build (one launch
+// per level): a 4-wide node starts from a binary node's two children and
+// opens the internal member with the largest box surface area until it has
+// four members or only leaves.  Each member keeps the binary slot that holds
+// its box, so a frame's boxes are copied from the binary refit (k_fill4).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float box_area(float4 a, float4 b) {  // sector: lo xyz hi.x | hi.y hi.z
+  float dx = a.w - a.x, dy = b.x - a.y, dz = b.y - a.z;
+  return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs, uint32_t nin,
+                           int32_t* __restrict__ out_pairs, uint32_t* __restrict__ counts, Node4* __restrict__ nodes4,
+                           int64_t cap4) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nin) return;
+  const int b = in_pairs[2 * i], q = in_pairs[2 * i + 1];
+  int link[4] = {kEmptyLink, kEmptyLink, kEmptyLink, kEmptyLink}, src[4] = {-1, -1, -1, -1};
+  float area[4] = {0, 0, 0, 0};
+  for (int side = 0; side < 2; ++side) {
+    const float4* s = side == 0 ? &nodes[b].a : &nodes[b].c;
+    float4 a = s[0], bb = s[1];
+    link[side] = __float_as_int(bb.z);
+    src[side] = 2 * b + side;
+    area[side] = box_area(a, bb);
+  }
+  int m = 2;
+  while (m < 4) {
+    int j = -1;
+    float best = -1.0f;
+    for (int k = 0; k < m; ++k)
+      if (link[k] >= 0 && area[k] > best) { best = area[k]; j = k; }
+    if (j < 0) break;
+    const int f = link[j];
+    float4 a0 = nodes[f].a, b0 = nodes[f].b, a1 = nodes[f].c, b1 = nodes[f].d;
+    link[j] = __float_as_int(b0.z);
+    src[j] = 2 * f;
+    area[j] = box_area(a0, b0);
+    link[m] = __float_as_int(b1.z);
+    src[m] = 2 * f + 1;
+    area[m] = box_area(a1, b1);
+    ++m;
+  }
+  int out[4];
+  for (int k = 0; k < 4; ++k) {
+    out[k] = link[k];
+    if (k < m && link[k] >= 0) {
+      uint32_t q2 = atomicAdd(counts + 1, 1u);   // 4-wide node index
+      uint32_t p = atomicAdd(counts + 0, 1u);    // next level's queue slot
+      if (q2 >= cap4) {                          // never: a 4-wide node consumes >= 1 binary node
+        out[k] = kEmptyLink;
+        continue;
+      }
+      out[k] = (int)q2;
+      out_pairs[2 * p] = link[k];
+      out_pairs[2 * p + 1] = (int)q2;
+    }
+  }
+  nodes4[q].link = make_int4(out[0], out[1], out[2], out[3]);
+  nodes4[q].src = make_int4(src[0], src[1], src[2], src[3]);
+}
+
+// Per frame: copy each member's box from its binary slot (whole 32-B sector
+// reads, 112-B node writes).
+__global__ void __launch_bounds__(256) k_fill4(const Node* __restrict__ nodes, Node4* __restrict__ nodes4, int64_t n4) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const int4 src = nodes4[q].src;
+  const int sv[4] = {src.x, src.y, src.z, src.w};
+  float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    // unused slot: the inverted infinite box, which no ray enters
+    const float inf = __int_as_float(0x7f800000);
+    float4 a = make_float4(inf, inf, inf, -inf), b = make_float4(-inf, -inf, 0, 0);
+    if (sv[c] >= 0) {
+      const float4* s = (sv[c] & 1) ? &nodes[sv[c] >> 1].c : &nodes[sv[c] >> 1].a;
+      a = __ldcg(s);
+      b = __ldcg(s + 1);
+    }
+    lx[c] = a.x; ly[c] = a.y; lz[c] = a.z; hx[c] = a.w; hy[c] = b.x; hz[c] = b.y;
+  }
+  Node4* n = nodes4 + q;
+  n->lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
+  n->loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
+  n->loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
+  n->hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
+  n->hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
+  n->hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
+}
+
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -605,6 +697,32 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
     if (int e = cuda_check(cudaGetLastError(), "level lists")) return e;
     if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // off_dev/hist reuse, host vector
   }
+  // 4-wide traversal tree: collapse level by level from the binary root
+  {
+    const int64_t cap4 = std::max<int64_t>(T - 1, 1);
+    int32_t* qa = s->q4;
+    int32_t* qb = s->q4 + 2 * cap4;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(s->lvl_aux + 12 * (kMaxHeight + 2));
+    const int32_t root[2] = {0, 0};
+    const uint32_t init[2] = {0u, 1u};  // next-level queue length, 4-wide nodes allocated (root)
+    if (int e = cuda_check(cudaMemcpyAsync(qa, root, sizeof(root), cudaMemcpyHostToDevice, st), "copy")) return e;
+    if (int e = cuda_check(cudaMemcpyAsync(counts, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
+    uint32_t nin = 1, h[2] = {0u, 1u};
+    int levels = 0;
+    while (nin > 0 && levels < 4 * kMaxHeight) {
+      if (int e = cuda_check(cudaMemsetAsync(counts, 0, 4, st), "memset")) return e;
+      k_collapse<<<grid_for(nin, 256), 256, 0, st>>>(s->nodes, qa, nin, qb, counts, s->nodes4, cap4);
+      if (int e = cuda_check(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, st), "copy")) return e;
+      if (int e = cuda_check(cudaStreamSynchronize(st), "collapse")) return e;
+      nin = h[0];
+      std::swap(qa, qb);
+      ++levels;
+    }
+    s->n4 = std::min<int64_t>(h[1], cap4);
+    s->height4 = levels;
+    k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
+    if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
+  }
   s->built = true;
   return FIRE_OK;
 }
@@ -627,6 +745,7 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
     }
     if (h <= H) k_refit_top<<<1, 1024, 0, st>>>(s->nodes, s->node_slot, s->lvl_nodes, off_dev, h, H, T);
   }
+  k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
   prof_end(s, kStageRefit, st);
   return cuda_check(cudaGetLastError(), "refit kernels");
 }

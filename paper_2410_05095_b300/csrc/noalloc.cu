@@ -77,7 +77,8 @@ extern "C" int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec*
   RenderArgs a;
   memset(&a, 0, sizeof(a));
   if (int e = make_lights(lights, nlights, &a.lights)) return e;
-  a.nodes = s->nodes;
+  a.nodes4 = s->nodes4;
+  a.n4 = s->n4;
   a.tris = s->tris;
   a.nt = s->nt;
   a.cam = make_cam(*cam);

@@ -27,8 +27,8 @@ template <int STACK>
 __global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;
-  TraceCtx c{a.nodes, a.tris, a.nt, a.iter_cap, a.ctrl + 8};
-  const float eps = scene_eps(a.nodes, a.nt);
+  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  const float eps = scene_eps(a.nodes4, a.nt);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 0, 1);
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int n
 template <int STACK>
 __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs) {
   const int lane = threadIdx.x & 31;
-  TraceCtx c{a.nodes, a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
   const uint32_t njobs = a.ctrl[4];
   int4* rec = reinterpret_cast<int4*>(a.g);
   while (true) {
@@ -133,8 +133,8 @@ __device__ __forceinline__ void resolve_write(const RenderArgs& a, int lane, boo
 template <int STACK, bool TRACE>
 __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int ntasks, const float* inten) {
   const int lane = threadIdx.x & 31;
-  TraceCtx c{a.nodes, a.tris, a.nt, a.iter_cap, a.ctrl + 8};
-  const float eps = scene_eps(a.nodes, a.nt);
+  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  const float eps = scene_eps(a.nodes4, a.nt);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 1, 1);
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const float eps = scene_eps(a.nodes, a.nt);
+  const float eps = scene_eps(a.nodes4, a.nt);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 2, 1);
@@ -375,7 +375,7 @@ int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o
   if (ntasks == 0) return FIRE_OK;
   // task counters, queue length and queue cursor (the error word at [8] stays)
   if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 8 * 4, st), "memset")) return e;
-  switch (stack_for_height(s->height, o.stack_depth)) {
+  switch (stack_for_height(stack_need(s), o.stack_depth)) {
     case 8: return launch_render<8>(s, a, g, ntasks, o, st);
     case 32: return launch_render<32>(s, a, g, ntasks, o, st);
     case 64: return launch_render<64>(s, a, g, ntasks, o, st);

@@ -85,7 +85,9 @@ __device__ __forceinline__ bool mt_t(float3 o, float3 d, float4 A, float4 B, flo
 }
 
 struct TraceCtx {
-  const Node* __restrict__ nodes;
+  const Node4* __restrict__ nodes4;  // 4-wide traversal tree
+  int64_t n4;
+  float span;        // largest |coordinate| of the scene box (box-test slack)
   const float4* __restrict__ tris;
   int64_t nt;
   int64_t cap;       // node-visit cap per ray (>= 1)
@@ -115,12 +117,88 @@ __device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o,
   return false;
 }
 
-// Stack traversal of the binary LBVH, nearest child first.  A leaf child
-// (one triangle) is tested as soon as its box is hit, so the nearest-hit
-// bound tightens early; only internal children go on the stack.
-// (Postponing leaves until the whole warp holds one -- the while-while form
-// of Aila and Laine -- measured 2x slower here: with one triangle per leaf the
-// delayed bound lets rays wander into far subtrees.)
+// Three-input min / max (one instruction each on sm_100-class GPUs).
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Per-ray data of the 4-wide box test: for each axis the member (0..5 =
+// lox, loy, loz, hix, hiy, hiz) holding the near plane and the far plane,
+// picked once from the sign of the direction, so a child's entry and exit
+// distances need no per-axis min/max.
+// Each plane distance is one FMA, t = fma(plane, inv, c), with the per-ray
+// constants c = -o*inv -+ s.  The slack s_a = 2^-19 (M + |o_a|) |inv_a| (M =
+// largest |coordinate| of the scene box) exceeds the FMA form's rounding
+// error, |plane*inv| u + |o*inv| u + |t| u <= 3u (M + |o_a|)|inv_a|, by a
+// factor of 10 and also covers the triangle test's own rounding, so entry
+// distances are only ever lowered and exit distances raised: a box holding a
+// hit the triangle test would accept is never culled.
+struct RaySetup {
+  float3 inv;
+  float cnx, cny, cnz, cfx, cfy, cfz;
+  int nx, ny, nz, fx, fy, fz;
+};
+
+__device__ __forceinline__ RaySetup ray_setup(float3 o, float3 d, float span) {
+  RaySetup r;
+  r.inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const float k = 1.0f / 524288.0f;  // 2^-19
+  const float sx = k * (span + fabsf(o.x)) * fabsf(r.inv.x);
+  const float sy = k * (span + fabsf(o.y)) * fabsf(r.inv.y);
+  const float sz = k * (span + fabsf(o.z)) * fabsf(r.inv.z);
+  const float ox = -o.x * r.inv.x, oy = -o.y * r.inv.y, oz = -o.z * r.inv.z;
+  r.cnx = ox - sx;
+  r.cny = oy - sy;
+  r.cnz = oz - sz;
+  r.cfx = ox + sx;
+  r.cfy = oy + sy;
+  r.cfz = oz + sz;
+  r.nx = r.inv.x >= 0.0f ? 0 : 3;
+  r.ny = r.inv.y >= 0.0f ? 1 : 4;
+  r.nz = r.inv.z >= 0.0f ? 2 : 5;
+  r.fx = 3 - r.nx;
+  r.fy = 5 - r.ny;
+  r.fz = 7 - r.nz;
+  return r;
+}
+
+// Entry/exit test of one child against [0, tmax].  Unused slots hold the
+// inverted infinite box (lo = +inf, hi = -inf): entry +inf, exit -inf, never hit.
+__device__ __forceinline__ bool slab4(const RaySetup& r, float nx, float ny, float nz, float fx, float fy, float fz,
+                                      float tmax, float& tnear) {
+  float tnx = fmaf(nx, r.inv.x, r.cnx), tny = fmaf(ny, r.inv.y, r.cny), tnz = fmaf(nz, r.inv.z, r.cnz);
+  float tfx = fmaf(fx, r.inv.x, r.cfx), tfy = fmaf(fy, r.inv.y, r.cfy), tfz = fmaf(fz, r.inv.z, r.cfz);
+  float tn = fmax3f(tnx, tny, fmaxf(tnz, 0.0f));
+  float tf = fmin3f(tfx, tfy, fminf(tfz, tmax));
+  tnear = tn;
+  return tn <= tf;
+}
+
+__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
+  const bool s = kb < ka;
+  const float tk = s ? kb : ka;
+  kb = s ? ka : kb;
+  ka = tk;
+  const int tv = s ? vb : va;
+  vb = s ? va : vb;
+  va = tv;
+}
+
+// Stack traversal of the 4-wide tree (collapsed from the Karras binary
+// tree), nearest child first.  One node fetch (7 x 16 B) tests all four child
+// boxes; leaf children (one triangle each) are tested at once, so the
+// nearest-hit bound tightens early; hit internal children are ordered by
+// entry distance with a 5-comparator network and all but the nearest pushed,
+// farthest first.  (Postponing leaves until the whole warp holds one -- the
+// while-while form of Aila and Laine -- measured 2x slower with one triangle
+// per leaf: the delayed bound lets rays wander into far subtrees.)
 //   ANY:  any hit in (0, tmax) other than `skip`; returns true on a hit.
 //   else: nearest hit in (0, inf) by (t, original index) -- independent of
 //         the visiting order; prim = original index (-1 = miss), pos = sorted
@@ -132,48 +210,86 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
   pos = -1;
   tb = ANY ? tmax : inf_f();
   if (c.nt == 0) return false;
-  const uint32_t nnodes = (uint32_t)(c.nt > 1 ? c.nt - 1 : 1);
-  const float3 inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const uint32_t n4 = (uint32_t)c.n4;
+  const RaySetup r = ray_setup(o, d, c.span);
   int stack[STACK];
   stack[0] = kDone;
   int sp = 1;
-  int cur = 0;  // internal node, or kDone
-  int64_t budget = c.cap;
+  int cur = 0;  // 4-wide node, or kDone
+  int budget = (int)min(c.cap, (int64_t)0x7fffffff);
   while (cur != kDone) {
     if (--budget < 0) {
       atomicOr(c.err, kErrTimeout);
       return false;
     }
-    if ((uint32_t)cur >= nnodes) {  // never for a built tree
+    if ((uint32_t)cur >= n4) {  // never for a built tree
       atomicOr(c.err, kErrCorrupt);
       return false;
     }
-    const Node* n = c.nodes + cur;
-    float4 a = __ldg(&n->a), b = __ldg(&n->b), cc = __ldg(&n->c), dq = __ldg(&n->d);
-    const int2 dd = make_int2(__float_as_int(b.z), __float_as_int(dq.z));  // child links
-    float tn0, tn1;
-    bool h0 = slab(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tb, tn0);
-    bool h1 = slab(o, inv, cc.x, cc.y, cc.z, cc.w, dq.x, dq.y, tb, tn1);
-    if (h0 && dd.x < 0) {
-      if (leaf_test<ANY>(c, dd.x, o, d, tmax, skip, prim, pos, tb)) return true;
-      h0 = false;
+    const float4* m = &c.nodes4[cur].lox;  // lox loy loz hix hiy hiz link
+    const float4 nx = __ldg(m + r.nx), ny = __ldg(m + r.ny), nz = __ldg(m + r.nz);
+    const float4 fx = __ldg(m + r.fx), fy = __ldg(m + r.fy), fz = __ldg(m + r.fz);
+    const int4 lk = __ldg(reinterpret_cast<const int4*>(m + 6));
+    float k0, k1, k2, k3;
+    int v0 = lk.x, v1 = lk.y, v2 = lk.z, v3 = lk.w;
+    bool h0 = slab4(r, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tb, k0);
+    bool h1 = slab4(r, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tb, k1);
+    bool h2 = slab4(r, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tb, k2);
+    bool h3 = slab4(r, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tb, k3);
+    // hit leaves as a bit mask, tested by one loop: a warp's lanes test their
+    // k-th leaf together instead of one masked test per child slot
+    unsigned lm = (unsigned)(h0 && v0 < 0) | ((unsigned)(h1 && v1 < 0) << 1) | ((unsigned)(h2 && v2 < 0) << 2) |
+                  ((unsigned)(h3 && v3 < 0) << 3);
+    h0 = h0 && !(lm & 1u);
+    h1 = h1 && !(lm & 2u);
+    h2 = h2 && !(lm & 4u);
+    h3 = h3 && !(lm & 8u);
+    while (lm) {
+      const int slot = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int code = slot == 0 ? v0 : slot == 1 ? v1 : slot == 2 ? v2 : v3;
+      if (leaf_test<ANY>(c, code, o, d, tmax, skip, prim, pos, tb)) return true;
     }
-    if (h1 && dd.y < 0) {
-      if (leaf_test<ANY>(c, dd.y, o, d, tmax, skip, prim, pos, tb)) return true;
-      h1 = false;
-    }
-    if (h0 && h1) {
-      bool first0 = tn0 <= tn1;
-      if (sp < STACK) stack[sp++] = first0 ? dd.y : dd.x;
-      else atomicOr(c.err, kErrStack);
-      cur = first0 ? dd.x : dd.y;
-    } else if (h0) {
-      cur = dd.x;
-    } else if (h1) {
-      cur = dd.y;
-    } else {
+    const int cnt = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+    if (cnt == 0) {
       cur = stack[--sp];
+      continue;
     }
+    if (cnt == 1) {
+      cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
+      continue;
+    }
+    if (ANY) {  // any hit: the visiting order does not matter, skip the sort
+      if (sp + cnt - 1 <= STACK) {
+        int first = kDone;
+        if (h3) { first = v3; }
+        if (h2) { if (first != kDone) stack[sp++] = first; first = v2; }
+        if (h1) { if (first != kDone) stack[sp++] = first; first = v1; }
+        if (h0) { if (first != kDone) stack[sp++] = first; first = v0; }
+        cur = first;
+      } else {
+        atomicOr(c.err, kErrStack);
+        cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
+      }
+      continue;
+    }
+    k0 = h0 ? k0 : inf_f();
+    k1 = h1 ? k1 : inf_f();
+    k2 = h2 ? k2 : inf_f();
+    k3 = h3 ? k3 : inf_f();
+    cswap(k0, v0, k1, v1);
+    cswap(k2, v2, k3, v3);
+    cswap(k0, v0, k2, v2);
+    cswap(k1, v1, k3, v3);
+    cswap(k1, v1, k2, v2);
+    if (sp + cnt - 1 <= STACK) {
+      if (cnt == 4) stack[sp++] = v3;
+      if (cnt >= 3) stack[sp++] = v2;
+      stack[sp++] = v1;
+    } else {
+      atomicOr(c.err, kErrStack);
+    }
+    cur = v0;
   }
   return false;
 }
@@ -191,15 +307,41 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
   return traverse<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
 }
 
-// Shadow-ray lift: eps = 1e-4 * |hi - lo| of the scene box (union of the
-// root's two child boxes).
-__device__ __forceinline__ float scene_eps(const Node* nodes, int64_t nt) {
+// Scene box = union of the 4-wide root's child boxes (the same exact min/max
+// as the binary root's box).
+__device__ __forceinline__ void root_box(const Node4* nodes4, float3& lo, float3& hi) {
+  const Node4* r = nodes4;
+  const int4 lk = __ldg(&r->link);
+  const float4 lx = __ldg(&r->lox), ly = __ldg(&r->loy), lz = __ldg(&r->loz);
+  const float4 hx = __ldg(&r->hix), hy = __ldg(&r->hiy), hz = __ldg(&r->hiz);
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  const float LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w}, LZ[4] = {lz.x, lz.y, lz.z, lz.w};
+  const float HX[4] = {hx.x, hx.y, hx.z, hx.w}, HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
+  lo = f3(inf_f(), inf_f(), inf_f());
+  hi = f3(-inf_f(), -inf_f(), -inf_f());
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (l[k] == kEmptyLink) continue;
+    lo = f3(fminf(lo.x, LX[k]), fminf(lo.y, LY[k]), fminf(lo.z, LZ[k]));
+    hi = f3(fmaxf(hi.x, HX[k]), fmaxf(hi.y, HY[k]), fmaxf(hi.z, HZ[k]));
+  }
+}
+
+// Shadow-ray lift: eps = 1e-4 * |hi - lo| of the scene box.
+__device__ __forceinline__ float scene_eps(const Node4* nodes4, int64_t nt) {
   if (nt == 0) return 0.0f;
-  float4 a = __ldg(&nodes[0].a), b = __ldg(&nodes[0].b), c = __ldg(&nodes[0].c), d = __ldg(&nodes[0].d);
-  float3 lo = f3(fminf(a.x, c.x), fminf(a.y, c.y), fminf(a.z, c.z));
-  float3 hi = f3(fmaxf(a.w, c.w), fmaxf(b.x, d.x), fmaxf(b.y, d.y));
+  float3 lo, hi;
+  root_box(nodes4, lo, hi);
   float3 ext = sub3(hi, lo);
   return 1e-4f * sqrtf(dot3(ext, ext));
+}
+
+// Largest |coordinate| of the scene box (scale of the box-test slack).
+__device__ __forceinline__ float scene_span(const Node4* nodes4, int64_t nt) {
+  if (nt == 0) return 0.0f;
+  float3 lo, hi;
+  root_box(nodes4, lo, hi);
+  return fmax3f(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y)), fmaxf(fabsf(lo.z), fabsf(hi.z)));
 }
 
 // ---------------------------------------------------------------------------
