@@ -207,7 +207,7 @@ void free_scene(fire_scene_s* s) {
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->lvl_nodes, s->lvl_aux, s->nodes4, s->q4};
+                  s->leaf_slot4, s->lvl_aux, s->nodes4, s->q4};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -250,8 +250,8 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris, 48 * (size_t)T},
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
-      {(void**)&s->lvl_nodes, 4 * (size_t)std::max<int64_t>(T - 1, 1)},
-      {(void**)&s->lvl_aux, 12 * (size_t)(kMaxHeight + 2) + 16},
+      {(void**)&s->leaf_slot4, 4 * (size_t)T},
+      {(void**)&s->lvl_aux, 8 * (size_t)kMaxDepth4 + 16},
       {(void**)&s->nodes4, 128 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},
   };
@@ -558,24 +558,52 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
           o[code(link(nodes[i], 1))] = (int32_t)i;
         }
       } else {
-        float* o = (float*)host_dst;
-        auto put = [&](int c, const float* b) { memcpy(o + 6 * (int64_t)c, b, 24); };
-        if (T == 1) {
-          put(0, reinterpret_cast<const float*>(&nodes[0]));
-        } else {
-          for (int64_t i = 0; i < ni; ++i) {
-            const float* f = reinterpret_cast<const float*>(&nodes[i]);
-            put(code(link(nodes[i], 0)), f);
-            put(code(link(nodes[i], 1)), f + 8);
+        // The per-frame boxes live in the 4-wide tree: each 4-wide member is
+        // one binary node (its box is copied out); a binary node collapsed
+        // inside a 4-wide node gets the union of its two children (exact
+        // min/max), computed bottom-up over the binary topology.
+        std::vector<Node4> n4(std::max<int64_t>(s->n4, 1));
+        if (int e = get(n4.data(), s->nodes4, 128 * n4.size())) return e;
+        const int64_t ncode = 2 * T - 1;
+        std::vector<float> box(6 * ncode, 0.0f);
+        std::vector<char> have(ncode, 0);
+        for (int64_t q = 0; q < s->n4; ++q) {
+          const int src[4] = {n4[q].src.x, n4[q].src.y, n4[q].src.z, n4[q].src.w};
+          const float* m = reinterpret_cast<const float*>(&n4[q]);
+          for (int k = 0; k < 4; ++k) {
+            if (src[k] < 0 || (src[k] >> 1) >= (int64_t)nodes.size()) continue;
+            int c = code(link(nodes[src[k] >> 1], src[k] & 1));
+            if (c < 0 || c >= ncode) continue;
+            for (int j = 0; j < 6; ++j) box[6 * (int64_t)c + j] = m[4 * j + k];
+            have[c] = 1;
           }
-          float root[6];
-          const float* f = reinterpret_cast<const float*>(&nodes[0]);
-          for (int k = 0; k < 3; ++k) {
-            root[k] = std::fmin(f[k], f[8 + k]);
-            root[3 + k] = std::fmax(f[3 + k], f[11 + k]);
-          }
-          put(0, root);
         }
+        // collapsed internal nodes (they can sit below a member, inside a
+        // 4-wide node): post-order walk over every internal node (explicit
+        // stack; leaves are always 4-wide members)
+        std::vector<std::pair<int64_t, int>> stk;
+        if (T > 1) stk.push_back({0, 0});
+        while (!stk.empty()) {
+          const int64_t c = stk.back().first;
+          if (c < 0 || c >= ni) { stk.pop_back(); continue; }
+          const int a = code(link(nodes[c], 0)), b = code(link(nodes[c], 1));
+          if (a < 0 || a >= ncode || b < 0 || b >= ncode) return set_error(FIRE_ERR_CUDA, "corrupt topology");
+          if (stk.back().second == 0) {
+            stk.back().second = 1;
+            if (a < ni) stk.push_back({a, 0});
+            if (b < ni) stk.push_back({b, 0});
+            continue;
+          }
+          if (!have[c]) {
+            for (int j = 0; j < 3; ++j) {
+              box[6 * c + j] = std::fmin(box[6 * (int64_t)a + j], box[6 * (int64_t)b + j]);
+              box[6 * c + 3 + j] = std::fmax(box[6 * (int64_t)a + 3 + j], box[6 * (int64_t)b + 3 + j]);
+            }
+            have[c] = 1;
+          }
+          stk.pop_back();
+        }
+        memcpy(host_dst, box.data(), 24 * (size_t)ncode);
       }
       return FIRE_OK;
     }

@@ -57,6 +57,7 @@ constexpr int kEmptyLink = (int)0x80000000;
 
 constexpr int kMaxLights = 8;
 constexpr int kMaxHeight = 128;              // tree height is at most 97 (64 + 32 prefix bits + 1)
+constexpr int kMaxDepth4 = 2 * kMaxHeight;   // 4-wide depths (each consumes >= 1 binary level)
 constexpr int kSortBits = 9;                 // 7 passes x 9 bits = 63-bit keys
 constexpr int kSortBins = 1 << kSortBits;
 constexpr int kSortPasses = 7;
@@ -119,9 +120,9 @@ struct fire_scene_s {
   int32_t* leaf_slot = nullptr; // [nt]   2*parent + side
   int32_t* node_slot = nullptr; // [nt-1] 2*parent + side (root -1)
   uint32_t* counters = nullptr; // [nt-1] arrival counters of the build's refit
-  int32_t* lvl_nodes = nullptr; // [nt-1] internal nodes grouped by height (per-frame refit)
-  uint8_t* lvl_aux = nullptr;   // level histogram / cursor (u32) + level offsets (i64) on the device
-  std::vector<int64_t> lvl_off; // host copy: level h = lvl_nodes[lvl_off[h] .. lvl_off[h+1])
+  uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]) + 2 collapse counters
+  std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
+  int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf
   fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree
   int64_t n4 = 0;               // 4-wide nodes in use
   int height4 = 0;              // 4-wide levels

@@ -429,96 +429,6 @@ __global__ void k_refit_build(const float4* __restrict__ rest, const uint16_t* _
 }
 
 // ----------------------------------------------------------------------------
-// Per-frame refit, level-synchronous and without fences: the build groups
-// the internal nodes by height (leaves = 0, node = 1 + max over children);
-// each frame then runs
-//   k_refit_leaves  one thread per leaf: transform, 48-B record, leaf box
-//                   into the parent's slot (no atomics);
-//   k_refit_level   one launch per large level: node box = union of its two
-//                   slots, stored into its parent's slot;
-//   k_refit_top     one block for the small top levels, __syncthreads()
-//                   between levels.
-// Kernel boundaries (and the block barrier) order every read after the
-// writes of the level below; min/max are exact, so the boxes equal the
-// atomic-climb boxes of the build bit for bit.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_refit_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
-                                                      const float* __restrict__ xf, const uint4* __restrict__ sidx,
-                                                      const uint32_t* __restrict__ smat, int64_t nt,
-                                                      float4* __restrict__ tris, Node* __restrict__ nodes,
-                                                      const int32_t* __restrict__ leaf_slot) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nt) return;
-  uint4 id = sidx[i];
-  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
-  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
-  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
-  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
-  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
-  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
-  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
-  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
-  if (nt == 1) {
-    store_child(nodes, 0, lo, hi, ~0, 0);
-    store_child(nodes, 1, lo, hi, ~0, 0);
-    return;
-  }
-  int32_t slot = leaf_slot[i];
-  if (slot < 0 || (slot >> 1) >= nt - 1) return;  // never for a complete topology
-  store_child(nodes + (slot >> 1), slot & 1, lo, hi, (int)~i, 0);
-}
-
-__device__ __forceinline__ void refit_node(Node* nodes, const int32_t* __restrict__ node_slot, int32_t n,
-                                           int64_t nt) {
-  if (n < 0 || n >= nt - 1) return;  // never for a complete topology
-  int32_t slot = node_slot[n];
-  if (slot < 0 || (slot >> 1) >= nt - 1) return;  // root: its box is the two slots themselves
-  float3 lo, hi;
-  int h;
-  load_node_box(nodes + n, lo, hi, h);
-  store_child(nodes + (slot >> 1), slot & 1, lo, hi, n, h);
-}
-
-__global__ void __launch_bounds__(256) k_refit_level(Node* nodes, const int32_t* __restrict__ node_slot,
-                                                     const int32_t* __restrict__ lvl_nodes, int64_t begin,
-                                                     int64_t end, int64_t nt) {
-  const int64_t j = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j < end) refit_node(nodes, node_slot, lvl_nodes[j], nt);
-}
-
-__global__ void __launch_bounds__(1024) k_refit_top(Node* nodes, const int32_t* __restrict__ node_slot,
-                                                    const int32_t* __restrict__ lvl_nodes,
-                                                    const int64_t* __restrict__ lvl_off, int h0, int h1,
-                                                    int64_t nt) {
-  for (int h = h0; h <= h1; ++h) {
-    for (int64_t j = lvl_off[h] + threadIdx.x; j < lvl_off[h + 1]; j += blockDim.x)
-      refit_node(nodes, node_slot, lvl_nodes[j], nt);
-    __syncthreads();
-  }
-}
-
-// Build: height of every internal node (from the child heights the build's
-// refit stored in d.z / d.w) and its level histogram.
-__global__ void k_heights(const Node* __restrict__ nodes, int64_t ni, int32_t* __restrict__ height,
-                          uint32_t* __restrict__ hist, int hmax) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= ni) return;
-  int h = 1 + max(__float_as_int(nodes[n].b.w), __float_as_int(nodes[n].d.w));
-  h = min(max(h, 1), hmax);
-  height[n] = h;
-  atomicAdd(hist + h, 1u);
-}
-
-__global__ void k_scatter_levels(const int32_t* __restrict__ height, int64_t ni, const int64_t* __restrict__ lvl_off,
-                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ lvl_nodes) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= ni) return;
-  int h = height[n];
-  uint32_t p = atomicAdd(cursor + h, 1u);
-  lvl_nodes[lvl_off[h] + p] = (int32_t)n;
-}
-
-// ----------------------------------------------------------------------------
 // 4-wide traversal tree, collapsed from the binary tree at build (one launch
 // per level): a 4-wide node starts from a binary node's two children and
 // opens the internal member with the largest box surface area until it has
@@ -532,7 +442,7 @@ __device__ __forceinline__ float box_area(float4 a, float4 b) {  // sector: lo x
 
 __global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs, uint32_t nin,
                            int32_t* __restrict__ out_pairs, uint32_t* __restrict__ counts, Node4* __restrict__ nodes4,
-                           int64_t cap4) {
+                           int64_t cap4, int32_t* __restrict__ leaf_slot4, int64_t nt) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nin) return;
   const int b = in_pairs[2 * i], q = in_pairs[2 * i + 1];
@@ -565,6 +475,8 @@ __global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __rest
   int out[4];
   for (int k = 0; k < 4; ++k) {
     out[k] = link[k];
+    if (k < m && link[k] < 0 && link[k] != kEmptyLink && (int64_t)~link[k] < nt)
+      leaf_slot4[~link[k]] = 4 * q + k;  // where the per-frame refit puts this leaf's box
     if (k < m && link[k] >= 0) {
       uint32_t q2 = atomicAdd(counts + 1, 1u);   // 4-wide node index
       uint32_t p = atomicAdd(counts + 0, 1u);    // next level's queue slot
@@ -608,6 +520,93 @@ __global__ void __launch_bounds__(256) k_fill4(const Node* __restrict__ nodes, N
   n->hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
   n->hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
   n->hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
+}
+
+// ----------------------------------------------------------------------------
+// Per-frame refit of the 4-wide tree.  The collapse numbers the 4-wide nodes
+// depth by depth, so each depth is a contiguous index range whose children
+// all lie in the next one.
+//   k_refit4_leaves  one thread per leaf: transform, 48-B record, leaf box
+//                    into its 4-wide slot
+//   k_refit4_level   nodes of one depth, deepest first: each internal
+//                    child's box = union of that child's four boxes (unused
+//                    slots hold the inverted infinite box, neutral for
+//                    min/max); the node is rewritten whole
+//   k_refit4_small   one block runs a run of small depths in order,
+//                    __syncthreads() between them
+// Min/max are exact, so every box equals the min/max over its triangles'
+// vertices bit for bit.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_refit4_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                                                       const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                                                       const uint32_t* __restrict__ smat, int64_t nt,
+                                                       float4* __restrict__ tris, Node4* __restrict__ nodes4,
+                                                       const int32_t* __restrict__ leaf_slot4, int64_t n4) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  uint4 id = sidx[i];
+  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
+  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
+  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
+  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
+  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
+  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
+  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
+  const int32_t ls = leaf_slot4[i];
+  if (ls < 0 || (ls >> 2) >= n4) return;  // never for a complete collapse
+  float* n = reinterpret_cast<float*>(nodes4 + (ls >> 2));
+  const int lanes = nt == 1 ? 2 : 1;  // a single triangle sits in two slots of the root
+  for (int k = 0; k < lanes; ++k) {
+    const int c = (ls & 3) + k;
+    n[0 + c] = lo.x;
+    n[4 + c] = lo.y;
+    n[8 + c] = lo.z;
+    n[12 + c] = hi.x;
+    n[16 + c] = hi.y;
+    n[20 + c] = hi.z;
+  }
+}
+
+__device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4) {
+  Node4* n = nodes4 + q;
+  const int4 lk = n->link;
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  if (l[0] < 0 && l[1] < 0 && l[2] < 0 && l[3] < 0) return;  // leaves only: written by the leaf kernel
+  float4 m[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) m[j] = __ldcg(&n->lox + j);
+  float* f = reinterpret_cast<float*>(m);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (l[c] < 0 || l[c] >= n4) continue;
+    const Node4* ch = nodes4 + l[c];
+    float4 a[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = __ldcg(&ch->lox + j);
+    f[0 * 4 + c] = fminf(fminf(a[0].x, a[0].y), fminf(a[0].z, a[0].w));
+    f[1 * 4 + c] = fminf(fminf(a[1].x, a[1].y), fminf(a[1].z, a[1].w));
+    f[2 * 4 + c] = fminf(fminf(a[2].x, a[2].y), fminf(a[2].z, a[2].w));
+    f[3 * 4 + c] = fmaxf(fmaxf(a[3].x, a[3].y), fmaxf(a[3].z, a[3].w));
+    f[4 * 4 + c] = fmaxf(fmaxf(a[4].x, a[4].y), fmaxf(a[4].z, a[4].w));
+    f[5 * 4 + c] = fmaxf(fmaxf(a[5].x, a[5].y), fmaxf(a[5].z, a[5].w));
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) (&n->lox)[j] = m[j];
+}
+
+__global__ void __launch_bounds__(256) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4) {
+  const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < end) refit4_node(nodes4, q, n4);
+}
+
+// depths lvl[d0] .. lvl[d1], deepest (d1) first
+__global__ void __launch_bounds__(1024) k_refit4_small(Node4* nodes4, const int64_t* __restrict__ lvl, int d0, int d1,
+                                                       int64_t n4) {
+  for (int dth = d1; dth >= d0; --dth) {
+    for (int64_t q = lvl[dth] + threadIdx.x; q < lvl[dth + 1]; q += blockDim.x) refit4_node(nodes4, q, n4);
+    __syncthreads();
+  }
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -675,53 +674,40 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   memcpy(&h0, &n0.b.w, 4);
   memcpy(&h1, &n0.d.w, 4);
   s->height = T > 1 ? 1 + std::max(h0, h1) : 1;
-  s->lvl_off.clear();
-  if (T > 1) {
-    // level lists for the per-frame refit (heights 1..H)
-    const int H = std::min(s->height, kMaxHeight);
-    const int64_t ni = T - 1;
-    int32_t* height = reinterpret_cast<int32_t*>(s->counters);  // the counters are free after the build
-    uint32_t* hist = reinterpret_cast<uint32_t*>(s->lvl_aux);
-    if (int e = cuda_check(cudaMemsetAsync(hist, 0, 4 * (kMaxHeight + 2), st), "memset")) return e;
-    k_heights<<<grid_for(ni, 256), 256, 0, st>>>(s->nodes, ni, height, hist, H);
-    std::vector<uint32_t> hh(kMaxHeight + 2);
-    if (int e = cuda_check(cudaMemcpyAsync(hh.data(), hist, 4 * hh.size(), cudaMemcpyDeviceToHost, st), "copy")) return e;
-    if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;
-    s->lvl_off.assign(H + 2, 0);
-    for (int h = 1; h <= H; ++h) s->lvl_off[h + 1] = s->lvl_off[h] + hh[h];
-    int64_t* off_dev = reinterpret_cast<int64_t*>(s->lvl_aux + 4 * (kMaxHeight + 2));
-    uint32_t* cursor = hist;
-    if (int e = cuda_check(cudaMemcpyAsync(off_dev, s->lvl_off.data(), 8 * s->lvl_off.size(), cudaMemcpyHostToDevice, st), "copy")) return e;
-    if (int e = cuda_check(cudaMemsetAsync(cursor, 0, 4 * (kMaxHeight + 2), st), "memset")) return e;
-    k_scatter_levels<<<grid_for(ni, 256), 256, 0, st>>>(height, ni, off_dev, cursor, s->lvl_nodes);
-    if (int e = cuda_check(cudaGetLastError(), "level lists")) return e;
-    if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // off_dev/hist reuse, host vector
-  }
-  // 4-wide traversal tree: collapse level by level from the binary root
+  // 4-wide traversal tree: collapse depth by depth from the binary root; the
+  // nodes of depth L get the contiguous indices [lvl4[L], lvl4[L+1])
   {
     const int64_t cap4 = std::max<int64_t>(T - 1, 1);
     int32_t* qa = s->q4;
     int32_t* qb = s->q4 + 2 * cap4;
-    uint32_t* counts = reinterpret_cast<uint32_t*>(s->lvl_aux + 12 * (kMaxHeight + 2));
+    uint32_t* counts = reinterpret_cast<uint32_t*>(s->lvl_aux + 8 * kMaxDepth4);
     const int32_t root[2] = {0, 0};
-    const uint32_t init[2] = {0u, 1u};  // next-level queue length, 4-wide nodes allocated (root)
+    const uint32_t init[2] = {0u, 1u};  // next-depth queue length, 4-wide nodes allocated (root)
     if (int e = cuda_check(cudaMemcpyAsync(qa, root, sizeof(root), cudaMemcpyHostToDevice, st), "copy")) return e;
     if (int e = cuda_check(cudaMemcpyAsync(counts, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
+    if (int e = cuda_check(cudaMemsetAsync(s->leaf_slot4, 0xff, 4 * T, st), "memset")) return e;
     uint32_t nin = 1, h[2] = {0u, 1u};
-    int levels = 0;
-    while (nin > 0 && levels < 4 * kMaxHeight) {
+    s->lvl4.assign(1, 0);
+    s->lvl4.push_back(1);
+    while (nin > 0 && (int)s->lvl4.size() < kMaxDepth4 - 1) {
       if (int e = cuda_check(cudaMemsetAsync(counts, 0, 4, st), "memset")) return e;
-      k_collapse<<<grid_for(nin, 256), 256, 0, st>>>(s->nodes, qa, nin, qb, counts, s->nodes4, cap4);
+      k_collapse<<<grid_for(nin, 256), 256, 0, st>>>(s->nodes, qa, nin, qb, counts, s->nodes4, cap4,
+                                                     s->leaf_slot4, T);
       if (int e = cuda_check(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, st), "copy")) return e;
       if (int e = cuda_check(cudaStreamSynchronize(st), "collapse")) return e;
       nin = h[0];
+      if (nin > 0) s->lvl4.push_back((int64_t)std::min<uint64_t>(h[1], cap4));
       std::swap(qa, qb);
-      ++levels;
     }
-    s->n4 = std::min<int64_t>(h[1], cap4);
-    s->height4 = levels;
+    if (nin > 0) return set_error(FIRE_ERR_CUDA, "4-wide collapse deeper than supported");
+    s->n4 = s->lvl4.back();
+    s->height4 = (int)s->lvl4.size() - 1;
+    if (int e = cuda_check(cudaMemcpyAsync(s->lvl_aux, s->lvl4.data(), 8 * s->lvl4.size(), cudaMemcpyHostToDevice, st),
+                           "copy"))
+      return e;
     k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
     if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
+    if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // lvl4 host vector copied
   }
   s->built = true;
   return FIRE_OK;
@@ -731,21 +717,24 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) return FIRE_OK;
   prof_begin(s, kStageRefit, st);
-  k_refit_leaves<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
-                                                   s->nodes, s->leaf_slot);
-  if (T > 1) {
-    const int H = (int)s->lvl_off.size() - 2;
-    const int64_t* off_dev = reinterpret_cast<const int64_t*>(s->lvl_aux + 4 * (kMaxHeight + 2));
-    int h = 1;
-    for (; h <= H; ++h) {
-      int64_t n = s->lvl_off[h + 1] - s->lvl_off[h];
-      if (n <= 4096) break;  // the rest is cheaper in one block
-      k_refit_level<<<grid_for(n, 256), 256, 0, st>>>(s->nodes, s->node_slot, s->lvl_nodes, s->lvl_off[h],
-                                                      s->lvl_off[h + 1], T);
+  k_refit4_leaves<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+                                                    s->nodes4, s->leaf_slot4, s->n4);
+  // depths, deepest first: runs of small depths go to one block, large ones get their own launch
+  const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
+  const int64_t* lvl_dev = reinterpret_cast<const int64_t*>(s->lvl_aux);
+  int d = D - 1;
+  while (d >= 0) {
+    const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
+    if (n > 8192) {
+      k_refit4_level<<<grid_for(n, 256), 256, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4);
+      --d;
+      continue;
     }
-    if (h <= H) k_refit_top<<<1, 1024, 0, st>>>(s->nodes, s->node_slot, s->lvl_nodes, off_dev, h, H, T);
+    int d0 = d;
+    while (d0 > 0 && s->lvl4[d0] - s->lvl4[d0 - 1] <= 8192) --d0;
+    k_refit4_small<<<1, 1024, 0, st>>>(s->nodes4, lvl_dev, d0, d, s->n4);
+    d = d0 - 1;
   }
-  k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
   prof_end(s, kStageRefit, st);
   return cuda_check(cudaGetLastError(), "refit kernels");
 }
