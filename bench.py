@@ -107,37 +107,39 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------- roofline
-KERNEL_NAMES = {"refit": "k_refit", "primary": "k_primary", "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
+KERNEL_NAMES = {"refit": "k_refit4_leaves+k_refit4_level+k_refit4_small", "primary": "k_primary",
+                "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
 
 
-def algorithmic_bytes(nt: int, nv: int, samples: int, pixels: int, shadow_rays: int):
-    """Minimum bytes each kernel must move per launch (one frame):
-    refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, sorted
-               index records (16 B) + material (4 B) + leaf slot (4 B) per
-               triangle; write the 48-B triangle record; per internal node
-               write 2 child boxes (48 B), read them back (48 B), counter
-               atomic (8 B) and parent slot (4 B)
-    primary -- read the whole tree once (64 B per internal node + 48 B per
-               triangle) + write a 16-B record per sample + a 32-B queued
-               shadow ray
-    shadow  -- read the whole tree once + read each 32-B queued ray and the
-               4-B skip id + a 4-B visibility update
+def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shadow_rays: int):
+    """Minimum bytes each kernel family must move per frame:
+    refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, the
+               sorted index record (16 B), material (4 B) and 4-wide lane
+               (4 B) per triangle; write the 48-B triangle record and the
+               24-B leaf box; per 4-wide node read its 112-B boxes+links once
+               (by its parent) and write its 96 B of boxes once
+    primary -- read the traversal tree once (128 B per 4-wide node + 48 B
+               per triangle) + write a 16-B record per sample + a 32-B
+               queued shadow ray
+    shadow  -- read the traversal tree once + each 32-B queued ray, its 4-B
+               skip id and a 4-B visibility update
     resolve -- read the 16-B record per sample + 32 B of its triangle for the
                hit frame + write a 16-B pixel."""
-    tree = 64 * max(nt - 1, 0) + 48 * nt
-    return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48) + max(nt - 1, 0) * (48 + 48 + 8 + 4),
+    tree = 128 * n4 + 48 * nt
+    return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48 + 24) + n4 * (112 + 96),
             "primary": tree + 16 * samples + 32 * shadow_rays,
             "shadow": tree + 40 * shadow_rays,
             "resolve": 16 * samples + 32 * samples + 16 * pixels}
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-    the current kernels from the committed ncu summary, else None."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic_frame7m.txt")
+def committed_counter(kind: str, kernel: str):
+    """Per-launch ncu counter of the current kernels from the committed
+    summary: kind "dram_bytes" (dram__bytes_read.sum + dram__bytes_write.sum)
+    or "warp_inst" (smsp__inst_executed.sum); None if not captured."""
+    p = os.path.join(ROOT, "profiles", "counters_frame7m.txt")
     if os.path.exists(p):
         lines = [l for l in open(p) if not l.startswith("#")]
-        return json.loads("".join(lines)).get(kernel)
+        return json.loads("".join(lines)).get(kind, {}).get(kernel)
     return None
 
 
@@ -208,7 +210,7 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------- side runs
 def batch_ratio(fb, torch, reps=5):
-    """Batched (one graph-replayed persistent launch) vs the same 64 frames
+    """Batched (three launches for the whole batch, one CUDA graph) vs the same 64 frames
     rendered by 64 fire_render calls; same images."""
     scenes, cams, cam_scene, lights = sg.batch16()
     G = []
@@ -309,7 +311,7 @@ def main():
     w = sg.workload_frame7m()
     K, W = args.steps, args.warmup
     xf_build = w.motion.xforms()
-    frames = np.stack([w.motion.step() for _ in range(W + 2 * K)])
+    frames = np.stack([w.motion.step() for _ in range(max(W + 2 * K, 99))])
     cam, lights = w.camera, w.lights
     G = fb.Scene.from_numpy(w.scene)
     xf_dev = torch.from_numpy(frames).cuda()
@@ -385,6 +387,22 @@ def main():
     e2e["breakdown_ms"] = dict(zip(["refit_from_host", "render", "d2h_image"], (parts / 3).tolist()))
     G.profile_read()
 
+    # --- the 100-frame sequence of the workload: build at frame 0, refit 1..99 --------
+    G.build(xf_build)
+    seq = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(99)]
+    for i in range(99):
+        evs[i][0].record(stream)
+        G.refit(xf_dev[i])
+        G.render(cam, lights, out=out)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    seq = np.array([a.elapsed_time(b) for a, b in evs])
+    G.profile_read()
+    sequence = {"frames": 99, "median_ms": float(np.median(seq)), "p95_ms": float(np.percentile(seq, 95)),
+                "first_ms": float(seq[0]), "last_ms": float(seq[-1]),
+                "note": "refit + render per frame after a build at frame 0 (tree quality decays with motion)"}
+
     # --- rays traced per frame (shadow rays counted from the G-buffer) ------------
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
     G.render(cam, lights, out=out, gbuf=gb)
@@ -398,17 +416,30 @@ def main():
     trace_ms = avg["primary"] + avg["shadow"] + avg["resolve"]
     grays = (primary_rays + shadow_rays) / (trace_ms * 1e-3) / 1e9
     grays_frame = (primary_rays + shadow_rays) / (ms_frame_rank * 1e-3) / 1e9
-    alg = algorithmic_bytes(w.scene.nt, w.scene.nv, primary_rays, cam.width * cam.height, shadow_rays)
+    alg = algorithmic_bytes(w.scene.nt, w.scene.nv, G.info()["n4"], primary_rays, cam.width * cam.height,
+                            shadow_rays)
     dom = max(avg, key=avg.get)
     peak, peak_kind = load_peaks()
     achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": committed_traffic(dom),
+                "frac": achieved / peak, "traffic": committed_counter("dram_bytes", dom),
                 "peak_source": f"{peak_kind} hbm_gbs (of measured)" if peak_kind == "measured" else "fallback",
                 "algorithmic_bytes": alg[dom],
                 "all_kernels": {k: {"ms": avg[k], "algorithmic_bytes": alg[k],
                                     "gbs": alg[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None}
                                 for k in avg}}
+    # the traversal kernels are issue-bound: warp instructions per launch (ncu)
+    # over the live launch time, against 4 schedulers x 1 warp-inst/clock per SM
+    clocks = clk.summary()
+    inst = committed_counter("warp_inst", dom)
+    if inst:
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_gi = sms * 4 * float(mhz) * 1e6 / 1e9
+        got_gi = inst / (avg[dom] * 1e-3) / 1e9
+        roofline["issue"] = {"warp_inst_per_launch": inst, "achieved": got_gi, "peak": peak_gi,
+                             "unit": "G warp-inst/s", "frac": got_gi / peak_gi,
+                             "peak_source": f"{sms} SMs x 4 schedulers x {float(mhz):.0f} MHz (median under load)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_frame_rank, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -417,7 +448,7 @@ def main():
             "grays_per_s": grays, "grays_per_s_frame": grays_frame,
             "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
             "stages_ms": {**avg, "build_once": build_stats["build"][0]},
-            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e}
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "sequence_100": sequence}
 
     if rank == 0 and not args.no_side:
         line["batched"] = batch_ratio(fb, torch)

@@ -81,7 +81,8 @@ typedef struct {
   int32_t row_begin;     /* render rows [row_begin, row_end) only; 0,0 = all rows.
                             Other rows of out_rgba are left untouched. */
   int32_t row_end;
-  int32_t block_threads; /* threads per block of the trace kernels (0 = default) */
+  int32_t block_threads; /* threads per block of the batch kernels, a multiple of
+                            32 up to 128 (0 = default); fire_render uses 128 */
   int32_t blocks_per_sm; /* persistent grid = SMs x blocks_per_sm (0 = default) */
   int32_t stack_depth;   /* traversal stack entries (0 = sufficient for the tree) */
   int32_t flags;         /* FIRE_RENDER_* bits, 0 by default */
@@ -129,8 +130,9 @@ int fire_scene_destroy(fire_scene s);
 int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nmat);
 
 /* Scene sizes: out[0] = nv, out[1] = nt, out[2] = nmat, out[3] = nbody,
- * out[4] = tree depth (after a build), out[5] = device bytes held. */
-int fire_scene_info(fire_scene s, int64_t* out6);
+ * out[4] = binary tree height (after a build), out[5] = device bytes held,
+ * out[6] = 4-wide traversal nodes, out[7] = 4-wide tree depth. */
+int fire_scene_info(fire_scene s, int64_t* out8);
 
 /* ------------------------------------------------------------------ LBVH */
 
@@ -165,9 +167,11 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
                 const fire_render_opts* opts, float* out_rgba, fire_gbuffer_rec* gbuf,
                 void* stream);
 
-/* Render many cameras over many scenes in one persistent launch, replayed as
- * a CUDA graph when the same batch is rendered again (scenes, cameras, lights,
- * outputs and options unchanged).
+/* Render many cameras over many scenes with three launches for the whole
+ * batch (primary rays of every camera, one shared shadow-ray queue, shading
+ * and resolve), replayed as one CUDA graph while the batch's shape and
+ * buffers are unchanged (descriptor changes are re-uploaded before replay).
+ * Batch-wide limit: sum of W*H*spp below 2^28, else FIRE_ERR_INVALID_ARG.
  *   scenes     host fire_scene[nscenes] (each built)
  *   cams       host fire_camera[ncams]; cam_scene host int32[ncams] (< nscenes)
  *   lights     host fire_light[light_off[nscenes]]; light_off host int32[nscenes+1]

@@ -1,12 +1,17 @@
 // Batched rendering: many cameras over many scenes (uneven triangle counts
-// and resolutions) in ONE persistent launch.  Each warp pulls a 32-sample
-// task from a single atomic counter that spans every camera's tiles, finds
-// its camera by binary search over the task prefix sums, and runs the whole
-// per-sample path (nearest hit, shadow rays, shading, resolve) in registers.
-// The launch (counter reset + kernel) is captured once as a CUDA graph and
-// replayed while the batch is unchanged.  Threads per block, blocks per SM
-// and stack depth are chosen by timing candidates on the first call of each
-// batch shape (autotuner), unless the caller fixes them.
+// and resolutions) in three launches for the whole batch, replayed as one
+// CUDA graph while the batch is unchanged:
+//   k_bprimary  warps pull 32-sample tasks from one counter spanning every
+//               camera's tiles (camera found by binary search over the task
+//               prefix sums); nearest hit into one G-buffer indexed by a
+//               global sample id; shadow rays appended to one dense queue
+//   k_bshadow   the queue, 32 consecutive rays per warp (camera found from
+//               the sample id), any-hit against that camera's scene
+//   k_bresolve  shading + box resolve into each camera's image
+// The per-sample arithmetic is the single-frame path's, so every image
+// equals a separate fire_render bit for bit.  Threads per block, blocks per
+// SM are chosen by timing candidates on the first call of each batch shape
+// (autotuner), unless the caller fixes them.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -25,56 +30,146 @@ struct BatchCam {
   int64_t nt;
   const float* mats;
   float* out;
+  uint32_t* err;          // the scene's sticky error word
+  int64_t sample_base;    // first global sample id of this camera
   CamParams cam;
   LightParams lights;
-  uint32_t* err;  // the scene's sticky error word
   int task_begin;
   int pad;
 };
 
+__device__ __forceinline__ int find_task_cam(const BatchCam* __restrict__ cams, int ncams, int task) {
+  int lo = 0, hi = ncams - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cams[mid].task_begin <= task) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_sample_cam(const BatchCam* __restrict__ cams, int ncams, int64_t sid) {
+  int lo = 0, hi = ncams - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cams[mid].sample_base <= sid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int STACK>
-__global__ void __launch_bounds__(256) k_batch(const BatchCam* __restrict__ cams, int ncams, int ntasks,
-                                               uint32_t* ctrl, int64_t cap) {
+__global__ void __launch_bounds__(128) k_bprimary(const BatchCam* __restrict__ cams, int ncams, int ntasks,
+                                                  uint32_t* ctrl, int4* __restrict__ gbuf, float4* __restrict__ jobs,
+                                                  int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lower = (1u << lane) - 1u;
+  while (true) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(ctrl + 0, 1);
+    task = __shfl_sync(kFull, task, 0);
+    if (task >= ntasks) return;
+    const BatchCam& bc = cams[find_task_cam(cams, ncams, task)];
+    TaskGrid g = make_grid(bc.cam.W, 0, bc.cam.H, bc.cam.spp);
+    int x, y, k;
+    const bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
+    TraceCtx c{bc.nodes4, bc.n4, scene_span(bc.nodes4, bc.nt), bc.tris, bc.nt, cap, bc.err};
+    const float eps = scene_eps(bc.nodes4, bc.nt);
+    int prim = -1, pos = -1;
+    float t = inf_f();
+    int64_t sid = 0;
+    float3 o = f3(bc.cam.ox, bc.cam.oy, bc.cam.oz), n = f3(0, 0, 0), po = f3(0, 0, 0);
+    if (valid) {
+      float3 d = cam_dir(bc.cam, x, y, k);
+      trace_nearest<STACK>(c, o, d, prim, pos, t);
+      sid = bc.sample_base + ((int64_t)y * bc.cam.W + x) * bc.cam.spp + k;
+      if (prim >= 0) {
+        float4 B = __ldg(bc.tris + 3 * (int64_t)pos + 1), C = __ldg(bc.tris + 3 * (int64_t)pos + 2);
+        hit_frame(B, C, o, d, t, eps, n, po);
+      }
+    }
+    uint32_t cast = 0;
+    for (int j = 0; j < bc.lights.n; ++j) {
+      float3 l = f3(0, 0, 0);
+      float E, tmax = 0.0f;
+      bool want = false;
+      if (prim >= 0) {
+        light_vec(bc.lights, j, bc.lights.I[j], po, l, E, tmax);
+        want = dot3(n, l) > 0.0f;
+      }
+      unsigned m = __ballot_sync(kFull, want);
+      if (m == 0) continue;
+      uint32_t base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(ctrl + 4, (uint32_t)__popc(m));
+      base = __shfl_sync(kFull, base, __ffs(m) - 1);
+      if (want) {
+        cast |= 1u << (8 + j);
+        int64_t slot = (int64_t)base + __popc(m & lower);
+        jobs[2 * slot] = make_float4(po.x, po.y, po.z, tmax);
+        jobs[2 * slot + 1] = make_float4(l.x, l.y, l.z, __int_as_float((int)(sid * 8 + j)));
+      }
+    }
+    if (valid) gbuf[sid] = make_int4(prim, __float_as_int(t), (int)cast, pos);
+  }
+}
+
+template <int STACK>
+__global__ void __launch_bounds__(128) k_bshadow(const BatchCam* __restrict__ cams, int ncams, uint32_t* ctrl,
+                                                 int4* gbuf, const float4* __restrict__ jobs, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t njobs = ctrl[4];
+  while (true) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(ctrl + 5, 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= njobs) return;
+    uint32_t jb = base + lane;
+    if (jb < njobs) {
+      float4 A = jobs[2 * (int64_t)jb], B = jobs[2 * (int64_t)jb + 1];
+      int sj = __float_as_int(B.w);
+      int64_t sid = sj >> 3;
+      const BatchCam& bc = cams[find_sample_cam(cams, ncams, sid)];
+      TraceCtx c{bc.nodes4, bc.n4, scene_span(bc.nodes4, bc.nt), bc.tris, bc.nt, cap, bc.err};
+      int skip = gbuf[sid].x;
+      if (!trace_any<STACK>(c, f3(A.x, A.y, A.z), f3(B.x, B.y, B.z), A.w, skip))
+        atomicOr(reinterpret_cast<unsigned*>(&gbuf[sid].z), 1u << (sj & 7));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_bresolve(const BatchCam* __restrict__ cams, int ncams, int ntasks,
+                                                  uint32_t* ctrl, const int4* __restrict__ gbuf) {
   const int lane = threadIdx.x & 31;
   while (true) {
     int task = 0;
-    if (lane == 0) task = atomicAdd(ctrl, 1);
+    if (lane == 0) task = atomicAdd(ctrl + 1, 1);
     task = __shfl_sync(kFull, task, 0);
     if (task >= ntasks) return;
-    int lo = 0, hi = ncams - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (cams[mid].task_begin <= task) lo = mid; else hi = mid - 1;
-    }
-    const BatchCam& bc = cams[lo];
+    const BatchCam& bc = cams[find_task_cam(cams, ncams, task)];
     TaskGrid g = make_grid(bc.cam.W, 0, bc.cam.H, bc.cam.spp);
     int x, y, k;
-    bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
-    TraceCtx c{bc.nodes4, bc.n4, scene_span(bc.nodes4, bc.nt), bc.tris, bc.nt, cap, bc.err};
+    const bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
     float3 rad = f3(0.0f, 0.0f, 0.0f);
     int hit = 0;
     if (valid) {
-      float3 o = f3(bc.cam.ox, bc.cam.oy, bc.cam.oz);
-      float3 d = cam_dir(bc.cam, x, y, k);
-      int prim, pos;
-      float t;
-      trace_nearest<STACK>(c, o, d, prim, pos, t);
-      if (prim >= 0) {
+      const int64_t sid = bc.sample_base + ((int64_t)y * bc.cam.W + x) * bc.cam.spp + k;
+      const int4 rr = gbuf[sid];
+      if (rr.x >= 0) {
         hit = 1;
         const float eps = scene_eps(bc.nodes4, bc.nt);
-        float4 B = __ldg(bc.tris + 3 * (int64_t)pos + 1), C = __ldg(bc.tris + 3 * (int64_t)pos + 2);
+        float3 o = f3(bc.cam.ox, bc.cam.oy, bc.cam.oz);
+        float3 d = cam_dir(bc.cam, x, y, k);
+        float4 B = __ldg(bc.tris + 3 * (int64_t)rr.w + 1), C = __ldg(bc.tris + 3 * (int64_t)rr.w + 2);
         float3 n, po;
-        hit_frame(B, C, o, d, t, eps, n, po);
+        hit_frame(B, C, o, d, __int_as_float(rr.y), eps, n, po);
         float3 v = neg3(d);
         const float* mp = bc.mats + 5 * (int64_t)__float_as_uint(B.w);
         float ar = __ldg(mp), ag = __ldg(mp + 1), ab = __ldg(mp + 2), rough = __ldg(mp + 3), metal = __ldg(mp + 4);
         for (int j = 0; j < bc.lights.n; ++j) {
+          if (!((rr.z >> j) & 1)) continue;
           float3 l;
           float E, tmax;
           light_vec(bc.lights, j, bc.lights.I[j], po, l, E, tmax);
           float ndl = dot3(n, l);
           if (!(ndl > 0.0f)) continue;
-          if (trace_any<STACK>(c, po, l, tmax, prim)) continue;
           float3 f = brdf(n, v, l, ar, ag, ab, rough, metal);
           float En = E * ndl;
           rad = f3(rad.x + f.x * En, rad.y + f.y * En, rad.z + f.z * En);
@@ -112,9 +207,23 @@ struct BatchCache {
   BatchCam* d_cams = nullptr;
   size_t cap_cams = 0;
   uint32_t* d_ctrl = nullptr;
+  int4* d_gbuf = nullptr;
+  size_t cap_samples = 0;
+  float4* d_jobs = nullptr;
+  size_t cap_jobs = 0;
   std::vector<unsigned char> last_bytes;
-  TuneCfg last_cfg;
-  int last_ncams = 0, last_ntasks = 0;
+  // everything the captured graph bakes in besides the descriptor contents
+  struct Key {
+    TuneCfg cfg;
+    int ncams = 0, ntasks = 0;
+    int64_t maxjobs = 0, cap = 0;
+    const void* ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool operator==(const Key& k) const {
+      return cfg.threads == k.cfg.threads && cfg.bps == k.cfg.bps && cfg.stack == k.cfg.stack &&
+             ncams == k.ncams && ntasks == k.ntasks && maxjobs == k.maxjobs && cap == k.cap &&
+             memcmp(ptrs, k.ptrs, sizeof(ptrs)) == 0;
+    }
+  } last_key;
   cudaGraphExec_t exec = nullptr;
   std::map<std::vector<int64_t>, TuneCfg> tuned;
   int32_t info[4] = {0, 0, 0, 0};
@@ -125,25 +234,44 @@ BatchCache& cache() {
   return *c;
 }
 
-template <int STACK>
-void launch_batch(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, uint32_t* ctrl,
-                  int64_t cap, cudaStream_t st) {
+template <typename K>
+int grid_of(K kernel, const TuneCfg& t, int64_t work_warps) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<STACK>, t.threads, 0) != cudaSuccess || occ < 1)
-    occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, t.threads, 0) != cudaSuccess || occ < 1) occ = 1;
   int bps = t.bps > 0 ? std::min(t.bps, occ) : occ;
   int warps = t.threads / 32;
-  int grid = std::max(1, std::min(sm_count() * bps, (ntasks + warps - 1) / warps));
-  k_batch<STACK><<<grid, t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, cap);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * bps, (work_warps + warps - 1) / warps));
 }
 
-void launch_cfg(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, uint32_t* ctrl, int64_t cap,
-                cudaStream_t st) {
-  cudaMemsetAsync(ctrl, 0, 4, st);
-  if (t.stack <= 8) launch_batch<8>(t, cams, ncams, ntasks, ctrl, cap, st);
-  else if (t.stack <= 32) launch_batch<32>(t, cams, ncams, ntasks, ctrl, cap, st);
-  else if (t.stack <= 64) launch_batch<64>(t, cams, ncams, ntasks, ctrl, cap, st);
-  else launch_batch<128>(t, cams, ncams, ntasks, ctrl, cap, st);
+template <int STACK>
+void launch_batch(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, int64_t maxjobs, uint32_t* ctrl,
+                  int4* gbuf, float4* jobs, int64_t cap, cudaStream_t st) {
+  cudaMemsetAsync(ctrl, 0, 32, st);
+  k_bprimary<STACK><<<grid_of(k_bprimary<STACK>, t, ntasks), t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, gbuf,
+                                                                                   jobs, cap);
+  if (maxjobs > 0)
+    k_bshadow<STACK><<<grid_of(k_bshadow<STACK>, t, (maxjobs + 31) / 32), t.threads, 0, st>>>(cams, ncams, ctrl, gbuf,
+                                                                                             jobs, cap);
+  k_bresolve<<<grid_of(k_bresolve, t, ntasks), t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, gbuf);
+}
+
+void launch_cfg(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, int64_t maxjobs, uint32_t* ctrl,
+                int4* gbuf, float4* jobs, int64_t cap, cudaStream_t st) {
+  if (t.stack <= 8) launch_batch<8>(t, cams, ncams, ntasks, maxjobs, ctrl, gbuf, jobs, cap, st);
+  else if (t.stack <= 32) launch_batch<32>(t, cams, ncams, ntasks, maxjobs, ctrl, gbuf, jobs, cap, st);
+  else if (t.stack <= 64) launch_batch<64>(t, cams, ncams, ntasks, maxjobs, ctrl, gbuf, jobs, cap, st);
+  else launch_batch<128>(t, cams, ncams, ntasks, maxjobs, ctrl, gbuf, jobs, cap, st);
+}
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t need, const char* what) {
+  if (*cap >= need) return FIRE_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaError_t e = dev_alloc((void**)p, need * sizeof(T), nullptr)) return cuda_check(e, what);
+  *cap = need;
+  return FIRE_OK;
 }
 
 }  // namespace
@@ -162,8 +290,8 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
   std::lock_guard<std::mutex> lk(C.mu);
   std::vector<BatchCam> h(ncams);
   std::vector<int64_t> shape;
-  int ntasks = 0, maxh = 0;
-  int64_t cap = 64;  // safety bound: a ray visits each node at most once
+  int ntasks = 0, maxh = 0, maxl = 0;
+  int64_t cap = 64, nsamples = 0;
   for (int i = 0; i < ncams; ++i) {
     fire_scene_s* s = scenes[cam_scene[i]];
     BatchCam& b = h[i];
@@ -180,9 +308,12 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     if (e) return e;
     b.err = s->ctrl + 8;
     b.task_begin = ntasks;
+    b.sample_base = nsamples;
     TaskGrid g = make_grid(b.cam.W, 0, b.cam.H, b.cam.spp);
     ntasks += g.tiles_x * g.tiles_y;
+    nsamples += (int64_t)b.cam.W * b.cam.H * b.cam.spp;
     maxh = std::max(maxh, stack_need(s));
+    maxl = std::max(maxl, b.lights.n);
     cap = std::max(cap, 2 * s->nt + 64);
     shape.push_back(s->nt);
     shape.push_back(b.cam.W);
@@ -191,17 +322,13 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     shape.push_back(b.lights.n);
   }
   if (ncams == 0 || ntasks == 0) return FIRE_OK;
-  // cameras whose image has no tasks still work: binary search skips them
-  if ((size_t)ncams > C.cap_cams) {
-    if (C.d_cams) cudaFree(C.d_cams);
-    C.d_cams = nullptr;
-    C.cap_cams = 0;
-    if (cudaError_t e = dev_alloc((void**)&C.d_cams, sizeof(BatchCam) * ncams, nullptr)) {
-      return cuda_check(e, "batch descriptors");
-    }
-    C.cap_cams = ncams;
-    C.last_bytes.clear();
-  }
+  if (nsamples >= ((int64_t)1 << 28)) return set_error(FIRE_ERR_INVALID_ARG, "batch has 2^28 samples or more");
+  const int64_t maxjobs = nsamples * maxl;
+  const BatchCam* old_cams = C.d_cams;
+  if (int e = grow(&C.d_cams, &C.cap_cams, (size_t)ncams, "batch descriptors")) return e;
+  if (C.d_cams != old_cams) C.last_bytes.clear();
+  if (int e = grow(&C.d_gbuf, &C.cap_samples, (size_t)nsamples, "batch records")) return e;
+  if (int e = grow(&C.d_jobs, &C.cap_jobs, (size_t)std::max<int64_t>(2 * maxjobs, 2), "batch shadow queue")) return e;
   if (!C.d_ctrl) {
     if (cudaError_t e = dev_alloc((void**)&C.d_ctrl, 64, nullptr)) return cuda_check(e, "batch ctrl");
     cudaMemsetAsync(C.d_ctrl, 0, 64, st);
@@ -218,7 +345,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
   fire_render_opts o{};
   if (opts) o = *opts;
   if (o.stack_depth > 0 && o.stack_depth < maxh)
-    return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below a scene's tree height");
+    return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below a scene's tree requirement");
   int need = stack_for_height(maxh, o.stack_depth);
   TuneCfg cfg;
   cfg.stack = need;
@@ -236,22 +363,20 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
       cudaEventCreate(&e1);
       float best = 1e30f;
       TuneCfg bestc = cfg;
-      const int thr_list[3] = {64, 128, 256};
-      const int bps_list[5] = {1, 2, 4, 8, 0};
-      const int stk_list[1] = {need};  // deeper stacks are never faster
-      for (int stk : stk_list)
-        for (int thr : thr_list)
-          for (int bps : bps_list) {
-            TuneCfg t{thr, bps, stk};
-            launch_cfg(t, C.d_cams, ncams, ntasks, C.d_ctrl, cap, st);  // warm
-            cudaEventRecord(e0, st);
-            launch_cfg(t, C.d_cams, ncams, ntasks, C.d_ctrl, cap, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; bestc = t; }
-          }
+      const int thr_list[2] = {64, 128};
+      const int bps_list[4] = {2, 4, 8, 0};
+      for (int thr : thr_list)
+        for (int bps : bps_list) {
+          TuneCfg t{thr, bps, need};
+          launch_cfg(t, C.d_cams, ncams, ntasks, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);  // warm
+          cudaEventRecord(e0, st);
+          launch_cfg(t, C.d_cams, ncams, ntasks, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) { best = ms; bestc = t; }
+        }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       if (int e = cuda_check(cudaGetLastError(), "autotune")) return e;
@@ -264,10 +389,18 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
   C.info[1] = cfg.bps;
   C.info[2] = cfg.stack;
   C.info[3] = tuned_now ? 1 : 0;
-  // graph: (re)capture when the launch shape changed
-  bool relaunch = C.exec && C.last_cfg.threads == cfg.threads && C.last_cfg.bps == cfg.bps &&
-                  C.last_cfg.stack == cfg.stack && C.last_ncams == ncams && C.last_ntasks == ntasks;
-  if (!relaunch) {
+  // graph: (re)capture when the launch shape or a scratch buffer changed
+  BatchCache::Key key;
+  key.cfg = cfg;
+  key.ncams = ncams;
+  key.ntasks = ntasks;
+  key.maxjobs = maxjobs;
+  key.cap = cap;
+  key.ptrs[0] = C.d_cams;
+  key.ptrs[1] = C.d_ctrl;
+  key.ptrs[2] = C.d_gbuf;
+  key.ptrs[3] = C.d_jobs;
+  if (!(C.exec && C.last_key == key)) {
     sm_count();  // cached before capture
     if (C.exec) {
       cudaGraphExecDestroy(C.exec);
@@ -277,16 +410,14 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     if (int e = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream")) return e;
     cudaGraph_t graph;
     cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    launch_cfg(cfg, C.d_cams, ncams, ntasks, C.d_ctrl, cap, cs);
+    launch_cfg(cfg, C.d_cams, ncams, ntasks, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (int e = cuda_check(ce, "graph capture")) return e;
     ce = cudaGraphInstantiate(&C.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (int e = cuda_check(ce, "graph instantiate")) return e;
-    C.last_cfg = cfg;
-    C.last_ncams = ncams;
-    C.last_ntasks = ntasks;
+    C.last_key = key;
   }
   return cuda_check(cudaGraphLaunch(C.exec, st), "graph launch");
 }

@@ -344,15 +344,17 @@ int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nm
   return upload_mats(s, mats, s->last_stream);
 }
 
-int fire_scene_info(fire_scene s, int64_t* out6) {
+int fire_scene_info(fire_scene s, int64_t* out8) {
   g_err.clear();
-  if (!s || !out6) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
-  out6[0] = s->nv;
-  out6[1] = s->nt;
-  out6[2] = s->nmat;
-  out6[3] = s->nbody;
-  out6[4] = s->height;
-  out6[5] = (int64_t)s->bytes;
+  if (!s || !out8) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  out8[0] = s->nv;
+  out8[1] = s->nt;
+  out8[2] = s->nmat;
+  out8[3] = s->nbody;
+  out8[4] = s->height;
+  out8[5] = (int64_t)s->bytes;
+  out8[6] = s->n4;
+  out8[7] = s->height4;
   return FIRE_OK;
 }
 
@@ -478,7 +480,7 @@ int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_came
     if (!outs[i]) return set_error(FIRE_ERR_INVALID_ARG, "NULL output");
   }
   if (opts && (opts->row_begin || opts->row_end || opts->flags || opts->stack_depth < 0 || opts->stack_depth > 128 ||
-               opts->blocks_per_sm < 0 || opts->block_threads < 0 || opts->block_threads > 256 ||
+               opts->blocks_per_sm < 0 || opts->block_threads < 0 || opts->block_threads > 128 ||
                (opts->block_threads % 32) != 0))
     return set_error(FIRE_ERR_INVALID_ARG, "invalid batch options");
   return render_batch(scenes, nscenes, cams, cam_scene, ncams, lights, light_off, outs, opts, as_stream(stream));

@@ -195,9 +195,10 @@ class Scene:
         _check(lib().fire_scene_set_materials(self.h, C.cast(self._mats, C.c_void_p), len(mats)))
 
     def info(self) -> dict:
-        out = (C.c_int64 * 6)()
+        out = (C.c_int64 * 8)()
         _check(lib().fire_scene_info(self.h, out))
-        return dict(nv=out[0], nt=out[1], nmat=out[2], nbody=out[3], height=out[4], bytes=out[5])
+        return dict(nv=out[0], nt=out[1], nmat=out[2], nbody=out[3], height=out[4], bytes=out[5],
+                    n4=out[6], depth4=out[7])
 
     def build(self, xforms, stream=None):
         """xforms: [nbody,12] f32 -- a CUDA tensor (device) or numpy/CPU tensor (host)."""
