@@ -196,11 +196,12 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
 //   df/dalb = (1-F)(1-m)/pi + (D vis - (1-m) alb/pi)(1 - w5) m
 //   df/dm   = (D vis - (1-m) alb/pi)(1 - w5)(alb - 0.04) - (1-F) alb/pi
 //   df/dr   = F (dD/dr vis + D dvis/dr)
-// Per-sample terms and per-warp sums (shuffles, when the warp shares one
-// material) are FP32; everything above is FP64: shared-memory atomics per
-// block, global atomics into `acc` (nmat*5 + nlights doubles, zero on entry),
-// and the last block to finish adds `acc` into the FP32 outputs and zeroes it.
-__global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
+// Per-sample terms and per-warp sums (shuffles; material terms per group of
+// lanes sharing a material) are FP32; everything above is FP64: shared-memory
+// atomics per block, global atomics into `acc` (nmat*5 + nlights doubles,
+// zero on entry), and the last block to finish adds `acc` into the FP32
+// outputs and zeroes it.
+__global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
                                                    const float* dL, float* dparams, float* dinten,
                                                    double* acc) {
   extern __shared__ double sacc[];  // [nmat*5 + nlights]
@@ -253,13 +254,13 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
           float nh = fmaxf(dot3(n, h), 0.0f), vh = fmaxf(dot3(v, h), 0.0f);
           float aa = r * r, a2 = aa * aa;
           float s1 = (1.0f - nh) * (1.0f + nh), nh2a2 = (nh * nh) * a2;
-          float dd = s1 + nh2a2;
-          float D = a2 / ((kPi * dd) * dd);
-          float dD_dr = (s1 - nh2a2) / (kPi * dd * dd * dd) * (4.0f * r * r * r);
+          float rdd = 1.0f / (s1 + nh2a2);
+          float D = a2 * kInvPi * rdd * rdd;
+          float dD_dr = (s1 - nh2a2) * kInvPi * (rdd * rdd * rdd) * (4.0f * r * r * r);
           float kk = (r + 1.0f) * (r + 1.0f) * 0.125f, dk_dr = (r + 1.0f) * 0.25f;
-          float gL = fmaf(nl, 1.0f - kk, kk), gV = fmaf(nv, 1.0f - kk, kk);
-          float vis = 0.25f / (gL * gV);
-          float dvis_dr = -vis * ((1.0f - nl) / gL + (1.0f - nv) / gV) * dk_dr;
+          float rgL = 1.0f / fmaf(nl, 1.0f - kk, kk), rgV = 1.0f / fmaf(nv, 1.0f - kk, kk);
+          float vis = 0.25f * rgL * rgV;
+          float dvis_dr = -vis * ((1.0f - nl) * rgL + (1.0f - nv) * rgV) * dk_dr;
           float w = 1.0f - vh, w5 = (w * w) * (w * w) * w;
           float wI = E * ndl;  // g_j (n.l)
 #pragma unroll
@@ -280,23 +281,32 @@ __global__ void __launch_bounds__(128) k_shade_bwd(RenderArgs a, TaskGrid g, int
         }
       }
     }
-    // warp aggregation when the whole warp shares one material
-    unsigned peers = __match_any_sync(kFull, mat);
-    if (peers == kFull) {
+    // FP32 warp sums: the light terms over the whole warp, the material
+    // terms over each group of lanes sharing a material (one pass per
+    // distinct material); one FP64 shared atomic per sum, by one lane (FP64
+    // instructions run at a small fraction of the FP32 rate)
+    unsigned todo = __ballot_sync(kFull, mat >= 0);
+    if (todo == 0) continue;
+    for (int j = 0; j < a.lights.n; ++j) {
+      float v = gl[j];
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+      if (lane == 0) atomicAdd(&sacc[nm5 + j], (double)v);
+    }
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int m = __shfl_sync(kFull, mat, leader);
+      const bool mine = mat == m;
+      todo &= ~__ballot_sync(kFull, mine);
+      float v[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q)
-        for (int off = 16; off; off >>= 1) gm[q] += __shfl_xor_sync(kFull, gm[q], off);
-      for (int j = 0; j < a.lights.n; ++j)
-        for (int off = 16; off; off >>= 1) gl[j] += __shfl_xor_sync(kFull, gl[j], off);
-      if (lane == 0 && mat >= 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], (double)gm[q]);
-        for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], (double)gl[j]);
+      for (int q = 0; q < 5; ++q) {
+        v[q] = mine ? gm[q] : 0.0f;
+        for (int off = 16; off; off >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], off);
       }
-    } else if (mat >= 0) {
+      if (lane == leader) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * mat + q], (double)gm[q]);
-      for (int j = 0; j < a.lights.n; ++j) atomicAdd(&sacc[nm5 + j], (double)gl[j]);
+        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * m + q], (double)v[q]);
+      }
     }
   }
   __syncthreads();
@@ -407,7 +417,7 @@ int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, con
                            "smem attr"))
       return e;
   }
-  int grid = std::max(1, std::min(sm_count() * 4, (ntasks + 3) / 4));
+  int grid = std::max(1, std::min(sm_count() * occupancy_blocks(k_shade_bwd, 128, smem), (ntasks + 3) / 4));
   size_t need = (size_t)nacc;
   if (s->bwd_partials_n < need) {
     if (s->bwd_partials) cudaFree(s->bwd_partials);
@@ -436,7 +446,8 @@ int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, 
   if (ntasks == 0) return FIRE_OK;
   const int nacc = a.mats.n * 5 + a.lights.n;
   if (nacc > 6144) return set_error(FIRE_ERR_INVALID_ARG, "too many parameters for the scratch backward");
-  int grid = std::max(1, std::min(sm_count() * 4, (ntasks + 3) / 4));
+  int grid = std::max(1, std::min(sm_count() * occupancy_blocks(k_shade_bwd, 128, sizeof(double) * nacc),
+                                  (ntasks + 3) / 4));
   k_shade_bwd<<<grid, 128, sizeof(double) * nacc, st>>>(a, g, ntasks, inten, dL, dparams, dinten, acc);
   return cuda_check(cudaGetLastError(), "k_shade_bwd");
 }
