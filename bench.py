@@ -343,6 +343,7 @@ def main():
             dist.barrier()
     t_ms = e0.elapsed_time(e1)
     stages = G.profile_read()
+    primary_info = G.render_info()
     launches = sum(n for (_, n) in stages.values())
     assert G.sync_status() == 0
     t_ms = max_over_ranks(t_ms, device="cuda")
@@ -412,7 +413,7 @@ def main():
     hits = int((gb[:, 0] >= 0).sum().item())
     del gb
 
-    avg = {k: stages[k][0] / max(1, stages[k][1]) for k in ("refit", "primary", "shadow", "resolve")}
+    avg = {k: stages[k][0] / K for k in ("refit", "primary", "shadow", "resolve")}  # one of each per frame
     trace_ms = avg["primary"] + avg["shadow"] + avg["resolve"]
     grays = (primary_rays + shadow_rays) / (trace_ms * 1e-3) / 1e9
     grays_frame = (primary_rays + shadow_rays) / (ms_frame_rank * 1e-3) / 1e9
@@ -448,6 +449,8 @@ def main():
             "grays_per_s": grays, "grays_per_s_frame": grays_frame,
             "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
             "stages_ms": {**avg, "build_once": build_stats["build"][0]},
+            "primary_pass": {"method": "raster" if primary_info["raster"] else "traversal",
+                             "fallback_bits": primary_info["fallback"], "pieces": primary_info["pieces"]},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "sequence_100": sequence}
 
     if rank == 0 and not args.no_side:

@@ -94,6 +94,20 @@ typedef struct {
  * access ever leaves the stack. */
 #define FIRE_RENDER_ALLOW_SHALLOW_STACK 1
 
+/* Primary visibility method (the result is the same either way, bit for
+ * bit: the nearest hit with the (t, original index) tie-break).  By default
+ * fire_render traverses the tree (FIRE_RENDER_TRACE_PRIMARY states it).
+ * FIRE_RENDER_RASTER_PRIMARY rasterises instead, like the paper's main pass
+ * (§IV-A-1): one pass over the triangles, each testing the samples of its
+ * conservative screen footprint with the same ray-triangle test, nearest
+ * hit kept per sample by a 64-bit atomic minimum; it needs 24 B per sample
+ * of extra scratch (allocated on first use) and hands a frame back to
+ * traversal, on the device, when a footprint cannot be bounded (geometry
+ * touching the camera, a full work list).  The two flags exclude each
+ * other. */
+#define FIRE_RENDER_TRACE_PRIMARY 2
+#define FIRE_RENDER_RASTER_PRIMARY 4
+
 /* One G-buffer record per sample, sample id = (y*W + x)*spp + k:
  * prim = original triangle index of the nearest hit (-1 = miss), t = hit
  * distance along the unit ray, vis = bit j set if light j was cast
@@ -133,6 +147,15 @@ int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nm
  * out[4] = binary tree height (after a build), out[5] = device bytes held,
  * out[6] = 4-wide traversal nodes, out[7] = 4-wide tree depth. */
 int fire_scene_info(fire_scene s, int64_t* out8);
+
+/* Facts of the scene's last fire_render; waits for the stream it ran on.
+ *   out4 host int64[4]: out[0] = 1 if its primary pass rasterised, 0 if it
+ *   traversed; out[1] = raster fallback reasons (bits: 1 geometry next to
+ *   the camera, 2 non-finite projection, 4 a raster work list full; any bit means
+ *   the traversal produced the primary hits); out[2] = raster pieces
+ *   queued; out[3] = shadow rays queued.
+ * Before any render -> zeros. */
+int fire_render_info(fire_scene s, int64_t* out4);
 
 /* ------------------------------------------------------------------ LBVH */
 
@@ -253,12 +276,13 @@ int fire_debug_set_iteration_cap(fire_scene s, int64_t cap);
 int fire_debug_fail_alloc(int32_t nth);
 
 /* Stage timing with CUDA events recorded on the launching stream around each
- * kernel of the scene's calls (off by default; negligible cost when on).
- * Stages: 0 refit, 1 primary rays, 2 shadow rays + shading + resolve,
- * 3 build (whole), 4 G-buffer shading, 5 shading backward.
+ * stage of the scene's calls (off by default; negligible cost when on).
+ * Stages: 0 refit, 1 primary pass (raster or traversal), 2 shadow rays,
+ * 3 build (up to the binary tree; the 4-wide collapse is not included),
+ * 4 G-buffer shading, 5 shading backward, 6 shading + resolve.
  * fire_profile_read synchronises the pending events and returns, per stage,
- * the summed milliseconds and the number of launches since the last read
- * (then resets). */
+ * the summed milliseconds and the number of kernel launches since the last
+ * read (then resets). */
 int fire_profile_enable(fire_scene s, int32_t enable);
 int fire_profile_read(fire_scene s, double* ms8, int64_t* launches8);
 

@@ -143,7 +143,7 @@ int check_mats(const fire_material* m, int n) {
 // oldest pairs are synchronised only when many are pending or on read).
 // ---------------------------------------------------------------------------
 struct Profiler {
-  struct Pending { int stage; cudaEvent_t a, b; };
+  struct Pending { int stage, launches; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::deque<Pending> pending;
   cudaEvent_t open[kStages] = {};
@@ -167,7 +167,7 @@ struct Profiler {
       cudaEventSynchronize(p.b);
       cudaEventElapsedTime(&t, p.a, p.b);
       ms[p.stage] += t;
-      n[p.stage] += 1;
+      n[p.stage] += p.launches;
       pool.push_back(p.a);
       pool.push_back(p.b);
     }
@@ -188,13 +188,13 @@ void prof_begin(fire_scene_s* s, int stage, cudaStream_t st) {
   cudaEventRecord(P->open[stage], st);
 }
 
-void prof_end(fire_scene_s* s, int stage, cudaStream_t st) {
+void prof_end(fire_scene_s* s, int stage, cudaStream_t st, int launches) {
   if (!s->prof) return;
   Profiler* P = static_cast<Profiler*>(s->prof);
   if (!P->open[stage]) return;
   cudaEvent_t e = P->get();
   cudaEventRecord(e, st);
-  P->pending.push_back({stage, P->open[stage], e});
+  P->pending.push_back({stage, launches, P->open[stage], e});
   P->open[stage] = nullptr;
   if (P->pending.size() > 1024) P->drain(512);
 }
@@ -207,7 +207,7 @@ void free_scene(fire_scene_s* s) {
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->leaf_slot4, s->lvl_aux, s->nodes4, s->q4};
+                  s->leaf_slot4, s->lvl_aux, s->nodes4, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -250,7 +250,7 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris, 48 * (size_t)T},
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
-      {(void**)&s->leaf_slot4, 4 * (size_t)T},
+      {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
       {(void**)&s->lvl_aux, 8 * (size_t)kMaxDepth4 + 16},
       {(void**)&s->nodes4, 128 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},
@@ -299,7 +299,7 @@ int fire_scene_create(const float* verts_xyzw, int64_t nv, const uint32_t* tri_i
   struct A { void** p; size_t b; } list[] = {
       {(void**)&s->rest, 16 * (size_t)nv}, {(void**)&s->idx, 12 * (size_t)nt}, {(void**)&s->tmat, 4 * (size_t)nt},
       {(void**)&s->vbody, 2 * (size_t)nv}, {(void**)&s->mats, 20 * (size_t)nmat},
-      {(void**)&s->xf, 48 * (size_t)nbody}, {(void**)&s->ctrl, 64}};
+      {(void**)&s->xf, 48 * (size_t)nbody}, {(void**)&s->ctrl, 128}};
   for (auto& a : list) {
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) {
       int rc = cuda_check(e, "scene buffers");
@@ -313,7 +313,7 @@ int fire_scene_create(const float* verts_xyzw, int64_t nv, const uint32_t* tri_i
   if (nv > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->vbody, vert_body, 2 * nv, cudaMemcpyDefault, st), "copy");
   if (nt > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->idx, tri_idx, 12 * nt, cudaMemcpyDefault, st), "copy");
   if (nt > 0) rc = rc ? rc : cuda_check(cudaMemcpyAsync(s->tmat, tri_mat, 4 * nt, cudaMemcpyDefault, st), "copy");
-  rc = rc ? rc : cuda_check(cudaMemsetAsync(s->ctrl, 0, 64, st), "memset");
+  rc = rc ? rc : cuda_check(cudaMemsetAsync(s->ctrl, 0, 128, st), "memset");
   rc = rc ? rc : upload_mats(s, mats, st);
   uint32_t bad = 0;
   rc = rc ? rc : lbvh_validate(s, st, &bad);
@@ -355,6 +355,21 @@ int fire_scene_info(fire_scene s, int64_t* out8) {
   out8[5] = (int64_t)s->bytes;
   out8[6] = s->n4;
   out8[7] = s->height4;
+  return FIRE_OK;
+}
+
+int fire_render_info(fire_scene s, int64_t* out4) {
+  g_err.clear();
+  if (!s || !out4) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  memset(out4, 0, 4 * sizeof(int64_t));
+  if (!s->rendered) return FIRE_OK;
+  if (int e = cuda_check(cudaStreamSynchronize(s->last_stream), "sync")) return e;
+  uint32_t w[32];
+  if (int e = cuda_check(cudaMemcpy(w, s->ctrl, sizeof(w), cudaMemcpyDeviceToHost), "copy")) return e;
+  out4[0] = s->last_raster ? 1 : 0;
+  out4[1] = s->last_raster ? w[kCtrlRasterFlag] : 0;
+  out4[2] = s->last_raster ? w[kCtrlRasterPieces] : 0;
+  out4[3] = w[4];
   return FIRE_OK;
 }
 
@@ -428,7 +443,8 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     a.row_end = o.row_end;
   }
   if (o.stack_depth < 0 || o.stack_depth > 128 || o.blocks_per_sm < 0 ||
-      (o.flags & ~FIRE_RENDER_ALLOW_SHALLOW_STACK) != 0)
+      (o.flags & ~(FIRE_RENDER_ALLOW_SHALLOW_STACK | FIRE_RENDER_TRACE_PRIMARY | FIRE_RENDER_RASTER_PRIMARY)) != 0 ||
+      ((o.flags & FIRE_RENDER_TRACE_PRIMARY) && (o.flags & FIRE_RENDER_RASTER_PRIMARY)))
     return set_error(FIRE_ERR_INVALID_ARG, "invalid render options");
   if (o.stack_depth > 0 && o.stack_depth < std::min(stack_need(s), 128) &&
       !(o.flags & FIRE_RENDER_ALLOW_SHALLOW_STACK))
@@ -455,6 +471,36 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     s->jobs_n = 0;
     if (cudaError_t e = dev_alloc((void**)&s->jobs, njobs * 32, &s->bytes)) return cuda_check(e, "shadow queue");
     s->jobs_n = njobs;
+  }
+  // raster primary pass scratch: one key and one direction per sample, a
+  // piece queue, a deferred-triangle list
+  if ((o.flags & FIRE_RENDER_RASTER_PRIMARY) && s->rkeys_n < nsamp) {
+    if (s->rkeys) {
+      cudaFree(s->rkeys);
+      cudaFree(s->rdirs);
+      s->bytes -= s->rkeys_n * 24;
+    }
+    s->rkeys = nullptr;
+    s->rdirs = nullptr;
+    s->rkeys_n = 0;
+    if (cudaError_t e = dev_alloc((void**)&s->rkeys, nsamp * 8, &s->bytes)) return cuda_check(e, "raster keys");
+    if (cudaError_t e = dev_alloc((void**)&s->rdirs, nsamp * 16, &s->bytes)) {
+      cudaFree(s->rkeys);
+      s->rkeys = nullptr;
+      s->bytes -= nsamp * 8;
+      return cuda_check(e, "raster directions");
+    }
+    s->rkeys_n = nsamp;
+  }
+  if ((o.flags & FIRE_RENDER_RASTER_PRIMARY) && !s->pieces) {
+    size_t cap = (size_t)std::min<int64_t>(std::max<int64_t>(s->nt / 4, 262144), 1 << 22);
+    if (cudaError_t e = dev_alloc((void**)&s->pieces, cap * 16, &s->bytes)) return cuda_check(e, "raster queue");
+    s->pieces_n = cap;
+  }
+  if ((o.flags & FIRE_RENDER_RASTER_PRIMARY) && !s->graze) {
+    size_t cap = (size_t)std::min<int64_t>(std::max<int64_t>(s->nt / 4, 65536), 1 << 22);
+    if (cudaError_t e = dev_alloc((void**)&s->graze, cap * 4, &s->bytes)) return cuda_check(e, "raster list");
+    s->graze_n = cap;
   }
   a.out = out_rgba;
   return render_frame(s, a, o, st);

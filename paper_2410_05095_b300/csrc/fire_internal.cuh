@@ -133,12 +133,21 @@ struct fire_scene_s {
   uint64_t* keys_alt = nullptr; // [nt]
   uint32_t* vals_alt = nullptr; // [nt]
   uint32_t* hist = nullptr;     // [kSortBins * nblocks]
-  uint32_t* ctrl = nullptr;     // [16]: [0..7] task counters, [8] error word, [9..14] bounds
+  uint32_t* ctrl = nullptr;     // [32]: [0..7] task counters, [8] error word, [9..14] bounds,
+                                //       [16..22] raster pass
+  int32_t* rank = nullptr;      // [nt] original triangle -> sorted position
   // render scratch
   fire_gbuffer_rec* gscratch = nullptr;
   size_t gscratch_n = 0;
   double* bwd_partials = nullptr;  // per-block gradient partials of the backward
   size_t bwd_partials_n = 0;
+  unsigned long long* rkeys = nullptr;  // raster keys, one per sample
+  float4* rdirs = nullptr;              // raster ray directions, one per sample
+  size_t rkeys_n = 0;
+  int4* pieces = nullptr;          // raster piece queue
+  size_t pieces_n = 0;
+  int32_t* graze = nullptr;        // raster deferred-triangle list
+  size_t graze_n = 0;
   float4* jobs = nullptr;          // shadow-ray queue, 32 B per ray
   size_t jobs_n = 0;               // capacity in rays
   // batch cache (see batch.cu)
@@ -146,6 +155,8 @@ struct fire_scene_s {
   int64_t iter_cap = 0;
   size_t bytes = 0;
   cudaStream_t last_stream = nullptr;
+  bool rendered = false;        // a fire_render ran (fire_render_info)
+  bool last_raster = false;     // its primary pass rasterised
   void* prof = nullptr;         // fire::Profiler when enabled
 };
 
@@ -165,7 +176,8 @@ int make_lights(const fire_light* lights, int n, LightParams* out);
 enum Stage { kStageRefit = 0, kStagePrimary = 1, kStageShadow = 2, kStageBuild = 3, kStageShadeGbuf = 4,
              kStageBackward = 5, kStageResolve = 6, kStages = 8 };
 void prof_begin(fire_scene_s* s, int stage, cudaStream_t st);
-void prof_end(fire_scene_s* s, int stage, cudaStream_t st);
+// launches: kernels launched between prof_begin and prof_end
+void prof_end(fire_scene_s* s, int stage, cudaStream_t st, int launches = 1);
 
 // lbvh.cu
 int lbvh_build(fire_scene_s* s, cudaStream_t st);
@@ -184,10 +196,33 @@ struct RenderArgs {
   int row_begin, row_end;
   int64_t iter_cap;
   uint32_t* ctrl;               // counters + error word
+  const unsigned long long* rkeys;  // raster keys (primary in key mode) or nullptr
+  const int32_t* rank;          // [nt] original triangle -> sorted position
   fire_gbuffer_rec* g;          // per-sample records
   int write_vis;                // store vis bits into g
   float* out;                   // [H*W*4]
 };
+// Raster primary pass (raster.cu).  Words of fire_scene_s::ctrl it uses:
+constexpr int kCtrlRasterPieces = 16;  // queued pieces
+constexpr int kCtrlRasterCursor = 17;  // next piece to take
+constexpr int kCtrlRasterFlag = 18;    // != 0: traversal fallback for this frame
+constexpr int kCtrlRasterGraze = 19;   // deferred triangles
+constexpr int kCtrlRasterParams = 20;  // [20..22] zn, rn, slack (float bits)
+struct RasterArgs {
+  const float4* tris;
+  int64_t nt;
+  const Node4* nodes4;
+  CamParams cam;
+  int row_begin, row_end;
+  unsigned long long* keys;  // [W*H*spp] per-sample (t bits << 32 | original index)
+  float4* dirs;              // [W*H*spp] per-sample ray direction (xyz)
+  int4* pieces;              // queued pieces: triangle, x0|x1<<16, y0|y1<<16
+  int64_t cap_pieces;
+  int32_t* graze;            // deferred triangles (sorted positions)
+  int64_t cap_graze;
+  uint32_t* ctrl;
+};
+int raster_primary(fire_scene_s* s, const RasterArgs& r, cudaStream_t st);
 int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o, cudaStream_t st);
 int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten, cudaStream_t st);
 int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,

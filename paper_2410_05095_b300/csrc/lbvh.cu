@@ -321,12 +321,13 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, Node* __rest
 // Permute the index buffer and materials into leaf (sorted) order.
 __global__ void k_gather_sorted(const uint32_t* __restrict__ order, const uint32_t* __restrict__ idx,
                                 const uint32_t* __restrict__ tmat, int64_t nt, uint4* __restrict__ sidx,
-                                uint32_t* __restrict__ smat) {
+                                uint32_t* __restrict__ smat, int32_t* __restrict__ rank) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
   uint32_t o = order[i];
   sidx[i] = make_uint4(idx[3 * (int64_t)o], idx[3 * (int64_t)o + 1], idx[3 * (int64_t)o + 2], o);
   smat[i] = tmat[o];
+  rank[o] = (int32_t)i;
 }
 
 // Write one child sector of a node: box, link and subtree height (a whole
@@ -660,12 +661,12 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
     if (int e = cuda_check(cudaMemsetAsync(s->nodes, 0xff, 64 * (T - 1), st), "memset")) return e;
     k_karras<<<grid_for(T - 1, 256), 256, 0, st>>>(s->keys, T, s->nodes, s->leaf_slot, s->node_slot);
   }
-  k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat);
+  k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat, s->rank);
   if (T > 1)
     if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;
   k_refit_build<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
                                                    s->nodes, s->leaf_slot, s->node_slot, s->counters);
-  prof_end(s, kStageBuild, st);
+  prof_end(s, kStageBuild, st, 2 + 3 * kSortPasses + (T > 1 ? 1 : 0) + 2);
   if (int e = cuda_check(cudaGetLastError(), "build kernels")) return e;
   Node n0;
   if (int e = cuda_check(cudaMemcpyAsync(&n0, &s->nodes[0], sizeof(Node), cudaMemcpyDeviceToHost, st), "copy")) return e;
@@ -722,9 +723,10 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   // depths, deepest first: runs of small depths go to one block, large ones get their own launch
   const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
   const int64_t* lvl_dev = reinterpret_cast<const int64_t*>(s->lvl_aux);
-  int d = D - 1;
+  int d = D - 1, launches = 1;
   while (d >= 0) {
     const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
+    ++launches;
     if (n > 8192) {
       k_refit4_level<<<grid_for(n, 256), 256, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4);
       --d;
@@ -735,7 +737,7 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
     k_refit4_small<<<1, 1024, 0, st>>>(s->nodes4, lvl_dev, d0, d, s->n4);
     d = d0 - 1;
   }
-  prof_end(s, kStageRefit, st);
+  prof_end(s, kStageRefit, st, launches);
   return cuda_check(cudaGetLastError(), "refit kernels");
 }
 

@@ -23,8 +23,12 @@ namespace {
 // shadow ray (lifted origin, unit direction, range, sample|light) to a dense
 // queue: one ballot per light, one atomicAdd per warp, lanes ranked by the
 // popcount of the lower lanes.
-template <int STACK>
+// MODE 0: traversal.  After a raster pass (raster.cu): MODE 1 traverses only
+// if that pass fell back, MODE 2 takes each sample's hit from its key
+// otherwise; exactly one of the two does the work.
+template <int STACK, int MODE>
 __global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
+  if (MODE != 0 && (MODE == 1) != (a.ctrl[kCtrlRasterFlag] != 0u)) return;
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;
   TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
@@ -42,8 +46,17 @@ __global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int n
     float3 o = f3(a.cam.ox, a.cam.oy, a.cam.oz), n = f3(0, 0, 0), po = f3(0, 0, 0);
     if (valid) {
       float3 d = cam_dir(a.cam, x, y, k);
-      trace_nearest<STACK>(c, o, d, prim, pos, t);
       sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
+      if (MODE == 2) {
+        const unsigned long long key = a.rkeys[sid];
+        if (key != ~0ull) {
+          prim = (int)(uint32_t)key;
+          t = __uint_as_float((uint32_t)(key >> 32));
+          pos = __ldg(a.rank + prim);
+        }
+      } else {
+        trace_nearest<STACK>(c, o, d, prim, pos, t);
+      }
       if (prim >= 0) {
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
         hit_frame(B, C, o, d, t, eps, n, po);
@@ -336,12 +349,12 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
 
 template <int STACK>
 int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int ntasks,
-                  const fire_render_opts& o, cudaStream_t st) {
+                  const fire_render_opts& o, bool raster, cudaStream_t st) {
   const int threads = 128;
   static int occ_p = 0, occ_s = 0, occ_r = 0;
   static std::once_flag once;
   std::call_once(once, [] {
-    occ_p = occupancy_blocks(k_primary<STACK>, 128, 0);
+    occ_p = occupancy_blocks(k_primary<STACK, 0>, 128, 0);
     occ_s = occupancy_blocks(k_shadow<STACK>, 128, 0);
     occ_r = occupancy_blocks(k_shade<32, false>, 128, 0);
   });
@@ -356,8 +369,19 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
   int gs = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * bs, (maxjobs + 127) / 128));
   int gr = std::max(1, std::min(sms * br, (ntasks + 3) / 4));
   prof_begin(s, kStagePrimary, st);
-  k_primary<STACK><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
-  prof_end(s, kStagePrimary, st);
+  if (raster) {
+    RasterArgs r{a.tris, a.nt, a.nodes4, a.cam, a.row_begin, a.row_end, s->rkeys, s->rdirs, s->pieces,
+                 (int64_t)s->pieces_n, s->graze, (int64_t)s->graze_n, a.ctrl};
+    if (int e = raster_primary(s, r, st)) return e;
+    RenderArgs ak = a;
+    ak.rkeys = s->rkeys;
+    ak.rank = s->rank;
+    k_primary<STACK, 1><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
+    k_primary<STACK, 2><<<gp, threads, 0, st>>>(ak, g, ntasks, s->jobs);
+  } else {
+    k_primary<STACK, 0><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
+  }
+  prof_end(s, kStagePrimary, st, raster ? (a.nt > 0 ? 6 : 3) : 1);
   if (a.lights.n > 0) {
     prof_begin(s, kStageShadow, st);
     k_shadow<STACK><<<gs, threads, 0, st>>>(a, s->jobs);
@@ -385,11 +409,18 @@ int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o
   if (ntasks == 0) return FIRE_OK;
   // task counters, queue length and queue cursor (the error word at [8] stays)
   if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 8 * 4, st), "memset")) return e;
+  // primary pass: traversal unless the raster pass is asked for (it
+  // measured slower on the scenes of sub-pixel triangles this library is
+  // timed on, and equal at best elsewhere)
+  bool raster = (o.flags & FIRE_RENDER_RASTER_PRIMARY) != 0;
+  raster = raster && s->rkeys && s->pieces && s->graze && a.cam.W < 65536 && a.cam.H < 65536;
+  s->rendered = true;
+  s->last_raster = raster;
   switch (stack_for_height(stack_need(s), o.stack_depth)) {
-    case 8: return launch_render<8>(s, a, g, ntasks, o, st);
-    case 32: return launch_render<32>(s, a, g, ntasks, o, st);
-    case 64: return launch_render<64>(s, a, g, ntasks, o, st);
-    default: return launch_render<128>(s, a, g, ntasks, o, st);
+    case 8: return launch_render<8>(s, a, g, ntasks, o, raster, st);
+    case 32: return launch_render<32>(s, a, g, ntasks, o, raster, st);
+    case 64: return launch_render<64>(s, a, g, ntasks, o, raster, st);
+    default: return launch_render<128>(s, a, g, ntasks, o, raster, st);
   }
 }
 

@@ -26,12 +26,18 @@ __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
 //   ndy = 1 - (2 fy)/H, sy = ndy * sys); d = normalize(fma(sx, r, fma(sy, u, f)))
 // 4 spp: rotated grid (-1/8,-3/8), (3/8,-1/8), (-3/8,1/8), (1/8,3/8).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 cam_dir(const CamParams& c, int x, int y, int k) {
-  float ox = 0.0f, oy = 0.0f;
-  if (c.spp == 4) {
+__device__ __forceinline__ void spp_offset(int spp, int k, float& ox, float& oy) {
+  ox = 0.0f;
+  oy = 0.0f;
+  if (spp == 4) {
     ox = (k == 0) ? -0.125f : (k == 1) ? 0.375f : (k == 2) ? -0.375f : 0.125f;
     oy = (k == 0) ? -0.375f : (k == 1) ? -0.125f : (k == 2) ? 0.125f : 0.375f;
   }
+}
+
+__device__ __forceinline__ float3 cam_dir(const CamParams& c, int x, int y, int k) {
+  float ox, oy;
+  spp_offset(c.spp, k, ox, oy);
   float fx = (float)x + (0.5f + ox);
   float fy = (float)y + (0.5f + oy);
   float ndx = (2.0f * fx) / (float)c.W - 1.0f;

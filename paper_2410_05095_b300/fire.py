@@ -26,8 +26,8 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_bvh_build", "fire_bvh_refit", "fire_render", "fire_render_batch", "fire_shade",
            "fire_shade_backward", "fire_debug_dump", "fire_sync_status",
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
-           "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_last_error",
-           "fire_version"]
+           "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
+           "fire_last_error", "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -88,6 +88,7 @@ def lib():
             "fire_profile_enable": [P, i32],
             "fire_profile_read": [P, P, P],
             "fire_shade_backward_noalloc": [P, P, P, P, i32, P, P, P, P, P, P],
+            "fire_render_info": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -199,6 +200,13 @@ class Scene:
         _check(lib().fire_scene_info(self.h, out))
         return dict(nv=out[0], nt=out[1], nmat=out[2], nbody=out[3], height=out[4], bytes=out[5],
                     n4=out[6], depth4=out[7])
+
+    def render_info(self) -> dict:
+        """Facts of the last render (waits for it): primary method, raster
+        fallback reasons, raster pieces queued, shadow rays queued."""
+        out = (C.c_int64 * 4)()
+        _check(lib().fire_render_info(self.h, out))
+        return dict(raster=bool(out[0]), fallback=out[1], pieces=out[2], shadow_rays=out[3])
 
     def build(self, xforms, stream=None):
         """xforms: [nbody,12] f32 -- a CUDA tensor (device) or numpy/CPU tensor (host)."""
