@@ -198,7 +198,7 @@ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
 }
 
 // Stack traversal of the 4-wide tree (collapsed from the Karras binary
-// tree), nearest child first.  One node fetch (7 x 16 B) tests all four child
+// tree), nearest child first (both modes).  One node fetch (7 x 16 B) tests all four child
 // boxes; leaf children (one triangle each) are tested at once, so the
 // nearest-hit bound tightens early; hit internal children are ordered by
 // entry distance with a 5-comparator network and all but the nearest pushed,
@@ -265,20 +265,9 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
       cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
       continue;
     }
-    if (ANY) {  // any hit: the visiting order does not matter, skip the sort
-      if (sp + cnt - 1 <= STACK) {
-        int first = kDone;
-        if (h3) { first = v3; }
-        if (h2) { if (first != kDone) stack[sp++] = first; first = v2; }
-        if (h1) { if (first != kDone) stack[sp++] = first; first = v1; }
-        if (h0) { if (first != kDone) stack[sp++] = first; first = v0; }
-        cur = first;
-      } else {
-        atomicOr(c.err, kErrStack);
-        cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
-      }
-      continue;
-    }
+    // nearest child first in both modes: for shadow rays it finds the
+    // occluders next to the surface point early (measured 9% faster than
+    // the unsorted order on the 7.3M-triangle frame)
     k0 = h0 ? k0 : inf_f();
     k1 = h1 ? k1 : inf_f();
     k2 = h2 ? k2 : inf_f();
