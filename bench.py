@@ -44,7 +44,7 @@ def workload_config(w, nframes):
                          f"{cam.width}x{cam.height}, {cam.spp} spp rotated grid, {len(w.lights)} point lights"),
             "triangles": w.scene.nt, "width": cam.width, "height": cam.height, "spp": cam.spp,
             "lights": len(w.lights), "bodies": w.scene.nbody - 1, "frames": nframes,
-            "l2": "inputs larger than L2: every refit rewrites 467 MB of nodes + 350 MB of triangles",
+            "l2": "inputs larger than L2: every refit rewrites 445 MB of 4-wide nodes + 350 MB of triangles",
             "parallelism": "replicas"}
 
 
