@@ -341,6 +341,9 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     // the pageable copy is staged before cudaMemcpyAsync returns
     C.last_bytes.assign((unsigned char*)h.data(), (unsigned char*)h.data() + nbytes);
   }
+  // the scenes' current frame buffers: wait for their build/refit (the
+  // tuning launches below read them too)
+  for (int i = 0; i < nscenes; ++i) frame_acquire(scenes[i], st);
   // configuration: caller's, else tuned once per batch shape
   fire_render_opts o{};
   if (opts) o = *opts;
@@ -419,7 +422,9 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     if (int e = cuda_check(ce, "graph instantiate")) return e;
     C.last_key = key;
   }
-  return cuda_check(cudaGraphLaunch(C.exec, st), "graph launch");
+  const int e = cuda_check(cudaGraphLaunch(C.exec, st), "graph launch");
+  for (int i = 0; i < nscenes; ++i) frame_release(scenes[i], st);
+  return e;
 }
 
 void batch_free(fire_scene_s*) {}

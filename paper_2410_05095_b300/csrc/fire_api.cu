@@ -205,11 +205,16 @@ void free_scene(fire_scene_s* s) {
   delete static_cast<Profiler*>(s->prof);
   s->prof = nullptr;
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
-                  s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris, s->cen,
+                  s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris_buf[0],
+                  s->tris_buf[1], s->nodes4_buf[0], s->nodes4_buf[1], s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->leaf_slot4, s->lvl_aux, s->nodes4, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze};
+                  s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int b = 0; b < 2; ++b) {
+    if (s->ready_ev[b]) cudaEventDestroy(s->ready_ev[b]);
+    if (s->used_ev[b]) cudaEventDestroy(s->used_ev[b]);
+  }
 }
 
 int upload_mats(fire_scene_s* s, const fire_material* m, cudaStream_t st) {
@@ -247,22 +252,49 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->order, 4 * (size_t)T},         {(void**)&s->sidx, 16 * (size_t)T},
       {(void**)&s->smat, 4 * (size_t)T},          {(void**)&s->nodes, 64 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->leaf_slot, 4 * (size_t)T},     {(void**)&s->node_slot, 4 * (size_t)std::max<int64_t>(T - 1, 1)},
-      {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris, 48 * (size_t)T},
+      {(void**)&s->counters, 4 * (size_t)std::max<int64_t>(T - 1, 1)}, {(void**)&s->tris_buf[0], 48 * (size_t)T},
+      {(void**)&s->tris_buf[1], 48 * (size_t)T},
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
       {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
       {(void**)&s->lvl_aux, 8 * (size_t)kMaxDepth4 + 16},
-      {(void**)&s->nodes4, 128 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},
   };
   for (auto& a : list)
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "LBVH buffers");
+  for (int b = 0; b < 2; ++b) {
+    if (int e = cuda_check(cudaEventCreateWithFlags(&s->ready_ev[b], cudaEventDisableTiming), "event")) return e;
+    if (int e = cuda_check(cudaEventCreateWithFlags(&s->used_ev[b], cudaEventDisableTiming), "event")) return e;
+  }
+  s->cur = 0;
+  s->tris = s->tris_buf[0];
+  s->nodes4 = s->nodes4_buf[0];
   return FIRE_OK;
 }
 
 cudaStream_t as_stream(void* st) { return reinterpret_cast<cudaStream_t>(st); }
 
+// Point s->tris / s->nodes4 at buffer b.
+void select_buffer(fire_scene_s* s, int b) {
+  s->cur = b;
+  s->tris = s->tris_buf[b];
+  s->nodes4 = s->nodes4_buf[b];
+}
+
 }  // namespace
+
+void frame_acquire(fire_scene_s* s, cudaStream_t st) {
+  if (s->ready_rec[s->cur]) cudaStreamWaitEvent(st, s->ready_ev[s->cur], 0);
+}
+
+void frame_release(fire_scene_s* s, cudaStream_t st) {
+  if (!s->used_ev[s->cur]) return;
+  cudaEventRecord(s->used_ev[s->cur], st);
+  s->used_rec[s->cur] = true;
+}
+
 }  // namespace fire
 
 using namespace fire;
@@ -363,7 +395,7 @@ int fire_render_info(fire_scene s, int64_t* out4) {
   if (!s || !out4) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
   memset(out4, 0, 4 * sizeof(int64_t));
   if (!s->rendered) return FIRE_OK;
-  if (int e = cuda_check(cudaStreamSynchronize(s->last_stream), "sync")) return e;
+  if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
   uint32_t w[32];
   if (int e = cuda_check(cudaMemcpy(w, s->ctrl, sizeof(w), cudaMemcpyDeviceToHost), "copy")) return e;
   out4[0] = s->last_raster ? 1 : 0;
@@ -380,7 +412,22 @@ int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
   s->last_stream = st;
   if (int e = load_xforms(s, body_xforms, xforms_on_device, st)) return e;
   if (int e = alloc_lbvh(s)) return e;
-  return lbvh_build(s, st);
+  // both buffers are rewritten: wait for their last users
+  for (int b = 0; b < 2; ++b)
+    if (s->used_rec[b]) cudaStreamWaitEvent(st, s->used_ev[b], 0);
+  select_buffer(s, 0);
+  if (int e = lbvh_build(s, st)) return e;
+  if (s->nt > 0) {
+    // buffer 1 gets the 4-wide links (a refit rewrites boxes and records only)
+    if (int e = cuda_check(cudaMemcpyAsync(s->nodes4_buf[1], s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(s->n4, 1),
+                                           cudaMemcpyDeviceToDevice, st), "copy"))
+      return e;
+    for (int b = 0; b < 2; ++b) {
+      cudaEventRecord(s->ready_ev[b], st);
+      s->ready_rec[b] = true;
+    }
+  }
+  return FIRE_OK;
 }
 
 int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream) {
@@ -389,8 +436,22 @@ int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
   if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "refit before build");
   cudaStream_t st = as_stream(stream);
   s->last_stream = st;
+  if (s->nt == 0) return load_xforms(s, body_xforms, xforms_on_device, st);
+  // write the buffer the current frame does not use, after its last reader
+  // and after the build that laid out its links
+  const int target = s->cur ^ 1;
+  if (s->used_rec[target]) cudaStreamWaitEvent(st, s->used_ev[target], 0);
+  if (s->ready_rec[target]) cudaStreamWaitEvent(st, s->ready_ev[target], 0);
   if (int e = load_xforms(s, body_xforms, xforms_on_device, st)) return e;
-  return lbvh_refit(s, st);
+  const int prev = s->cur;
+  select_buffer(s, target);
+  if (int e = lbvh_refit(s, st)) {
+    select_buffer(s, prev);
+    return e;
+  }
+  cudaEventRecord(s->ready_ev[target], st);
+  s->ready_rec[target] = true;
+  return FIRE_OK;
 }
 
 static int fill_args(fire_scene s, const fire_camera* cam, const fire_light* lights, int32_t nlights,
@@ -503,7 +564,10 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     s->graze_n = cap;
   }
   a.out = out_rgba;
-  return render_frame(s, a, o, st);
+  frame_acquire(s, st);
+  const int e = render_frame(s, a, o, st);
+  frame_release(s, st);
+  return e;
 }
 
 int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_camera* cams, const int32_t* cam_scene,
@@ -543,7 +607,10 @@ int fire_shade(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* ca
   a.out = out_rgba;
   cudaStream_t st = as_stream(stream);
   s->last_stream = st;
-  return shade_from_gbuffer(s, a, inten, st);
+  frame_acquire(s, st);
+  const int e = shade_from_gbuffer(s, a, inten, st);
+  frame_release(s, st);
+  return e;
 }
 
 int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam, const fire_light* lights,
@@ -559,7 +626,10 @@ int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_c
   a.mats.p = params;
   cudaStream_t st = as_stream(stream);
   s->last_stream = st;
-  return shade_backward(s, a, inten, dL_drgba, dparams, dinten, st);
+  frame_acquire(s, st);
+  const int e = shade_backward(s, a, inten, dL_drgba, dparams, dinten, st);
+  frame_release(s, st);
+  return e;
 }
 
 int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
@@ -567,8 +637,7 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
   if (!s || !host_dst) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
   if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "dump before build");
   const int64_t T = s->nt;
-  cudaStream_t st = s->last_stream;
-  if (cudaError_t e = cudaStreamSynchronize(st)) return cuda_check(e, "sync");
+  if (cudaError_t e = cudaDeviceSynchronize()) return cuda_check(e, "sync");
   auto need = [&](size_t n) { return bytes == n; };
   auto get = [&](void* dst, const void* src, size_t n) {
     return cuda_check(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost), "dump copy");

@@ -123,11 +123,23 @@ struct fire_scene_s {
   uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]) + 2 collapse counters
   std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
   int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf
-  fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree
+  fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree (current buffer)
   int64_t n4 = 0;               // 4-wide nodes in use
   int height4 = 0;              // 4-wide levels
   int32_t* q4 = nullptr;        // build queue: 2 x [nt] (binary node, 4-wide node) pairs
-  float4* tris = nullptr;       // [nt*3]
+  float4* tris = nullptr;       // [nt*3] triangle records of the current buffer
+  // Per-frame data is double-buffered (triangle records + 4-wide boxes): a
+  // refit writes the buffer the last render did not read, so a refit on one
+  // stream can overlap a render of the previous frame on another.  Events
+  // order the two: ready_ev[b] after the build/refit that wrote buffer b,
+  // used_ev[b] after the last render/shade enqueued on buffer b.
+  float4* tris_buf[2] = {nullptr, nullptr};
+  fire::Node4* nodes4_buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  cudaEvent_t ready_ev[2] = {nullptr, nullptr};
+  cudaEvent_t used_ev[2] = {nullptr, nullptr};
+  bool ready_rec[2] = {false, false};
+  bool used_rec[2] = {false, false};
   // build scratch
   float4* cen = nullptr;        // [nt]
   uint64_t* keys_alt = nullptr; // [nt]
@@ -166,6 +178,11 @@ namespace fire {
 // Host helpers (fire_api.cu)
 // ---------------------------------------------------------------------------
 int set_error(int code, const std::string& msg);
+// Double-buffered frame data (fire_api.cu): frame_acquire makes `st` wait
+// for the build/refit of the current buffer; frame_release marks the work
+// enqueued on `st` as the buffer's last user.
+void frame_acquire(fire_scene_s* s, cudaStream_t st);
+void frame_release(fire_scene_s* s, cudaStream_t st);
 int cuda_check(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes, size_t* counter);
 int sm_count();

@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(256) k_fill4(const Node* __restrict__ nodes, N
 // Min/max are exact, so every box equals the min/max over its triangles'
 // vertices bit for bit.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_refit4_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+__global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
                                                        const float* __restrict__ xf, const uint4* __restrict__ sidx,
                                                        const uint32_t* __restrict__ smat, int64_t nt,
                                                        float4* __restrict__ tris, Node4* __restrict__ nodes4,
@@ -596,7 +596,7 @@ __device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4
   for (int j = 0; j < 6; ++j) (&n->lox)[j] = m[j];
 }
 
-__global__ void __launch_bounds__(256) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4) {
+__global__ void __launch_bounds__(128) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4) {
   const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q < end) refit4_node(nodes4, q, n4);
 }
@@ -718,7 +718,9 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) return FIRE_OK;
   prof_begin(s, kStageRefit, st);
-  k_refit4_leaves<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
+  // 128-thread blocks: small enough to be scheduled beside the render
+  // kernels' blocks when a refit overlaps the previous frame's render
+  k_refit4_leaves<<<grid_for(T, 128), 128, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
                                                     s->nodes4, s->leaf_slot4, s->n4);
   // depths, deepest first: runs of small depths go to one block, large ones get their own launch
   const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
@@ -728,7 +730,7 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
     const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
     ++launches;
     if (n > 8192) {
-      k_refit4_level<<<grid_for(n, 256), 256, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4);
+      k_refit4_level<<<grid_for(n, 128), 128, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4);
       --d;
       continue;
     }

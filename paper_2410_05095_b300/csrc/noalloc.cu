@@ -98,5 +98,8 @@ extern "C" int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec*
   if (int e = cuda_check(cudaMemsetAsync(ctrl, 0, kNoAllocCtrlBytes, st), "clear scratch")) return e;
   if (int e = cuda_check(cudaMemsetAsync(acc, 0, sizeof(double) * nacc, st), "clear scratch")) return e;
   a.ctrl = ctrl;
-  return shade_backward_on(a, inten, dL_drgba, dparams, dinten, acc, st);
+  frame_acquire(s, st);
+  const int e = shade_backward_on(a, inten, dL_drgba, dparams, dinten, acc, st);
+  frame_release(s, st);
+  return e;
 }

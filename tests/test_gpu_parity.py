@@ -276,3 +276,32 @@ def test_shade_gbuffer_equals_render(fb):
     inten = torch.tensor([l.intensity for l in lights], dtype=torch.float32, device="cuda")
     img2 = G.shade(gb, cam, lights, params, inten)
     assert torch.equal(img, img2)
+
+
+def test_pipelined_frames_equal_serial(fb):
+    """Double-buffered frames: refits on their own stream (into the buffer
+    the last render did not read) interleaved with renders on another stream
+    give the images of the serial order, frame by frame."""
+    torch = torch_cuda()
+    w = sg.workload_frame7m(nspheres=120, cells=64)
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 160, 96, 4)
+    xf0 = w.motion.xforms()
+    poses = [w.motion.step() for _ in range(6)]
+    G1, G2 = fb.Scene.from_numpy(w.scene), fb.Scene.from_numpy(w.scene)
+    G1.build(xf0)
+    G2.build(xf0)
+    serial = []
+    for xf in poses:
+        G1.refit(xf)
+        serial.append(G1.render(cam, w.lights).clone())
+    dev = [torch.from_numpy(xf).cuda() for xf in poses]
+    outs = [torch.zeros_like(serial[0]) for _ in poses]
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    for i, xf in enumerate(dev):
+        G2.refit(xf if i % 2 else poses[i], stream=side)   # device and host poses
+        G2.render(cam, w.lights, out=outs[i])
+    torch.cuda.synchronize()
+    assert G2.sync_status() == 0
+    for a, b in zip(serial, outs):
+        assert torch.equal(a, b)
