@@ -171,7 +171,17 @@ int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
 
 /* Refit with the topology of the last build (§IV-B-3 step 4: new transforms
  * each frame): re-transform the vertices and recompute every box bottom-up.
- * Before any build -> FIRE_ERR_NOT_BUILT. */
+ * Before any build -> FIRE_ERR_NOT_BUILT.
+ *
+ * Frame buffers: the per-frame data (48-B triangle records and the 4-wide
+ * boxes, 48·nt + 128·n4 bytes) exists twice.  A refit writes the buffer the
+ * last render did not read and makes it current; renders, shading and the
+ * backward read the current buffer.  The library orders the calls with CUDA
+ * events across streams (a refit waits for the last reader of the buffer it
+ * overwrites; a render waits for the refit that wrote its buffer), so a
+ * refit issued on its own stream overlaps the previous frame's render, like
+ * the paper's asynchronous compute queue.  Supported overlap: one refit
+ * stream and one stream of render/shade calls per scene. */
 int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream);
 
 /* ---------------------------------------------------------------- render */
