@@ -81,6 +81,11 @@ def lib():
         L.orc_grad_f64.argtypes = [P, P, P, i32, P, P, P, P, P, P, P, P]
         L.orc_shadow_eps.restype = C.c_float
         L.orc_shadow_eps.argtypes = [P]
+        L.orc_display.argtypes = [P, i32, i32, C.c_float, i32, P, P]
+        L.orc_srgb_encode.restype = C.c_float
+        L.orc_srgb_encode.argtypes = [C.c_float]
+        L.orc_root12_pow5.restype = C.c_float
+        L.orc_root12_pow5.argtypes = [C.c_float]
         _lib = L
     return _lib
 
@@ -293,3 +298,23 @@ def params_of(mats: np.ndarray) -> np.ndarray:
         p[i, 3] = m["roughness"]
         p[i, 4] = m["metallic"]
     return p
+
+
+def display(hdr: np.ndarray, exposure: float = 1.0, fxaa: bool = True, want_gamma: bool = False):
+    """Display stage of an [H, W, 4] linear HDR image (rgb + coverage):
+    Reinhard tone map, sRGB encode, optional FXAA, 8-bit quantisation.
+    Returns [H, W, 4] uint8 (and the pre-FXAA gamma-space float image)."""
+    h = np.ascontiguousarray(hdr, np.float32)
+    H, W = h.shape[:2]
+    out = np.zeros((H, W, 4), np.uint8)
+    g = np.zeros((H, W, 4), np.float32) if want_gamma else None
+    lib().orc_display(_p(h), W, H, float(exposure), int(bool(fxaa)), _p(g) if want_gamma else None, _p(out))
+    return (out, g) if want_gamma else out
+
+
+def srgb_encode(r: float) -> float:
+    return float(lib().orc_srgb_encode(float(r)))
+
+
+def root12_pow5(r: float) -> float:
+    return float(lib().orc_root12_pow5(float(r)))

@@ -819,3 +819,150 @@ void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Display output stage (§IV-A-1: Reinhard tone mapping, then gamma
+// correction = the inverse of the sRGB-to-linear conversion; §IV-B-2: FXAA),
+// applied to the resolved linear HDR image.  FP32, in this order:
+//   c' = e * c; r = c' / (1 + c')                       (Reinhard, per channel)
+//   s = r <= 0.0031308 ? 12.92 * r : 1.055 * r^(1/2.4) - 0.055   (sRGB, IEC 61966-2-1)
+//   r^(1/2.4) = (r^(1/12))^5, r^(1/12) = m^(1/12) * 2^(-k/12) for r = m 2^-k,
+//   m in [1, 2); m^(1/12) by three Newton steps on t^12 = m from the chord
+//   1 + (m - 1)(2^(1/12) - 1); 2^(-k/12) and 2^(1/12) - 1 rounded from FP64
+//   byte = floor(clamp(v, 0, 1) * 255 + 0.5)
+// FXAA (Lottes' FXAA, its simple form), on the gamma-space image G with
+// clamp-to-edge fetches and bilinear taps (pixel centres at +0.5):
+//   luma = (0.299 r + 0.587 g) + 0.114 b
+//   gradient (x right, y down) from the four diagonal neighbours;
+//   edge direction d = (-(S - N), E - W) with N = lNW + lNE, S = lSW + lSE,
+//   W = lNW + lSW, E = lNE + lSE;
+//   d /= min(|d.x|, |d.y|) + max((lNW + lNE + lSW + lSE) * (0.25 / 8), 1/128),
+//   clamped to [-8, 8] pixels;
+//   A = (tap(p + d (1/3 - 1/2)) + tap(p + d (2/3 - 1/2))) / 2
+//   B = A / 2 + (tap(p - d / 2) + tap(p + d / 2)) / 4
+//   out = luma(B) outside [min, max] of the five lumas ? A : B
+// Alpha (coverage) is quantised as is.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DispConst {
+  float tab[12];   // 2^(-k/12)
+  float chord;     // 2^(1/12) - 1
+};
+
+DispConst disp_const() {
+  DispConst c;
+  for (int k = 0; k < 12; ++k) c.tab[k] = (float)std::pow(2.0, -k / 12.0);
+  c.chord = (float)(std::pow(2.0, 1.0 / 12.0) - 1.0);
+  return c;
+}
+
+float root12_pow5(const DispConst& C, float r) {  // r^(5/12), r in [2^-9, 1)
+  int e = 0;
+  float m = std::frexp(r, &e);  // r = m 2^e, m in [0.5, 1)
+  m = m * 2.0f;                 // [1, 2)
+  const int k = 1 - e;          // r = m 2^-k
+  float t = 1.0f + (m - 1.0f) * C.chord;
+  for (int i = 0; i < 3; ++i) {
+    float t2 = t * t, t4 = t2 * t2, t8 = t4 * t4, t11 = (t8 * t2) * t;
+    t = (11.0f * t + m / t11) / 12.0f;
+  }
+  const float u = t * C.tab[k];  // r^(1/12)
+  const float u2 = u * u;
+  return (u2 * u2) * u;
+}
+
+float srgb_encode(const DispConst& C, float r) {
+  if (r <= 0.0031308f) return 12.92f * r;
+  return 1.055f * root12_pow5(C, r) - 0.055f;
+}
+
+float tonemap(const DispConst& C, float c, float e) {
+  const float cc = e * c;
+  return srgb_encode(C, cc / (1.0f + cc));
+}
+
+uint8_t quant(float v) {
+  const float w = std::min(std::max(v, 0.0f), 1.0f) * 255.0f + 0.5f;
+  return (uint8_t)(int)std::floor(w);
+}
+
+float luma3(const float* c) { return (0.299f * c[0] + 0.587f * c[1]) + 0.114f * c[2]; }
+
+struct Img {
+  const float* g;  // [H*W*4] gamma-space rgb + coverage
+  int W, H;
+  const float* at(int i, int j) const {
+    i = std::min(std::max(i, 0), W - 1);
+    j = std::min(std::max(j, 0), H - 1);
+    return g + 4 * ((int64_t)j * W + i);
+  }
+  void tap(float px, float py, float* out) const {
+    const float u = px - 0.5f, v = py - 0.5f;
+    const float fi = std::floor(u), fj = std::floor(v);
+    const float fu = u - fi, fv = v - fj;
+    const int i0 = (int)fi, j0 = (int)fj;
+    const float *c00 = at(i0, j0), *c10 = at(i0 + 1, j0), *c01 = at(i0, j0 + 1), *c11 = at(i0 + 1, j0 + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+      const float top = c00[ch] + (c10[ch] - c00[ch]) * fu;
+      const float bot = c01[ch] + (c11[ch] - c01[ch]) * fu;
+      out[ch] = top + (bot - top) * fv;
+    }
+  }
+};
+
+void fxaa_pixel(const Img& I, int x, int y, float* out) {
+  const float lM = luma3(I.at(x, y)), lNW = luma3(I.at(x - 1, y - 1)), lNE = luma3(I.at(x + 1, y - 1)),
+              lSW = luma3(I.at(x - 1, y + 1)), lSE = luma3(I.at(x + 1, y + 1));
+  const float lmin = std::min(lM, std::min(std::min(lNW, lNE), std::min(lSW, lSE)));
+  const float lmax = std::max(lM, std::max(std::max(lNW, lNE), std::max(lSW, lSE)));
+  float dx = -((lSW + lSE) - (lNW + lNE));
+  float dy = (lNE + lSE) - (lNW + lSW);
+  const float reduce = std::max((((lNW + lNE) + lSW) + lSE) * (0.25f * 0.125f), 1.0f / 128.0f);
+  const float rcp = 1.0f / (std::min(std::fabs(dx), std::fabs(dy)) + reduce);
+  dx = std::min(std::max(dx * rcp, -8.0f), 8.0f);
+  dy = std::min(std::max(dy * rcp, -8.0f), 8.0f);
+  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const float k1 = 1.0f / 3.0f - 0.5f, k2 = 2.0f / 3.0f - 0.5f;
+  float a1[3], a2[3], b1[3], b2[3], A[3], B[3];
+  I.tap(px + dx * k1, py + dy * k1, a1);
+  I.tap(px + dx * k2, py + dy * k2, a2);
+  I.tap(px + dx * -0.5f, py + dy * -0.5f, b1);
+  I.tap(px + dx * 0.5f, py + dy * 0.5f, b2);
+  for (int ch = 0; ch < 3; ++ch) {
+    A[ch] = 0.5f * (a1[ch] + a2[ch]);
+    B[ch] = A[ch] * 0.5f + 0.25f * (b1[ch] + b2[ch]);
+  }
+  const float lB = luma3(B);
+  const float* pick = (lB < lmin || lB > lmax) ? A : B;
+  for (int ch = 0; ch < 3; ++ch) out[ch] = pick[ch];
+}
+
+}  // namespace
+
+extern "C" {
+
+float orc_srgb_encode(float r) { return srgb_encode(disp_const(), r); }
+float orc_root12_pow5(float r) { return root12_pow5(disp_const(), r); }
+
+void orc_display(const float* hdr, int32_t W, int32_t H, float exposure, int32_t fxaa, float* gamma_out,
+                 uint8_t* out) {
+  const DispConst C = disp_const();
+  std::vector<float> g(4 * (size_t)W * H);
+  for (int64_t p = 0; p < (int64_t)W * H; ++p) {
+    for (int ch = 0; ch < 3; ++ch) g[4 * p + ch] = tonemap(C, hdr[4 * p + ch], exposure);
+    g[4 * p + 3] = hdr[4 * p + 3];
+  }
+  if (gamma_out) std::copy(g.begin(), g.end(), gamma_out);
+  const Img I{g.data(), W, H};
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int64_t p = (int64_t)y * W + x;
+      float c[3] = {g[4 * p], g[4 * p + 1], g[4 * p + 2]};
+      if (fxaa) fxaa_pixel(I, x, y, c);
+      for (int ch = 0; ch < 3; ++ch) out[4 * p + ch] = quant(c[ch]);
+      out[4 * p + 3] = quant(g[4 * p + 3]);
+    }
+}
+
+}  // extern "C"

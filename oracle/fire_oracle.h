@@ -89,6 +89,16 @@ void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, i
 /* Shadow-ray offset epsilon = 1e-4 * scene-box diagonal. */
 float orc_shadow_eps(const orc_scene* s);
 
+/* Display output stage (§IV-A-1 Reinhard + gamma correction, §IV-B-2 FXAA):
+ * hdr [H*W*4] linear rgb + coverage -> out [H*W*4] bytes (sRGB-encoded rgb,
+ * coverage); gamma_out (optional, [H*W*4]) receives the tone-mapped,
+ * encoded image before FXAA.  orc_srgb_encode / orc_root12_pow5 expose the
+ * encode curve and its r^(5/12) for the pins. */
+void orc_display(const float* hdr, int32_t W, int32_t H, float exposure, int32_t fxaa, float* gamma_out,
+                 uint8_t* out);
+float orc_srgb_encode(float r);
+float orc_root12_pow5(float r);
+
 #ifdef __cplusplus
 }
 #endif
