@@ -218,6 +218,25 @@ int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_came
                       const int32_t* light_off, float* const* outs, const fire_render_opts* opts,
                       void* stream);
 
+/* ---------------------------------------------------------------- display */
+
+/* Display output stage of a rendered image (§IV-A-1: Reinhard tone mapping
+ * c' / (1 + c') of c' = exposure * c per channel, then gamma correction, the
+ * inverse of the sRGB-to-linear conversion (IEC 61966-2-1); §IV-B-2: FXAA,
+ * Lottes' post-process that blends along luma edges), then 8-bit rounding.
+ *   hdr_rgba     device float [H*W*4] as written by fire_render (alpha =
+ *                coverage, quantised as is)
+ *   exposure     > 0
+ *   flags        FIRE_DISPLAY_FXAA or 0
+ *   scratch_rgba device float [H*W*4] (the tone-mapped image before FXAA),
+ *                required with FIRE_DISPLAY_FXAA, else may be NULL
+ *   out_rgba8    device uint8 [H*W*4] sRGB-encoded rgb + coverage
+ * Stateless; asynchronous on `stream`.  Non-finite pixels give unspecified
+ * bytes. */
+#define FIRE_DISPLAY_FXAA 1
+int fire_display(const float* hdr_rgba, int32_t width, int32_t height, float exposure, int32_t flags,
+                 float* scratch_rgba, uint8_t* out_rgba8, void* stream);
+
 /* ------------------------------------------------------- differentiable */
 
 /* Shade a G-buffer (from fire_render) with device-side parameters, holding

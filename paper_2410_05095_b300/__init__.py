@@ -9,4 +9,4 @@ Python is argument marshalling only (fire.py); PyTorch supplies device
 memory and streams.
 """
 from . import fire  # noqa: F401
-from .fire import FireError, Scene, render_batch, batch_last_config  # noqa: F401
+from .fire import FireError, Scene, display, render_batch, batch_last_config  # noqa: F401

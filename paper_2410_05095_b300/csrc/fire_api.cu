@@ -390,6 +390,19 @@ int fire_scene_info(fire_scene s, int64_t* out8) {
   return FIRE_OK;
 }
 
+int fire_display(const float* hdr_rgba, int32_t width, int32_t height, float exposure, int32_t flags,
+                 float* scratch_rgba, uint8_t* out_rgba8, void* stream) {
+  g_err.clear();
+  if (width < 0 || height < 0 || (int64_t)width * height >= ((int64_t)1 << 31))
+    return set_error(FIRE_ERR_INVALID_ARG, "image size out of range");
+  if (!std::isfinite(exposure) || !(exposure > 0.0f)) return set_error(FIRE_ERR_INVALID_ARG, "exposure must be > 0");
+  if ((flags & ~FIRE_DISPLAY_FXAA) != 0) return set_error(FIRE_ERR_INVALID_ARG, "unknown display flags");
+  if ((int64_t)width * height > 0 && (!hdr_rgba || !out_rgba8 || ((flags & FIRE_DISPLAY_FXAA) && !scratch_rgba)))
+    return set_error(FIRE_ERR_INVALID_ARG, "NULL buffer");
+  return display_image(hdr_rgba, width, height, exposure, (flags & FIRE_DISPLAY_FXAA) != 0, scratch_rgba, out_rgba8,
+                       as_stream(stream));
+}
+
 int fire_render_info(fire_scene s, int64_t* out4) {
   g_err.clear();
   if (!s || !out4) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");

@@ -240,6 +240,9 @@ struct RasterArgs {
   uint32_t* ctrl;
 };
 int raster_primary(fire_scene_s* s, const RasterArgs& r, cudaStream_t st);
+// display.cu
+int display_image(const float* hdr, int W, int H, float exposure, bool fxaa, float* scratch, uint8_t* out,
+                  cudaStream_t st);
 int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o, cudaStream_t st);
 int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten, cudaStream_t st);
 int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,

@@ -27,7 +27,7 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_shade_backward", "fire_debug_dump", "fire_sync_status",
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
-           "fire_last_error", "fire_version"]
+           "fire_display", "fire_last_error", "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -89,6 +89,7 @@ def lib():
             "fire_profile_read": [P, P, P],
             "fire_shade_backward_noalloc": [P, P, P, P, i32, P, P, P, P, P, P],
             "fire_render_info": [P, P],
+            "fire_display": [P, i32, i32, C.c_float, i32, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -280,6 +281,20 @@ class Scene:
         ms, n = (C.c_double * 8)(), (C.c_int64 * 8)()
         _check(lib().fire_profile_read(self.h, ms, n))
         return {name: (ms[i], n[i]) for i, name in enumerate(STAGES)}
+
+
+def display(hdr, exposure: float = 1.0, fxaa: bool = True, out=None, scratch=None, stream=None):
+    """Display stage of an [H, W, 4] float CUDA image from render(): Reinhard
+    tone map, sRGB encode, optional FXAA -> [H, W, 4] uint8 CUDA tensor."""
+    import torch
+    H, W = int(hdr.shape[0]), int(hdr.shape[1])
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=hdr.device)
+    if fxaa and scratch is None:
+        scratch = torch.empty((H, W, 4), dtype=torch.float32, device=hdr.device)
+    _check(lib().fire_display(_ptr(hdr), W, H, float(exposure), 1 if fxaa else 0, _ptr(scratch) if fxaa else None,
+                              _ptr(out), _stream(stream)))
+    return out
 
 
 def render_batch(scenes, cams, cam_scene, lights_per_scene, outs, opts: RenderOpts | None = None, stream=None):
