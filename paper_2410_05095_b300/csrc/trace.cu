@@ -27,7 +27,7 @@ namespace {
 // if that pass fell back, MODE 2 takes each sample's hit from its key
 // otherwise; exactly one of the two does the work.
 template <int STACK, int MODE>
-__global__ void __launch_bounds__(128) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
+__global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
   if (MODE != 0 && (MODE == 1) != (a.ctrl[kCtrlRasterFlag] != 0u)) return;
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;
