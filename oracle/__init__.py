@@ -82,6 +82,7 @@ def lib():
         L.orc_shadow_eps.restype = C.c_float
         L.orc_shadow_eps.argtypes = [P]
         L.orc_display.argtypes = [P, i32, i32, C.c_float, i32, P, P]
+        L.orc_set_two_level.argtypes = [P, i32]
         L.orc_srgb_encode.restype = C.c_float
         L.orc_srgb_encode.argtypes = [C.c_float]
         L.orc_root12_pow5.restype = C.c_float
@@ -150,6 +151,11 @@ class OracleScene:
     def update(self, xforms: np.ndarray, rebuild: bool = False):
         x = np.ascontiguousarray(xforms, np.float32).reshape(-1)
         lib().orc_update(self.h, _p(x), int(rebuild))
+
+    def set_two_level(self, enable: bool = True):
+        """Two-level mode: bodies as instances of rest-space geometry."""
+        if lib().orc_set_two_level(self.h, int(bool(enable))) != 0:
+            raise ValueError("two-level mode needs every triangle's vertices in one body")
 
     def get(self, what: str) -> np.ndarray:
         T = self.nt

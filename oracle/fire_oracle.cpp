@@ -81,6 +81,14 @@ struct orc_scene {
   std::vector<Box> box;           // [2nt-1] by Karras code
   float cb[6] = {0, 0, 0, 0, 0, 0};  // centroid bounds
   Box scene_box;
+  // two-level mode (see the two-level section below)
+  bool two_level = false;
+  std::vector<float> xf;              // [nbody*12] transforms of the last update
+  struct BNode { Box box; int32_t left = -1, right = -1, first = 0, count = 0; };
+  struct Body { std::vector<BNode> nodes; std::vector<int32_t> tris; Box rest_box; };
+  std::vector<Body> bodies;           // rest-space BVH per body
+  std::vector<Box> inst_box;          // world box per body (empty bodies: unused)
+  Box inst_union;
 };
 
 namespace {
@@ -338,9 +346,162 @@ void trace_brute(const orc_scene& S, V3 o, V3 d, float tmin, Hit& h) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-level mode (§IV-B-3: one bottom-level structure per mesh in its own
+// frame, built once; a top level over the instances rebuilt every frame).
+// Here a body is an instance: its triangles stay in rest coordinates and a
+// ray meets them in the body's frame.  For the body matrix M = [R | t]
+// (rows m0..m11, rigid) the object-space ray is
+//   q = o - t;  o'_c = fma(R_0c, q.x, fma(R_1c, q.y, R_2c * q.z)),
+//   d'_c = the same with d               (R^T applied: columns of R)
+// and the Moller-Trumbore test runs on the rest triangle with (o', d'); its
+// t ranks hits across bodies with the usual (t, original index) order.  The
+// hit normal is normalize(R cross(e1', e2')) (rows of R), turned to face the
+// ray; the hit point is fma(t, d, o) of the world ray.  The shadow-ray
+// epsilon uses the union of the bodies' world boxes, each the min/max of the
+// 8 transformed corners of the body's rest box.  Each body's triangles must
+// share the body of their vertices.  The per-body trees here are plain
+// median splits (any conservative tree gives the brute-force result).
+// ---------------------------------------------------------------------------
+inline V3 rest_v(const orc_scene& S, uint32_t i) { return mk(S.rest[4 * i], S.rest[4 * i + 1], S.rest[4 * i + 2]); }
+
+Box rest_tri_box(const orc_scene& S, int32_t t) {
+  V3 a = rest_v(S, S.idx[3 * t]), b = rest_v(S, S.idx[3 * t + 1]), c = rest_v(S, S.idx[3 * t + 2]);
+  Box r;
+  const float A[3] = {a.x, a.y, a.z}, B[3] = {b.x, b.y, b.z}, C[3] = {c.x, c.y, c.z};
+  for (int k = 0; k < 3; ++k) {
+    r.lo[k] = std::min(A[k], std::min(B[k], C[k]));
+    r.hi[k] = std::max(A[k], std::max(B[k], C[k]));
+  }
+  return r;
+}
+
+int32_t body_build(const orc_scene& S, orc_scene::Body& B, int32_t first, int32_t count) {
+  orc_scene::BNode nd;
+  nd.box = rest_tri_box(S, B.tris[first]);
+  for (int32_t i = 1; i < count; ++i) nd.box = box_union(nd.box, rest_tri_box(S, B.tris[first + i]));
+  const int32_t me = (int32_t)B.nodes.size();
+  B.nodes.push_back(nd);
+  if (count <= 4) {
+    B.nodes[me].first = first;
+    B.nodes[me].count = count;
+    return me;
+  }
+  int axis = 0;
+  float ext = -1.0f;
+  for (int k = 0; k < 3; ++k)
+    if (nd.box.hi[k] - nd.box.lo[k] > ext) { ext = nd.box.hi[k] - nd.box.lo[k]; axis = k; }
+  auto cen = [&](int32_t t) { Box b = rest_tri_box(S, t); return b.lo[axis] + b.hi[axis]; };
+  const int32_t half = count / 2;
+  std::nth_element(B.tris.begin() + first, B.tris.begin() + first + half, B.tris.begin() + first + count,
+                   [&](int32_t a, int32_t b) { return cen(a) < cen(b) || (cen(a) == cen(b) && a < b); });
+  const int32_t l = body_build(S, B, first, half);
+  const int32_t r = body_build(S, B, first + half, count - half);
+  B.nodes[me].left = l;
+  B.nodes[me].right = r;
+  return me;
+}
+
+bool set_two_level(orc_scene& S) {
+  for (int64_t t = 0; t < S.nt; ++t) {
+    const uint16_t b = S.vbody[S.idx[3 * t]];
+    if (S.vbody[S.idx[3 * t + 1]] != b || S.vbody[S.idx[3 * t + 2]] != b) return false;
+  }
+  S.bodies.assign(S.nbody, orc_scene::Body());
+  for (int64_t t = 0; t < S.nt; ++t) S.bodies[S.vbody[S.idx[3 * t]]].tris.push_back((int32_t)t);
+  for (auto& B : S.bodies) {
+    if (B.tris.empty()) continue;
+    body_build(S, B, 0, (int32_t)B.tris.size());
+    B.rest_box = B.nodes[0].box;
+  }
+  S.two_level = true;
+  return true;
+}
+
+V3 xf_point(const float* m, V3 p) {
+  return mk(std::fmaf(m[0], p.x, std::fmaf(m[1], p.y, std::fmaf(m[2], p.z, m[3]))),
+            std::fmaf(m[4], p.x, std::fmaf(m[5], p.y, std::fmaf(m[6], p.z, m[7]))),
+            std::fmaf(m[8], p.x, std::fmaf(m[9], p.y, std::fmaf(m[10], p.z, m[11]))));
+}
+
+void instance_boxes(orc_scene& S) {
+  S.inst_box.assign(S.nbody, Box());
+  bool any = false;
+  for (int b = 0; b < S.nbody; ++b) {
+    const auto& B = S.bodies[b];
+    if (B.tris.empty()) continue;
+    const float* m = S.xf.data() + 12 * b;
+    Box w;
+    for (int c = 0; c < 8; ++c) {
+      V3 p = xf_point(m, mk((c & 1) ? B.rest_box.hi[0] : B.rest_box.lo[0], (c & 2) ? B.rest_box.hi[1] : B.rest_box.lo[1],
+                            (c & 4) ? B.rest_box.hi[2] : B.rest_box.lo[2]));
+      const float P[3] = {p.x, p.y, p.z};
+      for (int k = 0; k < 3; ++k) {
+        w.lo[k] = c ? std::min(w.lo[k], P[k]) : P[k];
+        w.hi[k] = c ? std::max(w.hi[k], P[k]) : P[k];
+      }
+    }
+    S.inst_box[b] = w;
+    S.inst_union = any ? box_union(S.inst_union, w) : w;
+    any = true;
+  }
+}
+
+void object_ray(const float* m, V3 o, V3 d, V3& oo, V3& dd) {
+  V3 q = sub3(o, mk(m[3], m[7], m[11]));
+  oo = mk(std::fmaf(m[0], q.x, std::fmaf(m[4], q.y, m[8] * q.z)),
+          std::fmaf(m[1], q.x, std::fmaf(m[5], q.y, m[9] * q.z)),
+          std::fmaf(m[2], q.x, std::fmaf(m[6], q.y, m[10] * q.z)));
+  dd = mk(std::fmaf(m[0], d.x, std::fmaf(m[4], d.y, m[8] * d.z)),
+          std::fmaf(m[1], d.x, std::fmaf(m[5], d.y, m[9] * d.z)),
+          std::fmaf(m[2], d.x, std::fmaf(m[6], d.y, m[10] * d.z)));
+}
+
+// Nearest hit (any = false) or any hit in (0, tmax) other than `skip` in
+// body b's frame; bvh = false tests every triangle of the body.
+bool body_trace(const orc_scene& S, int b, V3 o, V3 d, float tmin, float tmax, int32_t skip, bool any,
+                bool bvh, bool want2, Hit& h) {
+  const auto& B = S.bodies[b];
+  if (B.tris.empty()) return false;
+  V3 oo, dd;
+  object_ray(S.xf.data() + 12 * b, o, d, oo, dd);
+  auto test = [&](int32_t tri) {
+    if (tri == skip) return false;
+    float t, u, v;
+    V3 a = rest_v(S, S.idx[3 * tri]), bb = rest_v(S, S.idx[3 * tri + 1]), c = rest_v(S, S.idx[3 * tri + 2]);
+    if (!(mt_hit(oo, dd, a, bb, c, t, u, v) && t > tmin && t < tmax)) return false;
+    if (any) return true;
+    consider(h, tri, t, u, v);
+    return false;
+  };
+  if (!bvh) {
+    for (int32_t tri : B.tris) if (test(tri)) return true;
+    return false;
+  }
+  std::vector<int32_t> stack(1, 0);
+  while (!stack.empty()) {
+    const auto& nd = B.nodes[stack.back()];
+    stack.pop_back();
+    double bound = any ? (double)tmax : (want2 ? (double)h.t2 : (double)h.t);
+    double tn;
+    if (!box_hit(nd.box, oo, dd, tmin, bound, tn)) continue;
+    if (nd.left < 0) {
+      for (int32_t i = 0; i < nd.count; ++i) if (test(B.tris[nd.first + i])) return true;
+    } else {
+      stack.push_back(nd.right);
+      stack.push_back(nd.left);
+    }
+  }
+  return false;
+}
+
 Hit trace(const orc_scene& S, V3 o, V3 d, float tmin, bool bvh, bool want2) {
   Hit h;
   if (S.nt == 0) return h;
+  if (S.two_level) {
+    for (int b = 0; b < S.nbody; ++b) body_trace(S, b, o, d, tmin, kInfF, -1, false, bvh, want2, h);
+    return h;
+  }
   if (bvh) trace_bvh(S, o, d, tmin, h, want2); else trace_brute(S, o, d, tmin, h);
   return h;
 }
@@ -348,6 +509,12 @@ Hit trace(const orc_scene& S, V3 o, V3 d, float tmin, bool bvh, bool want2) {
 // Any hit with 0 < t < tmax, skipping triangle `skip`.
 bool occluded(const orc_scene& S, V3 o, V3 d, float tmax, int32_t skip, bool bvh) {
   if (S.nt == 0) return false;
+  if (S.two_level) {
+    Hit unused;
+    for (int b = 0; b < S.nbody; ++b)
+      if (body_trace(S, b, o, d, 0.0f, tmax, skip, true, bvh, false, unused)) return true;
+    return false;
+  }
   auto test = [&](int64_t tri) {
     if ((int32_t)tri == skip) return false;
     V3 a, b, c;
@@ -466,8 +633,8 @@ struct SampleOut { int32_t prim; float t, t2; uint16_t vis; float rgb[3]; };
 
 float scene_eps(const orc_scene& S) {
   if (S.nt == 0) return 0.0f;
-  V3 ext = mk(S.scene_box.hi[0] - S.scene_box.lo[0], S.scene_box.hi[1] - S.scene_box.lo[1],
-              S.scene_box.hi[2] - S.scene_box.lo[2]);
+  const Box& B = S.two_level ? S.inst_union : S.scene_box;
+  V3 ext = mk(B.hi[0] - B.lo[0], B.hi[1] - B.lo[1], B.hi[2] - B.lo[2]);
   return 1e-4f * std::sqrt(dot3(ext, ext));
 }
 
@@ -493,9 +660,20 @@ void light_vec(const orc_light& L, V3 po, V3& l, float& E, float& tmax) {
 // face the ray; shadow origin po = fma(eps, n, p).
 void hit_frame(const orc_scene& S, int32_t prim, V3 o, V3 d, float t, float eps, V3& n, V3& po) {
   V3 a, b, c;
-  tri_verts(S, prim, a, b, c);
-  V3 e1 = sub3(b, a), e2 = sub3(c, a);
-  n = normalize3(cross3(e1, e2));
+  if (S.two_level) {
+    a = rest_v(S, S.idx[3 * prim]);
+    b = rest_v(S, S.idx[3 * prim + 1]);
+    c = rest_v(S, S.idx[3 * prim + 2]);
+    const float* m = S.xf.data() + 12 * S.vbody[S.idx[3 * prim]];
+    V3 cr = cross3(sub3(b, a), sub3(c, a));
+    n = normalize3(mk(std::fmaf(m[0], cr.x, std::fmaf(m[1], cr.y, m[2] * cr.z)),
+                      std::fmaf(m[4], cr.x, std::fmaf(m[5], cr.y, m[6] * cr.z)),
+                      std::fmaf(m[8], cr.x, std::fmaf(m[9], cr.y, m[10] * cr.z))));
+  } else {
+    tri_verts(S, prim, a, b, c);
+    V3 e1 = sub3(b, a), e2 = sub3(c, a);
+    n = normalize3(cross3(e1, e2));
+  }
   if (dot3(n, d) > 0.0f) n = neg3(n);
   V3 p = mk(std::fmaf(t, d.x, o.x), std::fmaf(t, d.y, o.y), std::fmaf(t, d.z, o.z));
   po = mk(std::fmaf(eps, n.x, p.x), std::fmaf(eps, n.y, p.y), std::fmaf(eps, n.z, p.z));
@@ -644,6 +822,18 @@ int32_t orc_update(orc_scene* s, const float* xforms, int32_t rebuild) {
   transform(*s, xforms);
   if (rebuild || !s->built) build(*s);
   refit_all(*s);
+  s->xf.assign(xforms, xforms + 12 * s->nbody);
+  if (s->two_level) instance_boxes(*s);
+  return 0;
+}
+
+int32_t orc_set_two_level(orc_scene* s, int32_t enable) {
+  if (!enable) {
+    s->two_level = false;
+    return 0;
+  }
+  if (!set_two_level(*s)) return -1;
+  if (!s->xf.empty()) instance_boxes(*s);
   return 0;
 }
 

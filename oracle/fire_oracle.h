@@ -35,6 +35,13 @@ int32_t orc_set_materials(orc_scene* s, const orc_material* mats, int32_t nmat);
  * (rebuild != 0 or first call) or refit it with the topology kept. */
 int32_t orc_update(orc_scene* s, const float* xforms, int32_t rebuild);
 
+/* Two-level mode (§IV-B-3 per-mesh bottom level + per-frame top level): each
+ * body's triangles stay in rest coordinates and rays meet them in the body's
+ * frame (object ray = R^T (o - t), R^T d); nearest hits rank by the object-
+ * space t.  Every triangle's vertices must share one body, else -1.  Trace,
+ * occlusion, rendering and the shading frame follow the mode. */
+int32_t orc_set_two_level(orc_scene* s, int32_t enable);
+
 /* what: 0 world verts [nv*3] f32; 1 morton codes by original tri [nt] u64;
  * 2 sorted order [nt] u32; 3 children [(nt-1)*2] i32 (Karras codes: internal
  * i < nt-1, leaf = nt-1+sorted position); 4 parent [2nt-1] i32 (root -1);

@@ -243,7 +243,7 @@ def _kd_labels(cs, nbody: int):
     start = [(b * n + nbody - 1) // nbody for b in range(nbody + 1)]  # first id of body b
 
     def rec(ids, b0, b1):
-        if b1 - b0 <= 1:
+        if b1 - b0 <= 1 or len(ids) <= 1:  # (fewer spheres than bodies: empty bodies)
             return list(ids)
         mid = (b0 + b1) // 2
         cnt = start[mid] - start[b0]

@@ -1,0 +1,89 @@
+"""Pins of the oracle's two-level mode (bodies as instances of rest-space
+geometry, rays met in each body's frame): identity poses reduce it to the
+single-level renderer bit for bit; its per-body trees equal brute force
+over every body's triangles; under rigid motion it agrees with the
+single-level (world-space) renderer up to near ties (A9)."""
+import numpy as np
+
+import oracle
+import scenegen as sg
+
+TIE_REL = 1e-5
+
+
+def _scene():
+    w = sg.workload_frame7m(nspheres=24, cells=8)
+    return w, w.scene
+
+
+def _pair(sc, xf):
+    one, two = oracle.OracleScene(sc), oracle.OracleScene(sc)
+    one.update(xf, rebuild=True)
+    two.set_two_level(True)
+    two.update(xf, rebuild=True)
+    return one, two
+
+
+def test_identity_poses_equal_single_level():
+    w, sc = _scene()
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 40, 24, 4)
+    one, two = _pair(sc, sc.identity_xforms())
+    a = one.render_all_samples(cam, w.lights)
+    b = two.render_all_samples(cam, w.lights)
+    for k in ("prim", "t", "vis", "rgb"):
+        assert np.array_equal(a[k], b[k]), k
+    assert (a["prim"] >= 0).mean() > 0.3
+    assert one.shadow_eps() == two.shadow_eps()
+
+
+def test_body_trees_equal_brute_force_under_motion():
+    w, sc = _scene()
+    for _ in range(5):
+        w.motion.step()
+    _, two = _pair(sc, w.motion.xforms())
+    rng = np.random.default_rng(11)
+    n = 400
+    o = np.tile(np.float32(w.camera.pos), (n, 1)) + rng.normal(0, 0.5, (n, 3)).astype(np.float32)
+    tgt = rng.uniform(-10, 10, (n, 3)).astype(np.float32)
+    tgt[:, 1] = rng.uniform(-2, 3, n)
+    d = tgt - o
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    p1, t1, _, _, s1 = two.trace(o, d, bvh=True, want_t2=True)
+    p2, t2, _, _, s2 = two.trace(o, d, bvh=False, want_t2=True)
+    assert np.array_equal(p1, p2) and np.array_equal(t1, t2) and np.array_equal(s1, s2)
+    assert (p1 >= 0).mean() > 0.2
+    tmax = rng.uniform(0.5, 30, n).astype(np.float32)
+    skip = np.where(p1 >= 0, p1, -1).astype(np.int32)
+    assert np.array_equal(two.occluded(o, d, tmax, skip, bvh=True), two.occluded(o, d, tmax, skip, bvh=False))
+
+
+def test_two_level_agrees_with_single_level_under_motion():
+    w, sc = _scene()
+    for _ in range(10):
+        w.motion.step()
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 48, 32, 4)
+    one, two = _pair(sc, w.motion.xforms())
+    a = one.render_all_samples(cam, w.lights)
+    b = two.render_all_samples(cam, w.lights)
+    bad = (a["prim"] != b["prim"]) | (a["vis"] != b["vis"])
+    # different rounding (world triangles vs body-frame rays): disagreements
+    # only where the single-level renderer's two nearest hits nearly tie
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(a["t2"]) & (np.abs(a["t2"] - a["t"]) <= TIE_REL * np.abs(a["t"]))
+    vis_only = (a["prim"] == b["prim"]) & (a["vis"] != b["vis"])
+    assert bad.mean() <= 1e-3
+    assert not (bad & ~tie & ~vis_only).any()
+    # hit distances agree to rounding
+    same = (a["prim"] == b["prim"]) & (a["prim"] >= 0)
+    assert np.max(np.abs(a["t"][same] - b["t"][same]) / a["t"][same]) < 1e-5
+
+
+def test_two_level_needs_one_body_per_triangle():
+    sc = sg.assemble([(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.0]]), np.array([[0, 1, 2]]))], 1,
+                     sg.random_materials(sg.Rng(3), 1))
+    sc.vert_body[:] = [0, 1, 0]
+    sc.nbody = 2
+    S = oracle.OracleScene(sc)
+    import pytest
+    with pytest.raises(ValueError):
+        S.set_two_level(True)
