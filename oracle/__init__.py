@@ -87,6 +87,11 @@ def lib():
         L.orc_srgb_encode.argtypes = [C.c_float]
         L.orc_root12_pow5.restype = C.c_float
         L.orc_root12_pow5.argtypes = [C.c_float]
+        L.orc_set_materials_srgb.argtypes = [P, P, i32]
+        L.orc_srgb_decode.restype = C.c_float
+        L.orc_srgb_decode.argtypes = [C.c_float]
+        L.orc_set_normals.argtypes = [P, P]
+        L.orc_shading_normal.argtypes = [P, i32, P, P, P]
         _lib = L
     return _lib
 
@@ -147,6 +152,28 @@ class OracleScene:
     def set_materials(self, mats: np.ndarray):
         self.mats = make_materials(mats)
         assert lib().orc_set_materials(self.h, C.cast(self.mats, C.c_void_p), len(mats)) == 0
+
+    def set_materials_srgb(self, mats: np.ndarray):
+        """Materials whose albedo is sRGB-encoded (decoded once to linear)."""
+        self.mats = make_materials(mats)
+        assert lib().orc_set_materials_srgb(self.h, C.cast(self.mats, C.c_void_p), len(mats)) == 0
+
+    def set_normals(self, normals):
+        """Rest-pose vertex normals [nv, 4] (smooth shading); None = flat."""
+        if normals is None:
+            self._nrm = None
+            lib().orc_set_normals(self.h, None)
+            return
+        self._nrm = np.ascontiguousarray(normals, np.float32).reshape(self.nv, 4)
+        lib().orc_set_normals(self.h, _p(self._nrm))
+
+    def shading_normal(self, prim: int, o, d) -> np.ndarray:
+        """Shading normal of the ray (o, d) meeting triangle prim."""
+        o = np.ascontiguousarray(o, np.float32)
+        d = np.ascontiguousarray(d, np.float32)
+        n = np.zeros(3, np.float32)
+        lib().orc_shading_normal(self.h, int(prim), _p(o), _p(d), _p(n))
+        return n
 
     def update(self, xforms: np.ndarray, rebuild: bool = False):
         x = np.ascontiguousarray(xforms, np.float32).reshape(-1)
@@ -324,3 +351,7 @@ def srgb_encode(r: float) -> float:
 
 def root12_pow5(r: float) -> float:
     return float(lib().orc_root12_pow5(float(r)))
+
+
+def srgb_decode(c: float) -> float:
+    return float(lib().orc_srgb_decode(float(c)))

@@ -89,6 +89,8 @@ struct orc_scene {
   std::vector<Body> bodies;           // rest-space BVH per body
   std::vector<Box> inst_box;          // world box per body (empty bodies: unused)
   Box inst_union;
+  // smooth shading: rest-pose vertex normals [nv*4] (xyz; empty = flat)
+  std::vector<float> vnrm;
 };
 
 namespace {
@@ -679,6 +681,46 @@ void hit_frame(const orc_scene& S, int32_t prim, V3 o, V3 d, float t, float eps,
   po = mk(std::fmaf(eps, n.x, p.x), std::fmaf(eps, n.y, p.y), std::fmaf(eps, n.z, p.z));
 }
 
+// ---------------------------------------------------------------------------
+// Smooth shading normal (§IV-A-1: the main pass shades with the meshes'
+// per-vertex normal attribute, as glTF-like assets carry it).  For the hit
+// of the ray (o, d) on triangle prim:
+//   (u, v)  barycentrics from the ray/triangle test of the world-space
+//           triangle (the same FP32 steps that found the hit), so the point
+//           is (1-u-v) v0 + u v1 + v v2
+//   n_r     = fma(v, n2, fma(u, n1, w0 n0)) per component, w0 = (1 - u) - v,
+//           from the rest normals n0, n1, n2 of the triangle's vertices
+//   n_w     = R n_r with the rows of the body's rotation R (normals of a
+//           rigid body turn with it; no translation)
+//   n_s     = normalize(n_w), then negated if n_s . n_g < 0, n_g being the
+//           geometric normal already turned to face the ray; a zero n_w
+//           keeps n_g
+// n_s replaces n in n.l, n.v, n.h (shading and the cast test of the shadow
+// rays); the shadow origin stays lifted along n_g.
+// ---------------------------------------------------------------------------
+V3 shading_normal(const orc_scene& S, int32_t prim, V3 o, V3 d, V3 ng) {
+  if (S.vnrm.empty()) return ng;
+  const uint32_t i[3] = {S.idx[3 * prim], S.idx[3 * prim + 1], S.idx[3 * prim + 2]};
+  V3 a, b, c;
+  tri_verts(S, prim, a, b, c);
+  float t, u, v;
+  mt_hit(o, d, a, b, c, t, u, v);
+  V3 nn[3];
+  for (int k = 0; k < 3; ++k) nn[k] = mk(S.vnrm[4 * i[k]], S.vnrm[4 * i[k] + 1], S.vnrm[4 * i[k] + 2]);
+  const float w0 = (1.0f - u) - v;
+  const V3 nr = mk(std::fmaf(v, nn[2].x, std::fmaf(u, nn[1].x, w0 * nn[0].x)),
+                   std::fmaf(v, nn[2].y, std::fmaf(u, nn[1].y, w0 * nn[0].y)),
+                   std::fmaf(v, nn[2].z, std::fmaf(u, nn[1].z, w0 * nn[0].z)));
+  const float* m = S.xf.data() + 12 * S.vbody[i[0]];
+  const V3 nw = mk(std::fmaf(m[0], nr.x, std::fmaf(m[1], nr.y, m[2] * nr.z)),
+                   std::fmaf(m[4], nr.x, std::fmaf(m[5], nr.y, m[6] * nr.z)),
+                   std::fmaf(m[8], nr.x, std::fmaf(m[9], nr.y, m[10] * nr.z)));
+  if (!(dot3(nw, nw) > 0.0f)) return ng;
+  V3 ns = normalize3(nw);
+  if (dot3(ns, ng) < 0.0f) ns = neg3(ns);
+  return ns;
+}
+
 SampleOut shade_sample(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, int y,
                        int s, bool bvh, bool want2) {
   SampleOut out;
@@ -693,6 +735,7 @@ SampleOut shade_sample(const orc_scene& S, const Cam& K, const orc_light* L, int
   float eps = scene_eps(S);
   V3 n, po;
   hit_frame(S, h.prim, o, d, h.t, eps, n, po);
+  n = shading_normal(S, h.prim, o, d, n);
   V3 v = neg3(d);
   const orc_material& M = S.mats[S.tri_mat[h.prim]];
   for (int j = 0; j < nl; ++j) {
@@ -729,6 +772,7 @@ bool geo64(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, 
   V3 o = K.o, d = cam_dir(K, x, y, s);
   V3 n, po;
   hit_frame(S, prim, o, d, t, scene_eps(S), n, po);
+  n = shading_normal(S, prim, o, d, n);
   V3 v = neg3(d);
   G.nlights = nl;
   for (int j = 0; j < nl; ++j) {
@@ -816,6 +860,41 @@ int32_t orc_set_materials(orc_scene* s, const orc_material* mats, int32_t nmat) 
   if (nmat != s->nmat) return -1;
   s->mats.assign(mats, mats + nmat);
   return 0;
+}
+
+// sRGB-encoded colour to linear (IEC 61966-2-1 decode, §IV-A-1 colour
+// inputs): c / 12.92 for c <= 0.04045, else ((c + 0.055) / 1.055)^2.4;
+// evaluated in FP64 and rounded to FP32 once.
+float orc_srgb_decode(float c) {
+  const double x = c;
+  return (float)(x <= 0.04045 ? x / 12.92 : std::pow((x + 0.055) / 1.055, 2.4));
+}
+
+int32_t orc_set_materials_srgb(orc_scene* s, const orc_material* mats, int32_t nmat) {
+  if (nmat != s->nmat) return -1;
+  s->mats.assign(mats, mats + nmat);
+  for (auto& M : s->mats)
+    for (int c = 0; c < 3; ++c) M.albedo[c] = orc_srgb_decode(M.albedo[c]);
+  return 0;
+}
+
+int32_t orc_set_normals(orc_scene* s, const float* nrm4) {
+  if (!nrm4) {
+    s->vnrm.clear();
+    return 0;
+  }
+  s->vnrm.assign(nrm4, nrm4 + 4 * s->nv);
+  return 0;
+}
+
+void orc_shading_normal(const orc_scene* s, int32_t prim, const float* o, const float* d, float* n3) {
+  const orc_scene& S = *s;
+  V3 O = mk(o[0], o[1], o[2]), D = mk(d[0], d[1], d[2]), a, b, c;
+  tri_verts(S, prim, a, b, c);
+  V3 ng = normalize3(cross3(sub3(b, a), sub3(c, a)));
+  if (dot3(ng, D) > 0.0f) ng = neg3(ng);
+  V3 ns = shading_normal(S, prim, O, D, ng);
+  n3[0] = ns.x; n3[1] = ns.y; n3[2] = ns.z;
 }
 
 int32_t orc_update(orc_scene* s, const float* xforms, int32_t rebuild) {

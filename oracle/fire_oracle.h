@@ -30,6 +30,19 @@ orc_scene* orc_scene_new(const float* verts4, int64_t nv, const uint32_t* idx, i
                          const orc_material* mats, int32_t nmat, int32_t nbody);
 void orc_scene_free(orc_scene* s);
 int32_t orc_set_materials(orc_scene* s, const orc_material* mats, int32_t nmat);
+/* Materials whose albedo is sRGB-encoded: decoded to linear (orc_srgb_decode)
+ * once, then used as by orc_set_materials. */
+int32_t orc_set_materials_srgb(orc_scene* s, const orc_material* mats, int32_t nmat);
+float orc_srgb_decode(float c);
+
+/* Smooth shading (§IV-A-1 per-vertex normals): rest-pose vertex normals
+ * [nv*4] (xyz, w unused), interpolated with the hit's barycentrics, turned by
+ * the body's rotation, normalised and put on the facing side of the
+ * geometric normal; NULL = flat (geometric) normals.  orc_shading_normal
+ * gives that normal for the ray (o, d) meeting triangle prim (world frame of
+ * the last update). */
+int32_t orc_set_normals(orc_scene* s, const float* nrm4);
+void orc_shading_normal(const orc_scene* s, int32_t prim, const float* o, const float* d, float* n3);
 
 /* Transform vertices by the per-body 3x4 row-major matrices; build the LBVH
  * (rebuild != 0 or first call) or refit it with the topology kept. */

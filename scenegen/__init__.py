@@ -204,6 +204,25 @@ class Scene:
         return x
 
 
+def vertex_normals(scene: Scene) -> np.ndarray:
+    """Per-vertex rest-pose normals, as a glTF-like asset carries them: the
+    area-weighted mean of the incident faces' normals (sum of the faces'
+    unnormalised cross products in FP64, normalised).  float32 [V, 4], w = 0;
+    a vertex with no face (or a zero sum) gets (0, 1, 0)."""
+    v = scene.verts[:, :3].astype(np.float64)
+    f = scene.idx.astype(np.int64)
+    fn = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+    acc = np.zeros_like(v)
+    for k in range(3):
+        np.add.at(acc, f[:, k], fn)
+    ln = np.linalg.norm(acc, axis=1)
+    out = np.zeros((len(v), 4), dtype=np.float32)
+    ok = ln > 0
+    out[ok, :3] = acc[ok] / ln[ok, None]
+    out[~ok, 1] = 1.0
+    return out
+
+
 def random_materials(rng: Rng, nmat: int) -> np.ndarray:
     m = np.zeros(nmat, dtype=MATERIAL_DTYPE)
     for i in range(nmat):
