@@ -111,7 +111,8 @@ typedef struct {
 /* One G-buffer record per sample, sample id = (y*W + x)*spp + k:
  * prim = original triangle index of the nearest hit (-1 = miss), t = hit
  * distance along the unit ray, vis = bit j set if light j was cast
- * (n.l > 0) and unoccluded, bit 8+j set if light j was cast. */
+ * (n.l > 0, n the shading normal) and unoccluded, bit 8+j set if light j
+ * was cast. */
 typedef struct {
   int32_t prim;
   float t;
@@ -142,6 +143,35 @@ int fire_scene_destroy(fire_scene s);
 
 /* Replace the materials (host array of the same length nmat). */
 int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nmat);
+
+/* As fire_scene_set_materials; with FIRE_MATERIALS_SRGB_ALBEDO the albedo
+ * values are sRGB-encoded (as glTF-like assets store colours) and are
+ * decoded to linear on the device before shading (§IV-A-1: colour inputs are
+ * converted from sRGB to linear): c / 12.92 for c <= 0.04045, else
+ * ((c + 0.055) / 1.055)^2.4.  Roughness and metallic are not colours and are
+ * kept.  Unknown flag bits -> FIRE_ERR_INVALID_ARG.  (fire_shade and
+ * fire_shade_backward take their material table as an argument: it is
+ * linear.) */
+#define FIRE_MATERIALS_SRGB_ALBEDO 1
+int fire_scene_set_materials_ex(fire_scene s, const fire_material* mats, int32_t nmat, int32_t flags);
+
+/* Smooth shading (§IV-A-1: the main pass shades with the meshes' per-vertex
+ * normal attribute).  normals: [nv*4] floats, rest-pose normal of each
+ * vertex in xyz (w ignored), host or device memory (on_device != 0; host
+ * values must be finite, else FIRE_ERR_INVALID_ARG); copied.  NULL returns
+ * the scene to flat shading.  At a hit with barycentrics (u, v) (from the
+ * same FP32 triangle test that found it) the shading normal is
+ *   n_s = normalize(R (w0 n0 + u n1 + v n2)), w0 = (1 - u) - v,
+ * evaluated as fma(v, n2, fma(u, n1, w0 n0)) per component, R = rotation of
+ * the vertex's body in the matrices of the frame being rendered; n_s is
+ * negated if it points away from the ray's side of the triangle, and a zero
+ * interpolated normal keeps the geometric one.  n_s replaces the geometric
+ * normal in the shading (n.l, n.v, n.h) and in the decision to cast a
+ * shadow ray (n_s . l > 0); the shadow-ray origin stays lifted along the
+ * geometric normal.  Applies to fire_render, fire_render_batch, fire_shade
+ * and the backward calls.  Replacing or clearing the normals synchronises
+ * the device (renders in flight may read them). */
+int fire_scene_set_normals(fire_scene s, const float* normals, int32_t on_device, void* stream);
 
 /* Scene sizes: out[0] = nv, out[1] = nt, out[2] = nmat, out[3] = nbody,
  * out[4] = binary tree height (after a build), out[5] = device bytes held,

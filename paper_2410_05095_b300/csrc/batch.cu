@@ -29,6 +29,7 @@ struct BatchCam {
   const float4* tris;
   int64_t nt;
   const float* mats;
+  SmoothCtx sm;           // smooth shading inputs (sm.vnrm == nullptr: flat)
   float* out;
   uint32_t* err;          // the scene's sticky error word
   int64_t sample_base;    // first global sample id of this camera
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(128) k_bprimary(const BatchCam* __restrict__ c
       if (prim >= 0) {
         float4 B = __ldg(bc.tris + 3 * (int64_t)pos + 1), C = __ldg(bc.tris + 3 * (int64_t)pos + 2);
         hit_frame(B, C, o, d, t, eps, n, po);
+        if (bc.sm.vnrm) n = shading_normal(bc.sm, pos, __ldg(bc.tris + 3 * (int64_t)pos), B, C, o, d, n);
       }
     }
     uint32_t cast = 0;
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(128) k_bresolve(const BatchCam* __restrict__ c
         float4 B = __ldg(bc.tris + 3 * (int64_t)rr.w + 1), C = __ldg(bc.tris + 3 * (int64_t)rr.w + 2);
         float3 n, po;
         hit_frame(B, C, o, d, __int_as_float(rr.y), eps, n, po);
+        if (bc.sm.vnrm) n = shading_normal(bc.sm, rr.w, __ldg(bc.tris + 3 * (int64_t)rr.w), B, C, o, d, n);
         float3 v = neg3(d);
         const float* mp = bc.mats + 5 * (int64_t)__float_as_uint(B.w);
         float ar = __ldg(mp), ag = __ldg(mp + 1), ab = __ldg(mp + 2), rough = __ldg(mp + 3), metal = __ldg(mp + 4);
@@ -301,6 +304,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     b.tris = s->tris;
     b.nt = s->nt;
     b.mats = s->mats;
+    b.sm = SmoothCtx{s->vnrm, s->xf_buf[s->cur], s->sidx, s->vbody};
     b.out = outs[i];
     b.cam = make_cam(cams[i]);
     int sc = cam_scene[i];

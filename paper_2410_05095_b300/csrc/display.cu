@@ -131,7 +131,25 @@ __global__ void __launch_bounds__(256) k_fxaa(DisplayConsts C, const float4* __r
   out[p] = pack(quant(c.x), quant(c.y), quant(c.z), quant(M.w));
 }
 
+// sRGB-encoded albedo to linear (IEC 61966-2-1 decode; §IV-A-1 converts
+// sRGB colour inputs to linear before lighting): c / 12.92 at or below
+// 0.04045, else ((c + 0.055) / 1.055)^2.4, on the three albedo entries of
+// each 5-float material record.
+__global__ void k_srgb_decode(float* mats, int nmat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nmat) return;
+  float* p = mats + 5 * (i / 3) + i % 3;
+  const float c = *p;
+  *p = c <= 0.04045f ? c / 12.92f : powf((c + 0.055f) / 1.055f, 2.4f);
+}
+
 }  // namespace
+
+int srgb_decode_materials(float* mats, int nmat, cudaStream_t st) {
+  if (nmat <= 0) return FIRE_OK;
+  k_srgb_decode<<<(3 * nmat + 255) / 256, 256, 0, st>>>(mats, nmat);
+  return cuda_check(cudaGetLastError(), "sRGB decode");
+}
 
 int display_image(const float* hdr, int W, int H, float exposure, bool fxaa, float* scratch, uint8_t* out,
                   cudaStream_t st) {

@@ -204,6 +204,9 @@ namespace {
 void free_scene(fire_scene_s* s) {
   delete static_cast<Profiler*>(s->prof);
   s->prof = nullptr;
+  void* ptrs0[] = {s->vnrm, s->xf_buf[0], s->xf_buf[1]};
+  for (void* p : ptrs0)
+    if (p) cudaFree(p);
   void* ptrs[] = {s->rest, s->idx, s->tmat, s->vbody, s->mats, s->xf, s->keys, s->keys_orig, s->order,
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris_buf[0],
                   s->tris_buf[1], s->nodes4_buf[0], s->nodes4_buf[1], s->cen,
@@ -331,7 +334,8 @@ int fire_scene_create(const float* verts_xyzw, int64_t nv, const uint32_t* tri_i
   struct A { void** p; size_t b; } list[] = {
       {(void**)&s->rest, 16 * (size_t)nv}, {(void**)&s->idx, 12 * (size_t)nt}, {(void**)&s->tmat, 4 * (size_t)nt},
       {(void**)&s->vbody, 2 * (size_t)nv}, {(void**)&s->mats, 20 * (size_t)nmat},
-      {(void**)&s->xf, 48 * (size_t)nbody}, {(void**)&s->ctrl, 128}};
+      {(void**)&s->xf, 48 * (size_t)nbody}, {(void**)&s->xf_buf[0], 48 * (size_t)nbody},
+      {(void**)&s->xf_buf[1], 48 * (size_t)nbody}, {(void**)&s->ctrl, 128}};
   for (auto& a : list) {
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) {
       int rc = cuda_check(e, "scene buffers");
@@ -369,11 +373,48 @@ int fire_scene_destroy(fire_scene s) {
 }
 
 int fire_scene_set_materials(fire_scene s, const fire_material* mats, int32_t nmat) {
+  return fire_scene_set_materials_ex(s, mats, nmat, 0);
+}
+
+int fire_scene_set_materials_ex(fire_scene s, const fire_material* mats, int32_t nmat, int32_t flags) {
   g_err.clear();
   if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
   if (nmat != s->nmat) return set_error(FIRE_ERR_INVALID_ARG, "material count differs from the scene's");
+  if (flags & ~FIRE_MATERIALS_SRGB_ALBEDO) return set_error(FIRE_ERR_INVALID_ARG, "unknown material flags");
   if (int e = check_mats(mats, nmat)) return e;
-  return upload_mats(s, mats, s->last_stream);
+  if (int e = upload_mats(s, mats, s->last_stream)) return e;
+  if (flags & FIRE_MATERIALS_SRGB_ALBEDO) return srgb_decode_materials(s->mats, s->nmat, s->last_stream);
+  return FIRE_OK;
+}
+
+int fire_scene_set_normals(fire_scene s, const float* normals, int32_t on_device, void* stream) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  cudaStream_t st = as_stream(stream);
+  if (!normals) {
+    if (s->vnrm) {
+      // renders in flight may still read the normals
+      if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
+      cudaFree(s->vnrm);
+      s->bytes -= 16 * (size_t)s->nv;
+      s->vnrm = nullptr;
+    }
+    return FIRE_OK;
+  }
+  if (!on_device)
+    for (int64_t i = 0; i < 4 * s->nv; ++i)
+      if (i % 4 != 3 && !std::isfinite(normals[i])) return set_error(FIRE_ERR_INVALID_ARG, "non-finite normal");
+  if (!s->vnrm) {
+    if (cudaError_t e = dev_alloc((void**)&s->vnrm, 16 * (size_t)s->nv, &s->bytes)) return cuda_check(e, "normals");
+  } else {
+    // renders in flight may still read the old normals
+    if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
+  }
+  s->last_stream = st;
+  if (s->nv == 0) return FIRE_OK;
+  if (int e = cuda_check(cudaMemcpyAsync(s->vnrm, normals, 16 * (size_t)s->nv, cudaMemcpyDefault, st), "normals"))
+    return e;
+  return on_device ? FIRE_OK : cuda_check(cudaStreamSynchronize(st), "normals");
 }
 
 int fire_scene_info(fire_scene s, int64_t* out8) {
@@ -485,6 +526,7 @@ static int fill_args(fire_scene s, const fire_camera* cam, const fire_light* lig
   a->row_end = cam->height;
   a->iter_cap = s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64;
   a->ctrl = s->ctrl;
+  set_smooth_args(a, s);
   return FIRE_OK;
 }
 

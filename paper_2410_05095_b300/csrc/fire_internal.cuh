@@ -108,6 +108,11 @@ struct fire_scene_s {
   float* mats = nullptr;        // [nmat*5] device copy
   std::vector<fire_material> h_mats;
   float* xf = nullptr;          // [nbody*12]
+  // smooth shading: rest-pose vertex normals (nullptr = flat normals) and,
+  // per frame buffer, the body matrices the buffer was refit with (the
+  // normals turn with them while the next refit loads new matrices)
+  float4* vnrm = nullptr;       // [nv]
+  float* xf_buf[2] = {nullptr, nullptr};  // [nbody*12] each
   // LBVH
   bool built = false;
   int height = 0;               // internal levels on the longest root-leaf path
@@ -215,6 +220,12 @@ struct RenderArgs {
   uint32_t* ctrl;               // counters + error word
   const unsigned long long* rkeys;  // raster keys (primary in key mode) or nullptr
   const int32_t* rank;          // [nt] original triangle -> sorted position
+  // smooth shading (vnrm != nullptr): rest vertex normals, the frame's body
+  // matrices, sorted index records (the hit triangle's vertices), vertex -> body
+  const float4* vnrm;
+  const float* bxf;
+  const uint4* sidx;
+  const uint16_t* vbody;
   fire_gbuffer_rec* g;          // per-sample records
   int write_vis;                // store vis bits into g
   float* out;                   // [H*W*4]
@@ -248,6 +259,16 @@ int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten,
 int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, const float* dL,
                    float* dparams, float* dinten, cudaStream_t st);
 int stack_for_height(int height, int requested);
+// Smooth-shading inputs of the scene's current frame buffer (vnrm stays
+// nullptr for a scene without vertex normals: flat shading).
+inline void set_smooth_args(RenderArgs* a, const fire_scene_s* s) {
+  a->vnrm = s->vnrm;
+  a->bxf = s->xf_buf[s->cur];
+  a->sidx = s->sidx;
+  a->vbody = s->vbody;
+}
+// display.cu: sRGB-encoded albedo of the [nmat*5] material table -> linear
+int srgb_decode_materials(float* mats, int nmat, cudaStream_t st);
 // stack entries the 4-wide traversal of this scene can need: 3 per level + sentinel
 inline int stack_need(const fire_scene_s* s) { return 3 * s->height4 + 1; }
 int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, float* dparams, float* dinten,

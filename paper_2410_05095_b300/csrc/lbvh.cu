@@ -358,8 +358,10 @@ __global__ void k_refit_build(const float4* __restrict__ rest, const uint16_t* _
                               const float* __restrict__ xf, const uint4* __restrict__ sidx,
                               const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
                               Node* nodes, const int32_t* __restrict__ leaf_slot,
-                              const int32_t* __restrict__ node_slot, uint32_t* counters) {
+                              const int32_t* __restrict__ node_slot, uint32_t* counters,
+                              float* __restrict__ xfb, int nxf) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nxf) xfb[i] = xf[i];  // the frame buffer's copy of the body matrices
   const int lane = threadIdx.x & 31;
   const bool valid = i < nt;
   float3 lo = f3(0, 0, 0), hi = f3(0, 0, 0);
@@ -542,8 +544,10 @@ __global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict_
                                                        const float* __restrict__ xf, const uint4* __restrict__ sidx,
                                                        const uint32_t* __restrict__ smat, int64_t nt,
                                                        float4* __restrict__ tris, Node4* __restrict__ nodes4,
-                                                       const int32_t* __restrict__ leaf_slot4, int64_t n4) {
+                                                       const int32_t* __restrict__ leaf_slot4, int64_t n4,
+                                                       float* __restrict__ xfb, int nxf) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nxf) xfb[i] = xf[i];  // the frame buffer's copy of the body matrices
   if (i >= nt) return;
   uint4 id = sidx[i];
   float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
@@ -664,8 +668,10 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   k_gather_sorted<<<grid_for(T, 256), 256, 0, st>>>(s->order, s->idx, s->tmat, T, s->sidx, s->smat, s->rank);
   if (T > 1)
     if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;
-  k_refit_build<<<grid_for(T, 256), 256, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
-                                                   s->nodes, s->leaf_slot, s->node_slot, s->counters);
+  const int nxf = 12 * s->nbody;
+  k_refit_build<<<grid_for(std::max<int64_t>(T, nxf), 256), 256, 0, st>>>(
+      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes, s->leaf_slot, s->node_slot, s->counters,
+      s->xf_buf[s->cur], nxf);
   prof_end(s, kStageBuild, st, 2 + 3 * kSortPasses + (T > 1 ? 1 : 0) + 2);
   if (int e = cuda_check(cudaGetLastError(), "build kernels")) return e;
   Node n0;
@@ -720,8 +726,9 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   prof_begin(s, kStageRefit, st);
   // 128-thread blocks: small enough to be scheduled beside the render
   // kernels' blocks when a refit overlaps the previous frame's render
-  k_refit4_leaves<<<grid_for(T, 128), 128, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris,
-                                                    s->nodes4, s->leaf_slot4, s->n4);
+  const int nxf = 12 * s->nbody;
+  k_refit4_leaves<<<grid_for(std::max<int64_t>(T, nxf), 128), 128, 0, st>>>(
+      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes4, s->leaf_slot4, s->n4, s->xf_buf[s->cur], nxf);
   // depths, deepest first: runs of small depths go to one block, large ones get their own launch
   const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
   const int64_t* lvl_dev = reinterpret_cast<const int64_t*>(s->lvl_aux);

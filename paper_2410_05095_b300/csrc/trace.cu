@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
       if (prim >= 0) {
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
         hit_frame(B, C, o, d, t, eps, n, po);
+        if (a.vnrm)
+          n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, pos, __ldg(a.tris + 3 * (int64_t)pos), B,
+                             C, o, d, n);
       }
     }
     uint32_t cast = 0;
@@ -170,6 +173,9 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
         float3 n, po;
         hit_frame(B, C, o, d, t, eps, n, po);
+        if (a.vnrm)
+          n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, pos, __ldg(a.tris + 3 * (int64_t)pos), B,
+                             C, o, d, n);
         float3 v = neg3(d);
         const float* mp = a.mats.p + 5 * (int64_t)__float_as_uint(B.w);
         float ar = __ldg(mp), ag = __ldg(mp + 1), ab = __ldg(mp + 2), rough = __ldg(mp + 3), metal = __ldg(mp + 4);
@@ -249,6 +255,9 @@ __global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, 
         float4 B = __ldg(a.tris + 3 * (int64_t)rr.w + 1), C = __ldg(a.tris + 3 * (int64_t)rr.w + 2);
         float3 n, po;
         hit_frame(B, C, o, d, __int_as_float(rr.y), eps, n, po);
+        if (a.vnrm)
+          n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, rr.w, __ldg(a.tris + 3 * (int64_t)rr.w), B,
+                             C, o, d, n);
         float3 v = neg3(d);
         mat = (int)__float_as_uint(B.w);
         const float* mp = a.mats.p + 5 * (int64_t)mat;

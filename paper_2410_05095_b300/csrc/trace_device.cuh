@@ -302,6 +302,49 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
   return traverse<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
 }
 
+// ---------------------------------------------------------------------------
+// Smooth shading normal (§IV-A-1: the main pass shades with the meshes'
+// per-vertex normals).  For the hit of the ray (o, d) on the triangle at
+// sorted position pos (record A = v0, B = e1, C = e2):
+//   (u, v)  barycentrics from the same FP32 triangle-test steps that found
+//           the hit, so they are the traversal's own values
+//   n_r     = fma(v, n2, fma(u, n1, w0 n0)) per component, w0 = (1 - u) - v,
+//           from the rest normals of the triangle's three vertices
+//   n_w     = R n_r, R = rotation of the vertex's body in the frame's matrices
+//   n_s     = normalize(n_w), negated if n_s . n_g < 0 (n_g: the geometric
+//           normal already facing the ray); a zero n_w keeps n_g
+// The shadow-ray origin stays lifted along n_g (hit_frame).
+// ---------------------------------------------------------------------------
+struct SmoothCtx {
+  const float4* vnrm;  // [nv] rest normals, or nullptr (flat)
+  const float* bxf;    // [nbody*12] body matrices of the frame
+  const uint4* sidx;   // [nt] sorted index records (i0, i1, i2, orig)
+  const uint16_t* vbody;
+};
+
+__device__ __forceinline__ float3 shading_normal(const SmoothCtx& c, int pos, float4 A, float4 B, float4 C,
+                                                 float3 o, float3 d, float3 ng) {
+  const float3 v0 = xyz(A), e1 = xyz(B), e2 = xyz(C);
+  const float3 p = cross3(d, e2);
+  const float inv = __frcp_rn(dot3(e1, p));
+  const float3 s = sub3(o, v0);
+  const float u = dot3(s, p) * inv;
+  const float3 q = cross3(s, e1);
+  const float v = dot3(d, q) * inv;
+  const uint4 id = __ldg(c.sidx + pos);
+  const float4 n0 = __ldg(c.vnrm + id.x), n1 = __ldg(c.vnrm + id.y), n2 = __ldg(c.vnrm + id.z);
+  const float w0 = (1.0f - u) - v;
+  const float3 nr = f3(fmaf(v, n2.x, fmaf(u, n1.x, w0 * n0.x)), fmaf(v, n2.y, fmaf(u, n1.y, w0 * n0.y)),
+                       fmaf(v, n2.z, fmaf(u, n1.z, w0 * n0.z)));
+  const float* m = c.bxf + 12 * (uint32_t)__ldg(c.vbody + id.x);
+  const float3 nw = f3(fmaf(__ldg(m + 0), nr.x, fmaf(__ldg(m + 1), nr.y, __ldg(m + 2) * nr.z)),
+                       fmaf(__ldg(m + 4), nr.x, fmaf(__ldg(m + 5), nr.y, __ldg(m + 6) * nr.z)),
+                       fmaf(__ldg(m + 8), nr.x, fmaf(__ldg(m + 9), nr.y, __ldg(m + 10) * nr.z)));
+  if (!(dot3(nw, nw) > 0.0f)) return ng;
+  const float3 ns = normalize3(nw);
+  return dot3(ns, ng) < 0.0f ? neg3(ns) : ns;
+}
+
 // Scene box = union of the 4-wide root's child boxes (the same exact min/max
 // as the binary root's box).
 __device__ __forceinline__ void root_box(const Node4* nodes4, float3& lo, float3& hi) {

@@ -27,7 +27,8 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_shade_backward", "fire_debug_dump", "fire_sync_status",
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
-           "fire_display", "fire_last_error", "fire_version"]
+           "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_last_error",
+           "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -90,6 +91,8 @@ def lib():
             "fire_shade_backward_noalloc": [P, P, P, P, i32, P, P, P, P, P, P],
             "fire_render_info": [P, P],
             "fire_display": [P, i32, i32, C.c_float, i32, P, P, P],
+            "fire_scene_set_materials_ex": [P, P, i32, i32],
+            "fire_scene_set_normals": [P, P, i32, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -192,9 +195,25 @@ class Scene:
         except Exception:
             pass
 
-    def set_materials(self, mats: np.ndarray):
+    def set_materials(self, mats: np.ndarray, srgb: bool = False):
+        """Replace the materials; srgb=True: albedo is sRGB-encoded (decoded on the device)."""
         self._mats = make_materials(mats)
-        _check(lib().fire_scene_set_materials(self.h, C.cast(self._mats, C.c_void_p), len(mats)))
+        _check(lib().fire_scene_set_materials_ex(self.h, C.cast(self._mats, C.c_void_p), len(mats),
+                                                 1 if srgb else 0))
+
+    def set_normals(self, normals, stream=None):
+        """Rest-pose vertex normals [nv, 4] (numpy host array or CUDA tensor) for
+        smooth shading; None returns to flat shading (see include/fire.h)."""
+        if normals is None:
+            _check(lib().fire_scene_set_normals(self.h, None, 0, _stream(stream)))
+            return
+        dev = hasattr(normals, "is_cuda") and normals.is_cuda
+        if dev:
+            assert normals.dtype.itemsize == 4 and normals.numel() == 4 * self.nv and normals.is_contiguous()
+            x = normals
+        else:
+            x = np.ascontiguousarray(np.asarray(normals, np.float32).reshape(self.nv, 4))
+        _check(lib().fire_scene_set_normals(self.h, _ptr(x), int(dev), _stream(stream)))
 
     def info(self) -> dict:
         out = (C.c_int64 * 8)()
