@@ -318,7 +318,11 @@ def main():
     G = fb.Scene.from_numpy(w.scene)
     xf_dev = torch.from_numpy(frames).cuda()
     xf_pinned = torch.from_numpy(frames).pin_memory()
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
     G.build(xf_build)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t_build) * 1e3  # wall clock: the collapse synchronises per depth
     out = torch.zeros((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     G.profile(True)
@@ -496,7 +500,7 @@ def main():
             "config": workload_config(w, K), "gpu_launches": int(launches),
             "grays_per_s": grays, "grays_per_s_frame": grays_frame,
             "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
-            "stages_ms": {**avg, "build_once": build_stats["build"][0]},
+            "stages_ms": {**avg, "build_once": build_ms},
             "serial_ms_per_frame": t_serial / K,
             "frame_loop": "pipelined: refit of frame i (own stream, second frame buffer) overlaps the render of "
                           "frame i-1; stages_ms from the serial loop",

@@ -190,3 +190,29 @@ def test_normals_errors(fb):
     assert L.fire_scene_set_normals(None, None, 0, None) != 0
     G.set_normals(None)                             # clearing twice is fine
     G.set_normals(None)
+
+
+def test_smooth_device_normals_zero_fallback_and_empty(fb):
+    """Normals given as a CUDA tensor render like the same host array; a
+    triangle whose three normals are zero falls back to its geometric
+    normal on both sides; an empty scene takes normals and renders black."""
+    torch = torch_cuda()
+    w = sg.workload_tiny41k()
+    cam = sg.Camera((0.0, 4.0, 12.0), (0, 0, 0), (0, 1, 0), 60.0, 64, 48, 4)
+    nrm = sg.vertex_normals(w.scene)
+    nrm[w.scene.idx[::3].ravel()] = 0.0           # every third triangle: all-zero normals
+    G, S = build_pair(w.scene)
+    S.set_normals(nrm)
+    G.set_normals(torch.from_numpy(nrm).cuda())
+    img_dev, _, _ = _check(G, S, cam, w.lights)
+    G.set_normals(nrm)
+    img_host, _, _ = _render(G, cam, w.lights)
+    assert np.array_equal(img_dev, img_host)
+    empty = sg.Scene(verts=np.zeros((0, 4), np.float32), idx=np.zeros((0, 3), np.uint32),
+                     tri_mat=np.zeros(0, np.uint32), vert_body=np.zeros(0, np.uint16),
+                     mats=sg.random_materials(sg.Rng(5), 1), nbody=1)
+    E = fb.Scene.from_numpy(empty)
+    E.build(empty.identity_xforms())
+    E.set_normals(np.zeros((0, 4), np.float32))
+    img = E.render(cam, w.lights)
+    assert E.sync_status() == 0 and float(img.abs().sum()) == 0.0
