@@ -198,11 +198,11 @@ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
 }
 
 // Stack traversal of the 4-wide tree (collapsed from the Karras binary
-// tree), nearest child first (both modes).  One node fetch (7 x 16 B) tests all four child
+// tree), nearest child first (any hit: farthest first).  One node fetch (7 x 16 B) tests all four child
 // boxes; leaf children (one triangle each) are tested at once, so the
 // nearest-hit bound tightens early; hit internal children are ordered by
-// entry distance with a 5-comparator network and all but the nearest pushed,
-// farthest first.  (Postponing leaves until the whole warp holds one -- the
+// entry distance with a 5-comparator network and all but the first pushed,
+// last first.  (Postponing leaves until the whole warp holds one -- the
 // while-while form of Aila and Laine -- measured 2x slower with one triangle
 // per leaf: the delayed bound lets rays wander into far subtrees.)
 //   ANY:  any hit in (0, tmax) other than `skip`; returns true on a hit.
@@ -265,9 +265,18 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
       cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
       continue;
     }
-    // nearest child first in both modes: for shadow rays it finds the
-    // occluders next to the surface point early (measured 9% faster than
-    // the unsorted order on the 7.3M-triangle frame)
+    // nearest child first for the nearest hit; farthest first for any hit:
+    // on the 7.3M-triangle frame 57-61 % of the shadow rays are occluded,
+    // mostly by bodies between the surface and the light rather than by the
+    // surface's own neighbourhood, and the far-first order reaches them
+    // sooner (measured 1.41 -> 1.37 ms; nearest first was 9 % faster than
+    // the unsorted order)
+    if (ANY) {
+      k0 = -k0;
+      k1 = -k1;
+      k2 = -k2;
+      k3 = -k3;
+    }
     k0 = h0 ? k0 : inf_f();
     k1 = h1 ? k1 : inf_f();
     k2 = h2 ? k2 : inf_f();
