@@ -453,8 +453,26 @@ def main():
     seq = np.array([a.elapsed_time(b) for a, b in evs])
     G.profile_read()
     sequence = {"frames": 99, "median_ms": float(np.median(seq)), "p95_ms": float(np.percentile(seq, 95)),
-                "first_ms": float(seq[0]), "last_ms": float(seq[-1]),
+                "mean_ms": float(seq.mean()), "first_ms": float(seq[0]), "last_ms": float(seq[-1]),
                 "note": "refit + render per frame after a build at frame 0 (tree quality decays with motion)"}
+    # the same sequence with a full rebuild (fire_bvh_build) in place of the
+    # refit every 25th frame: the rebuild frames cost more, the others stay
+    # near the frame-1 quality
+    G.build(xf_build)
+    for i in range(99):
+        evs[i][0].record(stream)
+        if (i + 1) % 25 == 0:
+            G.build(xf_dev[i])
+        else:
+            G.refit(xf_dev[i])
+        G.render(cam, lights, out=out)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    seq2 = np.array([a.elapsed_time(b) for a, b in evs])
+    G.profile_read()
+    sequence["rebuild_every_25"] = {"median_ms": float(np.median(seq2)), "p95_ms": float(np.percentile(seq2, 95)),
+                                    "mean_ms": float(seq2.mean()), "last_ms": float(seq2[-1]),
+                                    "rebuild_frames_ms": [float(seq2[i]) for i in range(24, 99, 25)]}
 
     # --- rays traced per frame (shadow rays counted from the G-buffer) ------------
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")

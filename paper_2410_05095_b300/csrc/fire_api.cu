@@ -260,7 +260,7 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
       {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
-      {(void**)&s->lvl_aux, 8 * (size_t)kMaxDepth4 + 16},
+      {(void**)&s->lvl_aux, 12 * (size_t)kMaxDepth4 + 16},
       {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
       {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},

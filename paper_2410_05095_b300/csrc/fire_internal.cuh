@@ -125,7 +125,8 @@ struct fire_scene_s {
   int32_t* leaf_slot = nullptr; // [nt]   2*parent + side
   int32_t* node_slot = nullptr; // [nt-1] 2*parent + side (root -1)
   uint32_t* counters = nullptr; // [nt-1] arrival counters of the build's refit
-  uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]) + 2 collapse counters
+  uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]), collapse queue
+                                //   lengths (u32 [kMaxDepth4]) and the node counter (u32)
   std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
   int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf
   fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree (current buffer)

@@ -443,11 +443,10 @@ __device__ __forceinline__ float box_area(float4 a, float4 b) {  // sector: lo x
   return dx * dy + dy * dz + dz * dx;
 }
 
-__global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs, uint32_t nin,
-                           int32_t* __restrict__ out_pairs, uint32_t* __restrict__ counts, Node4* __restrict__ nodes4,
-                           int64_t cap4, int32_t* __restrict__ leaf_slot4, int64_t nt) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nin) return;
+__device__ __forceinline__ void collapse_one(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs,
+                                             uint32_t i, int32_t* __restrict__ out_pairs, uint32_t* nout,
+                                             uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4,
+                                             int32_t* __restrict__ leaf_slot4, int64_t nt) {
   const int b = in_pairs[2 * i], q = in_pairs[2 * i + 1];
   int link[4] = {kEmptyLink, kEmptyLink, kEmptyLink, kEmptyLink}, src[4] = {-1, -1, -1, -1};
   float area[4] = {0, 0, 0, 0};
@@ -481,12 +480,12 @@ __global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __rest
     if (k < m && link[k] < 0 && link[k] != kEmptyLink && (int64_t)~link[k] < nt)
       leaf_slot4[~link[k]] = 4 * q + k;  // where the per-frame refit puts this leaf's box
     if (k < m && link[k] >= 0) {
-      uint32_t q2 = atomicAdd(counts + 1, 1u);   // 4-wide node index
-      uint32_t p = atomicAdd(counts + 0, 1u);    // next level's queue slot
+      const uint32_t q2 = atomicAdd(alloc, 1u);  // 4-wide node index
       if (q2 >= cap4) {                          // never: a 4-wide node consumes >= 1 binary node
         out[k] = kEmptyLink;
         continue;
       }
+      const uint32_t p = atomicAdd(nout, 1u);    // next level's queue slot
       out[k] = (int)q2;
       out_pairs[2 * p] = link[k];
       out_pairs[2 * p + 1] = (int)q2;
@@ -494,6 +493,20 @@ __global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __rest
   }
   nodes4[q].link = make_int4(out[0], out[1], out[2], out[3]);
   nodes4[q].src = make_int4(src[0], src[1], src[2], src[3]);
+}
+
+// One depth of the collapse: the queue of this depth holds *nin_p (binary
+// node, 4-wide node) pairs (written by the previous depth's launch); each
+// pair is collapsed by collapse_one, which allocates the internal members
+// at the next depth (alloc) and queues them (*nout).  Grid-stride, so the
+// host launches one fixed grid per depth without reading the length back.
+__global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs,
+                           const uint32_t* __restrict__ nin_p, int32_t* __restrict__ out_pairs, uint32_t* nout,
+                           uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4,
+                           int32_t* __restrict__ leaf_slot4, int64_t nt) {
+  const uint32_t nin = *nin_p;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nin; i += gridDim.x * blockDim.x)
+    collapse_one(nodes, in_pairs, i, out_pairs, nout, alloc, nodes4, cap4, leaf_slot4, nt);
 }
 
 // Per frame: copy each member's box from its binary slot (whole 32-B sector
@@ -682,31 +695,38 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   memcpy(&h1, &n0.d.w, 4);
   s->height = T > 1 ? 1 + std::max(h0, h1) : 1;
   // 4-wide traversal tree: collapse depth by depth from the binary root; the
-  // nodes of depth L get the contiguous indices [lvl4[L], lvl4[L+1])
+  // nodes of depth L get the contiguous indices [lvl4[L], lvl4[L+1]).  One
+  // launch per depth with the queue lengths kept on the device (qlen[d] =
+  // nodes at depth d); a 4-wide depth consumes at least one binary level,
+  // so `height` launches suffice, and the lengths are read back once.
   {
     const int64_t cap4 = std::max<int64_t>(T - 1, 1);
     int32_t* qa = s->q4;
     int32_t* qb = s->q4 + 2 * cap4;
-    uint32_t* counts = reinterpret_cast<uint32_t*>(s->lvl_aux + 8 * kMaxDepth4);
+    uint32_t* qlen = reinterpret_cast<uint32_t*>(s->lvl_aux + 8 * kMaxDepth4);  // [kMaxDepth4]
+    uint32_t* alloc = qlen + kMaxDepth4;                                         // 4-wide nodes allocated
     const int32_t root[2] = {0, 0};
-    const uint32_t init[2] = {0u, 1u};  // next-depth queue length, 4-wide nodes allocated (root)
+    const int L = std::max(1, std::min(s->height, kMaxDepth4 - 1));
+    std::vector<uint32_t> h(kMaxDepth4 + 1, 0u);
+    h[0] = 1u;           // depth 0: the root
+    h[kMaxDepth4] = 1u;  // the root is allocated
     if (int e = cuda_check(cudaMemcpyAsync(qa, root, sizeof(root), cudaMemcpyHostToDevice, st), "copy")) return e;
-    if (int e = cuda_check(cudaMemcpyAsync(counts, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
+    if (int e = cuda_check(cudaMemcpyAsync(qlen, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, st), "copy"))
+      return e;
     if (int e = cuda_check(cudaMemsetAsync(s->leaf_slot4, 0xff, 4 * T, st), "memset")) return e;
-    uint32_t nin = 1, h[2] = {0u, 1u};
-    s->lvl4.assign(1, 0);
-    s->lvl4.push_back(1);
-    while (nin > 0 && (int)s->lvl4.size() < kMaxDepth4 - 1) {
-      if (int e = cuda_check(cudaMemsetAsync(counts, 0, 4, st), "memset")) return e;
-      k_collapse<<<grid_for(nin, 256), 256, 0, st>>>(s->nodes, qa, nin, qb, counts, s->nodes4, cap4,
-                                                     s->leaf_slot4, T);
-      if (int e = cuda_check(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, st), "copy")) return e;
-      if (int e = cuda_check(cudaStreamSynchronize(st), "collapse")) return e;
-      nin = h[0];
-      if (nin > 0) s->lvl4.push_back((int64_t)std::min<uint64_t>(h[1], cap4));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(cap4, 256), (int64_t)sm_count() * 8));
+    for (int d = 0; d < L; ++d) {
+      k_collapse<<<grid, 256, 0, st>>>(s->nodes, qa, qlen + d, qb, qlen + d + 1, alloc, s->nodes4, cap4,
+                                       s->leaf_slot4, T);
       std::swap(qa, qb);
     }
-    if (nin > 0) return set_error(FIRE_ERR_CUDA, "4-wide collapse deeper than supported");
+    if (int e = cuda_check(cudaGetLastError(), "collapse")) return e;
+    if (int e = cuda_check(cudaMemcpyAsync(h.data(), qlen, 4 * h.size(), cudaMemcpyDeviceToHost, st), "copy"))
+      return e;
+    if (int e = cuda_check(cudaStreamSynchronize(st), "collapse")) return e;
+    if (h[L] != 0u) return set_error(FIRE_ERR_CUDA, "4-wide collapse deeper than supported");
+    s->lvl4.assign(1, 0);
+    for (int d = 0; d < L && h[d] > 0; ++d) s->lvl4.push_back(std::min<int64_t>(s->lvl4.back() + h[d], cap4));
     s->n4 = s->lvl4.back();
     s->height4 = (int)s->lvl4.size() - 1;
     if (int e = cuda_check(cudaMemcpyAsync(s->lvl_aux, s->lvl4.data(), 8 * s->lvl4.size(), cudaMemcpyHostToDevice, st),
