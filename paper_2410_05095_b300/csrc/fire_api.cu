@@ -571,11 +571,9 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
   size_t nsamp = (size_t)cam->width * cam->height * cam->spp;
   if (gbuf) {
     a.g = gbuf;
-    a.write_vis = 1;
   } else {
     if (int e = ensure_scratch(s, nsamp)) return e;
     a.g = s->gscratch;
-    a.write_vis = 0;
   }
   size_t njobs = nsamp * (size_t)std::max(1, nlights);
   if (s->jobs_n < njobs) {

@@ -228,7 +228,6 @@ struct RenderArgs {
   const uint4* sidx;
   const uint16_t* vbody;
   fire_gbuffer_rec* g;          // per-sample records
-  int write_vis;                // store vis bits into g
   float* out;                   // [H*W*4]
 };
 // Raster primary pass (raster.cu).  Words of fire_scene_s::ctrl it uses:

@@ -144,12 +144,11 @@ __device__ __forceinline__ void resolve_write(const RenderArgs& a, int lane, boo
   }
 }
 
-// TRACE: cast the shadow rays (fire_render); otherwise read visibility from
-// the G-buffer (fire_shade).  inten: device intensities or nullptr.
-template <int STACK, bool TRACE>
+// Shading + resolve of the samples' records, visibility read from the
+// records (fire_render's last pass and fire_shade).  inten: device
+// intensities or nullptr (the lights' own).
 __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int ntasks, const float* inten) {
   const int lane = threadIdx.x & 31;
-  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
   const float eps = scene_eps(a.nodes4, a.nt);
   while (true) {
     int task = 0;
@@ -164,7 +163,7 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
       int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
       int4 rr = reinterpret_cast<const int4*>(a.g)[sid];
       int prim = rr.x, pos = rr.w;
-      uint32_t vis = TRACE ? 0u : (uint32_t)rr.z;
+      const uint32_t vis = (uint32_t)rr.z;
       if (prim >= 0) {
         hit = 1;
         float t = __int_as_float(rr.y);
@@ -185,26 +184,18 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
           float E, tmax;
           light_vec(a.lights, j, I, po, l, E, tmax);
           float ndl = dot3(n, l);
-          if (!(ndl > 0.0f)) continue;
-          if (TRACE) {
-            vis |= 1u << (8 + j);
-            if (trace_any<STACK>(c, po, l, tmax, prim)) continue;
-            vis |= 1u << j;
-          } else if (!((vis >> j) & 1u)) {
-            continue;
-          }
+          if (!(ndl > 0.0f) || !((vis >> j) & 1u)) continue;
           float3 f = brdf(n, v, l, ar, ag, ab, rough, metal);
           float En = E * ndl;
           rad = f3(rad.x + f.x * En, rad.y + f.y * En, rad.z + f.z * En);
         }
       }
-      if (TRACE && a.write_vis) reinterpret_cast<int4*>(a.g)[sid].z = (int)vis;
     }
     resolve_write(a, lane, valid, x, y, rad, hit);
   }
 }
 
-// Backward of k_shade<.., false> for L(image): per sample, the upstream
+// Backward of k_shade for L(image): per sample, the upstream
 // gradient of the pixel divided by spp, chained through
 //   rad_c = sum_j I_j g_j (n.l_j) f_c(albedo, r, m)
 // with g_j = 1/d^2 (point) or 1.  Derivatives of f_c (a = r^2, a2 = a^2,
@@ -365,7 +356,7 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
   std::call_once(once, [] {
     occ_p = occupancy_blocks(k_primary<STACK, 0>, 128, 0);
     occ_s = occupancy_blocks(k_shadow<STACK>, 128, 0);
-    occ_r = occupancy_blocks(k_shade<32, false>, 128, 0);
+    occ_r = occupancy_blocks(k_shade, 128, 0);
   });
   int sms = sm_count();
   int bp = o.blocks_per_sm > 0 ? o.blocks_per_sm : occ_p;
@@ -397,7 +388,7 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
     prof_end(s, kStageShadow, st);
   }
   prof_begin(s, kStageResolve, st);
-  k_shade<32, false><<<gr, threads, 0, st>>>(a, g, ntasks, nullptr);
+  k_shade<<<gr, threads, 0, st>>>(a, g, ntasks, nullptr);
   prof_end(s, kStageResolve, st);
   return cuda_check(cudaGetLastError(), "render kernels");
 }
@@ -440,7 +431,7 @@ int shade_from_gbuffer(fire_scene_s* s, const RenderArgs& a, const float* inten,
   if (int e = cuda_check(cudaMemsetAsync(a.ctrl, 0, 4 * 4, st), "memset")) return e;
   int grid = std::max(1, std::min(sm_count() * 8, (ntasks + 3) / 4));
   prof_begin(s, kStageShadeGbuf, st);
-  k_shade<32, false><<<grid, 128, 0, st>>>(a, g, ntasks, inten);
+  k_shade<<<grid, 128, 0, st>>>(a, g, ntasks, inten);
   prof_end(s, kStageShadeGbuf, st);
   return cuda_check(cudaGetLastError(), "k_shade_gbuf");
 }
