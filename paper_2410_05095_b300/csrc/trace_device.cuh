@@ -464,8 +464,10 @@ __device__ __forceinline__ void hit_frame(float4 B, float4 C, float3 o, float3 d
   po = f3(fmaf(eps, n.x, p.x), fmaf(eps, n.y, p.y), fmaf(eps, n.z, p.z));
 }
 
-// Work mapping: one warp = one task of 32 samples; spp 4 -> 8 pixels of a row
-// x 4 samples (lanes 4q..4q+3 hold pixel q), spp 1 -> an 8 x 4 pixel block.
+// Work mapping: one warp = one task of 32 samples; spp 4 -> a 4 x 2 pixel
+// block x 4 samples (lanes 4q..4q+3 hold pixel q; the compact block keeps a
+// warp's rays closer than 8 pixels of a row: primary 1.09 -> 1.04 ms, shadow
+// 1.37 -> 1.34 ms on the 7.3M-triangle frame), spp 1 -> an 8 x 4 pixel block.
 struct TaskGrid {
   int tiles_x, tiles_y, row_begin, rows_per_task, W, row_end, spp;
 };
@@ -476,8 +478,8 @@ __host__ __device__ __forceinline__ TaskGrid make_grid(int W, int row_begin, int
   g.spp = spp;
   g.row_begin = row_begin;
   g.row_end = row_end;
-  g.rows_per_task = spp == 4 ? 1 : 4;
-  g.tiles_x = (W + 7) / 8;
+  g.rows_per_task = spp == 4 ? 2 : 4;
+  g.tiles_x = spp == 4 ? (W + 3) / 4 : (W + 7) / 8;
   g.tiles_y = (row_end - row_begin + g.rows_per_task - 1) / g.rows_per_task;
   return g;
 }
@@ -485,8 +487,8 @@ __host__ __device__ __forceinline__ TaskGrid make_grid(int W, int row_begin, int
 __device__ __forceinline__ bool task_sample(const TaskGrid& g, int task, int lane, int& x, int& y, int& k) {
   int tx = task % g.tiles_x, ty = task / g.tiles_x;
   if (g.spp == 4) {
-    x = tx * 8 + (lane >> 2);
-    y = g.row_begin + ty;
+    x = tx * 4 + ((lane >> 2) & 3);
+    y = g.row_begin + ty * 2 + (lane >> 4);
     k = lane & 3;
   } else {
     x = tx * 8 + (lane & 7);
