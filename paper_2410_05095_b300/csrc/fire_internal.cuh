@@ -236,6 +236,7 @@ constexpr int kCtrlRasterCursor = 17;  // next piece to take
 constexpr int kCtrlRasterFlag = 18;    // != 0: traversal fallback for this frame
 constexpr int kCtrlRasterGraze = 19;   // deferred triangles
 constexpr int kCtrlRasterParams = 20;  // [20..22] zn, rn, slack (float bits)
+constexpr int kCtrlShadowLen = 24;     // [24..31] shadow rays queued per light
 struct RasterArgs {
   const float4* tris;
   int64_t nt;
