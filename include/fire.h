@@ -83,7 +83,12 @@ typedef struct {
   int32_t row_end;
   int32_t block_threads; /* threads per block of the batch kernels, a multiple of
                             32 up to 128 (0 = default); fire_render uses 128 */
-  int32_t blocks_per_sm; /* persistent grid = SMs x blocks_per_sm (0 = default) */
+  int32_t blocks_per_sm; /* persistent grid = SMs x blocks_per_sm (0 = default).
+                            fire_render: applies to its primary pass only -- the
+                            pass that a refit of the next frame on another stream
+                            overlaps, so fewer blocks leave it room; the shadow
+                            and resolve passes always run at full occupancy.
+                            fire_render_batch: all of its kernels. */
   int32_t stack_depth;   /* traversal stack entries (0 = sufficient for the tree) */
   int32_t flags;         /* FIRE_RENDER_* bits, 0 by default */
 } fire_render_opts;

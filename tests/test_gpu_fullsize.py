@@ -2,8 +2,8 @@
 64 moving bodies, 1920x1080, 4 spp, 2 lights): the whole LBVH bit for bit,
 sampled outputs of a refit frame that the oracle computes one by one, and
 the launch configuration the benchmark times (refit of frame i on a
-high-priority second stream overlapping the render of frame i-1, render
-kernels at 6 blocks per SM) giving the serial frames bit for bit."""
+high-priority second stream overlapping the render of frame i-1, primary
+pass at 6 blocks per SM) giving the serial frames bit for bit."""
 import numpy as np
 import pytest
 
