@@ -455,7 +455,7 @@ int fire_render_info(fire_scene s, int64_t* out4) {
   out4[0] = s->last_raster ? 1 : 0;
   out4[1] = s->last_raster ? w[kCtrlRasterFlag] : 0;
   out4[2] = s->last_raster ? w[kCtrlRasterPieces] : 0;
-  out4[3] = w[4];
+  for (int j = 0; j < 8; ++j) out4[3] += w[kCtrlShadowLen + j];  // per-light queue segments
   return FIRE_OK;
 }
 

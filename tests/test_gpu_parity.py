@@ -96,6 +96,17 @@ def test_render_tiny_full_image(fb):
     assert (g["prim"] >= 0).mean() > 0.5
 
 
+def test_render_info_counts_the_shadow_rays(fb):
+    """fire_render_info's shadow-ray count equals the cast bits of the
+    G-buffer (rays queued over all lights' segments)."""
+    w = sg.workload_mid1m(160, 90, 4)
+    G, _ = build_pair(w.scene)
+    img, g = _render(G, w.camera, w.lights)
+    cast = sum(int(((g["vis"] >> (8 + j)) & 1).sum()) for j in range(len(w.lights)))
+    info = G.render_info()
+    assert cast > 0 and info["shadow_rays"] == cast and not info["raster"]
+
+
 def test_render_mid_4spp_three_lights(fb):
     w = sg.workload_mid1m(320, 180, 4)
     G, S = build_pair(w.scene)
