@@ -1,0 +1,69 @@
+"""Host-side logic of the benchmark (no GPU): the clock-sample summary that
+decides whether a run is kept, the algorithmic-byte model behind the
+roofline, and the committed ncu counters it reads."""
+import json
+import os
+
+import bench
+
+
+def _clocks_from(lines):
+    c = bench.Clocks(0)
+    fd, c.path = bench.tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    return c.summary()
+
+
+def test_clock_summary_median_under_load_and_reasons():
+    # index, sm, max sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    rows = ["0, 345, 2032, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # idle: dropped
+            "0, 2032, 2032, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2032, 1100.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2032, 2032, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    s = _clocks_from(rows)
+    assert s["sm_mhz"] == 2032.0 and s["sm_max_mhz"] == 2032.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+
+
+def test_clock_summary_reports_throttling():
+    rows = ["0, 1500, 2032, 700.0, 0x40, Not Active, Active, Not Active, Not Active"] * 3
+    s = _clocks_from(rows)
+    assert s["reasons"] == ["hw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
+
+
+def test_clock_summary_without_samples():
+    assert _clocks_from([""])["reasons"] == ["no samples"]
+
+
+def test_algorithmic_bytes_model():
+    nt, nv, n4, samples, pixels, rays = 1000, 600, 400, 80, 20, 30
+    b = bench.algorithmic_bytes(nt, nv, n4, samples, pixels, rays)
+    tree = 128 * n4 + 48 * nt
+    assert b["shadow"] == tree + 40 * rays
+    assert b["primary"] == tree + 16 * samples + 32 * rays
+    assert b["resolve"] == 48 * samples + 16 * pixels
+    assert b["refit"] == 18 * nv + 96 * nt + 208 * n4
+    # the headline frame: 7,299,072 triangles, 3,652,849 vertices
+    full = bench.algorithmic_bytes(7_299_072, 3_652_849, 3_476_669, 8_294_400, 2_073_600, 3_842_521)
+    assert 0.9e9 < full["shadow"] < 1.0e9
+
+
+def test_committed_counters_are_per_launch_integers():
+    for kernel in ("shadow", "primary", "resolve"):
+        v = bench.committed_counter("dram_bytes", kernel)
+        w = bench.committed_counter("warp_inst", kernel)
+        assert isinstance(v, int) and 1e7 < v < 2e9
+        assert isinstance(w, int) and 1e7 < w < 2e9
+    assert bench.committed_counter("dram_bytes", "refit") is None
+    assert bench.committed_counter("dram_bytes", "no such kernel") is None
+
+
+def test_workload_config_names_the_headline_frame():
+    import scenegen as sg
+    w = sg.workload_frame7m(nspheres=4, cells=4)   # small stand-in: the fields, not the sizes
+    cfg = bench.workload_config(w, 20)
+    assert cfg["workload"].startswith("frame7m") and cfg["frames"] == 20
+    assert cfg["parallelism"] == "replicas" and "L2" in cfg["l2"]
+    json.dumps(cfg)
