@@ -12,7 +12,9 @@ splitmix64 (both published generators, written out here), with
 u = (x >> 40) * 2**-24, so results never depend on a library's
 distributions.  Seed = 2410 * 100 + workload index.
 
-Workloads (triangle counts follow the reading documented in the design doc, A1):
+Workloads (every sphere is the 5,120-triangle icosphere, 20 * 4^4, and the
+terrain a 256x256-cell heightfield; with the stated sphere counts the
+headline frame then has the paper's ">7M" triangles):
   tiny41k    8 icospheres (5,120 tris) + 2-tri ground quad = 40,962 tris, 256x256, 1 spp, 1 light
   mid1m      200 icospheres + 256x256-cell terrain = 1,155,072 tris, 1280x720, 4 spp, 3 lights
   frame7m    1,400 icospheres + 256x256 terrain = 7,299,072 tris, 1920x1080, 4 spp, 2 lights,
