@@ -1,7 +1,8 @@
 """Shared helpers of the GPU parity tests: build the same seeded scene on the
 CUDA path (through the C ABI) and in the oracle, and compare by the
-tolerances of the method (bit-exact integers; A9 agreement rule for hits and
-visibility; 1e-4 relative radiance)."""
+tolerances of the method (bit-exact integers; for hits and visibility the
+agreement rule: >= 99.99 % of samples agree and every disagreement is a near
+tie of the two nearest hits; 1e-4 relative radiance)."""
 from __future__ import annotations
 
 import os
@@ -64,7 +65,7 @@ def gbuf_of(gbuf_tensor):
 
 
 def compare_samples(gpu: dict, ref: dict, ids=None):
-    """A9 rule: hit id and visibility bits agree on >= 99.99% of samples, and
+    """Agreement rule: hit id and visibility bits agree on >= 99.99% of samples, and
     every disagreement is a sample whose oracle two nearest hits lie within
     1e-5 relative distance.  Returns (agree fraction, bad mask)."""
     gp, gv = gpu["prim"], gpu["vis"]

@@ -3,7 +3,8 @@ the nearest hit of every sample with the same ray-triangle test and the
 same (t, original index) tie-break, so images and G-buffers must be equal
 bit for bit -- across cameras outside, inside and grazing the scene, both
 sample counts, row bands, the fallback cases and the headline frame after
-motion.  The oracle check of the raster path itself is the A9 rule."""
+motion.  The raster path itself is checked against the oracle by the
+agreement rule for hits and visibility and 1e-4 radiance."""
 import numpy as np
 import pytest
 
@@ -88,7 +89,7 @@ def test_raster_equals_traversal_mid(fb):
 
 
 def test_raster_against_oracle(fb):
-    """The raster path alone against the oracle (A9 rule, radiance)."""
+    """The raster path alone against the oracle (agreement rule, radiance)."""
     torch = torch_cuda()
     w = sg.workload_tiny41k()
     cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 128, 96, 4)

@@ -2,7 +2,8 @@
 geometry, rays met in each body's frame): identity poses reduce it to the
 single-level renderer bit for bit; its per-body trees equal brute force
 over every body's triangles; under rigid motion it agrees with the
-single-level (world-space) renderer up to near ties (A9)."""
+single-level (world-space) renderer up to near ties (the two nearest hits
+within 1e-5 relative t)."""
 import numpy as np
 
 import oracle
