@@ -1,8 +1,8 @@
 """Smooth shading normals and sRGB albedo on the GPU (§IV-A-1 vertex normals
-and colour decode) against the oracle: hits and visibility by the
-agreement rule, t exact, radiance within 1e-4, under rigid motion and refits, through the pipelined (double-
-buffered), batched, G-buffer shading and backward paths; switching the
-normals off restores the flat image bit for bit."""
+and colour decode) against the oracle: hits and visibility by the agreement
+rule, t exact, radiance within 1e-4, under rigid motion and refits, through
+the pipelined (double-buffered), batched, G-buffer shading and backward
+paths; switching the normals off restores the flat image bit for bit."""
 import numpy as np
 import pytest
 
