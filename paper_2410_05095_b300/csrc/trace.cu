@@ -1,14 +1,17 @@
 // Per-frame render kernels:
 //   k_primary      nearest hit per sample (replaces the rasterised main pass
 //                  of §IV-A-1; 4-spp supersampling in the role of the MSAA
-//                  of §IV-B-2)
-//   k_shade        per sample: any-hit shadow ray per light (§IV-B-3), Cook-
-//                  Torrance GGX + Lambert shading (§IV-B-1), box-filter
-//                  resolve of the pixel's samples (§IV-B-2)
-//   k_shade_gbuf   shading of a stored G-buffer with device parameters
+//                  of §IV-B-2); queues one shadow ray per lit light
+//   k_shadow       the queued any-hit shadow rays (§IV-B-3), one visibility
+//                  bit per sample and light
+//   k_shade        per sample: Cook-Torrance GGX + Lambert shading of the
+//                  visible lights (§IV-B-1), box-filter resolve of the
+//                  pixel's samples (§IV-B-2); also shades a stored G-buffer
+//                  with device parameters (fire_shade)
 //   k_shade_bwd    its backward: dL/d(material params, light intensities)
 // All of them are persistent: a grid of SMs x k blocks whose warps pull
-// 32-sample tasks from an atomic counter until the image is done.
+// work (32-sample tasks, or 32 queued rays) from an atomic counter until
+// the image is done.
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
@@ -20,9 +23,9 @@ namespace {
 
 // Nearest hit per sample; writes the sample's record (prim, t, cast bits,
 // leaf position) and, for every light with n.l > 0 at the hit, appends a
-// shadow ray (lifted origin, unit direction, range, sample|light) to a dense
-// queue: one ballot per light, one atomicAdd per warp, lanes ranked by the
-// popcount of the lower lanes.
+// shadow ray (lifted origin, unit direction, range, sample|light) to that
+// light's segment of a dense queue: one ballot per light, one atomicAdd per
+// warp, lanes ranked by the popcount of the lower lanes.
 // MODE 0: traversal.  After a raster pass (raster.cu): MODE 1 traverses only
 // if that pass fell back, MODE 2 takes each sample's hit from its key
 // otherwise; exactly one of the two does the work.
