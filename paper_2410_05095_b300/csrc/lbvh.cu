@@ -1,9 +1,10 @@
 // LBVH build and refit (§IV-B-3 acceleration-structure build; §IV-C per-body
 // world matrices each frame), restated as a Karras (2012) linear BVH:
 //   transform -> centroid bounds -> 63-bit Morton codes -> stable LSD radix
-//   sort -> radix-tree topology -> bottom-up boxes.
-// The refit re-runs only the transform and the bottom-up boxes with the
-// topology of the last build.
+//   sort -> radix-tree topology -> bottom-up boxes -> collapse into the 4-wide
+//   tree the traversal walks.
+// The refit re-runs only the transform and the 4-wide tree's boxes, bottom
+// up, with the topology of the last build.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
