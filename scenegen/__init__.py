@@ -386,7 +386,9 @@ def workload_grad500k(width: int = 512, height: int = 512) -> Workload:
 
 def batch16(nscenes: int = 16, ncams_per: int = 4, tmin: float = 20e3, tmax: float = 2e6,
             seed_offset: int = 3):
-    """Scenes of uneven size, four orbit cameras each, 1-3 lights each, 1 spp."""
+    """Scenes of uneven size (target T log-uniform in [tmin, tmax], rounded to
+    whole spheres inside that range), four orbit cameras each, 1-3 lights
+    each, 1 spp."""
     rng = Rng(SEED_BASE + seed_offset)
     res = [(128, 128), (256, 256), (320, 240), (640, 480)]
     scenes, cams, cam_scene, lights = [], [], [], []
@@ -394,6 +396,11 @@ def batch16(nscenes: int = 16, ncams_per: int = 4, tmin: float = 20e3, tmax: flo
         T = math.exp(rng.uniform(math.log(tmin), math.log(tmax)))
         g = 64 if T < 200e3 else (128 if T < 800e3 else 256)
         n = max(1, int(round((T - 2 * g * g) / 5120.0)))
+        # whole spheres: keep the total inside [tmin, tmax]
+        while 2 * g * g + 5120 * n < tmin:
+            n += 1
+        while 2 * g * g + 5120 * n > tmax and n > 1:
+            n -= 1
         scenes.append(scene_icospheres_terrain(rng, n, g, 32))
         nl = 1 + int(rng.u() * 3)
         lights.append(LIGHTS_MAIN[:nl])

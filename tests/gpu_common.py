@@ -95,3 +95,22 @@ def assert_radiance_close(img_gpu: np.ndarray, img_ref: np.ndarray, ok_pixels: n
 
 def pixel_ok_mask(bad_samples: np.ndarray, W: int, H: int, spp: int) -> np.ndarray:
     return ~bad_samples.reshape(H, W, spp).any(axis=2)
+
+
+def compare_images(img_gpu: np.ndarray, img_ref: np.ndarray, ref: dict, spp: int):
+    """Image-level form of the agreement rule, for paths that return images
+    only (the batch): a pixel agrees when its coverage (alpha) is equal and
+    its radiance is within 1e-4 relative; >= 99.99 % of the pixels agree, and
+    every pixel that does not holds a sample whose oracle two nearest hits
+    lie within 1e-5 relative distance.  Returns the disagreeing-pixel mask."""
+    H, W = img_ref.shape[:2]
+    a, b = img_gpu[..., :3].astype(np.float64), img_ref[..., :3].astype(np.float64)
+    rel = (np.abs(a - b) / np.maximum(np.abs(b), 1e-6)).max(axis=2)
+    ok = (img_gpu[..., 3] == img_ref[..., 3]) & (rel <= REL_TOL_RADIANCE)
+    rt, rt2 = ref["t"], ref["t2"]
+    with np.errstate(invalid="ignore"):
+        tie = (np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))).reshape(H, W, spp).any(axis=2)
+    bad = ~ok
+    assert bad.mean() <= 1.0 - AGREE_MIN, f"pixel agreement {1 - bad.mean():.6f}"
+    assert not (bad & ~tie).any(), f"{int((bad & ~tie).sum())} disagreeing pixels without a near tie"
+    return bad

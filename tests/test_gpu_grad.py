@@ -1,7 +1,9 @@
-"""Differentiable shading on the GPU: the hand-written backward kernel
-against the oracle's FP64 analytic gradient (1e-4) and FP64 central finite
-differences (1e-3), both with |delta| <= tol * max(|g_ref|, 1e-3 ||g_ref||_inf),
-and the torch.autograd.Function wrapper."""
+"""Differentiable shading on the GPU at the size of the gradient workload
+(499,712 triangles, 512 x 512, 1 spp, 32 materials, 2 lights): the
+hand-written backward kernel against the oracle's FP64 analytic gradient
+(1e-4) and FP64 central finite differences (1e-3), both with
+|delta| <= tol * max(|g_ref|, 1e-3 ||g_ref||_inf), and the
+torch.autograd.Function wrapper."""
 import numpy as np
 import pytest
 
@@ -23,7 +25,7 @@ def _close(g, ref, tol):
 def setup():
     torch = torch_cuda()
     import paper_2410_05095_b300 as fb
-    w = sg.workload_grad500k(192, 192)
+    w = sg.workload_grad500k()  # 512 x 512, 1 spp, 32 materials, 2 lights
     cam, lights = w.camera, w.lights
     G, S = build_pair(w.scene)
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
@@ -31,14 +33,18 @@ def setup():
     g = gbuf_of(gb)
     ref = S.render_all_samples(cam, lights, threads=THREADS)
     _, bad = compare_samples(g, ref)
-    assert not bad.any(), "gradient test needs identical visibility"
+    # the loss covers the pixels whose samples agree (a near tie allowed by
+    # the agreement rule would give the two sides different fixed
+    # visibility); both sides use the same mask
+    keep = (~bad).reshape(cam.height, cam.width, cam.spp).all(axis=2)
+    assert keep.mean() >= 0.9999
     P0 = oracle.params_of(w.scene.mats)
     I0 = np.array([l.intensity for l in lights], np.float64)
     tm, ti = sg.perturbed_params(w.scene.mats, I0)
     Pt = oracle.params_of(tm)
     target = S.shade_f64(cam, lights, ref, Pt, ti.astype(np.float64))
     return dict(torch=torch, fb=fb, w=w, cam=cam, lights=lights, G=G, S=S, gb=gb, ref=ref, P0=P0, I0=I0,
-                target=target)
+                target=target, keep=keep)
 
 
 def _gpu_grad(s, P, I):
@@ -51,6 +57,7 @@ def _gpu_grad(s, P, I):
     tgt = torch.from_numpy(s["target"].astype(np.float32)).cuda()
     dimg = torch.zeros_like(img)
     dimg[..., :3] = 2.0 * (img[..., :3] - tgt) / npx
+    dimg[..., :3] *= torch.from_numpy(s["keep"].astype(np.float32)).cuda()[..., None]
     dP = torch.zeros_like(params)
     dI = torch.zeros_like(inten)
     s["G"].shade_backward(s["gb"], cam, s["lights"], params, inten, dimg, dP, dI)
@@ -63,13 +70,13 @@ def test_backward_matches_oracle_analytic(setup):
     # oracle analytic gradient at the same upstream (FP64 forward image)
     img64 = s["S"].shade_f64(s["cam"], s["lights"], s["ref"], s["P0"], s["I0"])
     npx = s["cam"].width * s["cam"].height * 3
-    d64 = 2.0 * (img64 - s["target"]) / npx
+    d64 = 2.0 * (img64 - s["target"]) / npx * s["keep"][..., None]
     rP, rI = s["S"].grad_f64(s["cam"], s["lights"], s["ref"], s["P0"], s["I0"], d64)
     err = _close(np.concatenate([gP.ravel(), gI]), np.concatenate([rP.ravel(), rI]), 1e-4)
     assert err <= 1e-4, err
     # the forward image agrees with the FP64 twin too
     a = img.cpu().numpy()[..., :3].astype(np.float64)
-    assert np.max(np.abs(a - img64) / np.maximum(np.abs(img64), 1e-6)) < 2e-3
+    assert np.max((np.abs(a - img64) / np.maximum(np.abs(img64), 1e-6))[s["keep"]]) < 2e-3
 
 
 def test_backward_matches_finite_differences(setup):
@@ -78,8 +85,10 @@ def test_backward_matches_finite_differences(setup):
     S, cam, lights, ref = s["S"], s["cam"], s["lights"], s["ref"]
     npx = cam.width * cam.height * 3
 
+    keep = s["keep"][..., None]
+
     def loss(P, I):
-        return float(np.sum((S.shade_f64(cam, lights, ref, P, I) - s["target"]) ** 2) / npx)
+        return float(np.sum(((S.shade_f64(cam, lights, ref, P, I) - s["target"]) ** 2) * keep) / npx)
 
     used = np.unique(s["w"].scene.tri_mat[ref["prim"][ref["prim"] >= 0]])
     fd, g = [], []
@@ -111,8 +120,9 @@ def test_autograd_function_and_descent(setup):
     P = torch.from_numpy(s["P0"].astype(np.float32)).cuda().requires_grad_(True)
     I = torch.from_numpy(s["I0"].astype(np.float32)).cuda().requires_grad_(True)
     tgt = torch.from_numpy(s["target"].astype(np.float32)).cuda()
+    keep = torch.from_numpy(s["keep"].astype(np.float32)).cuda()[..., None]
     img = FireShade.apply(P, I, s["G"], s["gb"], s["cam"], s["lights"])
-    loss = ((img[..., :3] - tgt) ** 2).mean()
+    loss = (((img[..., :3] - tgt) ** 2) * keep).sum() / (3 * keep.numel())
     loss.backward()
     _, _, gP, gI = _gpu_grad(s, s["P0"], s["I0"])
     assert np.allclose(P.grad.cpu().numpy(), gP, rtol=1e-5, atol=1e-12)
