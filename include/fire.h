@@ -296,12 +296,19 @@ int fire_shade_backward(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_c
  * they run, e.g. a frame loop whose device memory is fixed at start-up, or a
  * host that must not pay the device synchronisation an allocation can cause).
  * Same arguments, results and accumulate-into-outputs behaviour as
- * fire_shade_backward, within the same tolerance.  Its scratch (counters and
- * the FP64 accumulator) is a fixed array inside the library image, 33,024 B
- * per GPU that loads the library, held until the process exits.
+ * fire_shade_backward, within the same tolerance; unlike it, the call is not
+ * timed by the stage profiler (fire_profile_*), whose events it would have to
+ * create.  Its scratch (counters and the FP64 accumulator) is a fixed array
+ * inside the library image, 33,024 B per GPU that loads the library, held
+ * until the process exits.
  *  - nmat*5 + nlights must be <= 4096, else FIRE_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *    that device current).  That first call may also make CUDA load the
+ *    library's module on the device (lazy module loading is CUDA's default),
+ *    and the driver then allocates the array and may synchronise: make one
+ *    warm-up call at start-up, before the frame loop and before any stream
+ *    capture.  After a cudaDeviceReset in the process the cached address is
+ *    stale: do not call this entry point again in that process.
  *  - Every call shares the one array and clears it on `stream` before use:
  *    calls whose GPU work overlaps (other streams or host threads) race. */
 int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec* gbuf, const fire_camera* cam,

@@ -152,7 +152,7 @@ struct fire_scene_s {
   uint32_t* vals_alt = nullptr; // [nt]
   uint32_t* hist = nullptr;     // [kSortBins * nblocks]
   uint32_t* ctrl = nullptr;     // [32]: [0..7] task counters, [8] error word, [9..14] bounds,
-                                //       [16..22] raster pass
+                                //       [16..22] raster pass, [24..31] shadow rays queued per light
   int32_t* rank = nullptr;      // [nt] original triangle -> sorted position
   // render scratch
   fire_gbuffer_rec* gscratch = nullptr;

@@ -33,7 +33,10 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device.  In host code the
 // array's name only stands in for the symbol, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached.  The first lookup
+// on a device can load this file's module there (CUDA loads modules lazily
+// by default), which is when the driver allocates the array; a cached
+// address goes stale if the process resets the device (cudaDeviceReset).
 int scratch_address(unsigned char** out) {
   int dev = 0;
   if (cudaError_t e = cudaGetDevice(&dev)) return cuda_check(e, "cudaGetDevice");
@@ -99,6 +102,9 @@ extern "C" int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec*
   if (int e = cuda_check(cudaMemsetAsync(ctrl, 0, kNoAllocCtrlBytes, st), "clear scratch")) return e;
   if (int e = cuda_check(cudaMemsetAsync(acc, 0, sizeof(double) * nacc, st), "clear scratch")) return e;
   a.ctrl = ctrl;
+  // later calls that default to the scene's last stream (fire_debug_dump,
+  // fire_sync_status) see this one, as after fire_shade_backward
+  s->last_stream = st;
   frame_acquire(s, st);
   const int e = shade_backward_on(a, inten, dL_drgba, dparams, dinten, acc, st);
   frame_release(s, st);

@@ -4,8 +4,16 @@ It serves callers that cannot call cudaMalloc while they run -- a frame loop
 whose device memory is fixed at start-up, or a host that must not pay the
 device synchronisation an allocation can cause.  Its scratch is a fixed
 array inside the library, so it must give the same gradients as
-fire_shade_backward, call after call, and refuse a parameter count that does
-not fit that array.  (This file is collected last on purpose.)"""
+fire_shade_backward, call after call, allocate nothing (the library's
+allocation-failure hook stays armed through the calls and the scene's device
+bytes do not change), and refuse a parameter count that does not fit that
+array.
+
+The file is named to be collected last: it is the newest addition, and a run
+that stops at the first failure has then already run every other test.  It
+does not depend on running last: each test builds its own scene, and the
+fixture below disarms the allocation-failure hook whatever happened before or
+during the test."""
 import numpy as np
 import pytest
 
@@ -20,6 +28,14 @@ def _close(g, ref):
     g, ref = np.asarray(g, np.float64).ravel(), np.asarray(ref, np.float64).ravel()
     floor = 1e-3 * np.abs(ref).max()
     return float(np.max(np.abs(g - ref) / np.maximum(np.abs(ref), floor)))
+
+
+@pytest.fixture(autouse=True)
+def disarmed_alloc_hook():
+    import paper_2410_05095_b300 as fb
+    fb.fire.fail_next_alloc(0)
+    yield
+    fb.fire.fail_next_alloc(0)
 
 
 def test_noalloc_backward_matches_fire_shade_backward():
@@ -46,10 +62,17 @@ def test_noalloc_backward_matches_fire_shade_backward():
     torch.cuda.synchronize()
     assert float(dP_ref.abs().sum()) > 0
 
-    for _ in range(2):  # two calls in a row share (and must re-clear) the scratch
-        dP, dI = torch.zeros_like(params), torch.zeros_like(inten)  # caller-owned outputs
+    outs = [(torch.zeros_like(params), torch.zeros_like(inten)) for _ in range(2)]  # caller-owned
+    torch.cuda.synchronize()
+    bytes_before = G.info()["bytes"]
+    # the next library allocation would fail: the calls below must make none
+    fb.fire.fail_next_alloc(1)
+    for dP, dI in outs:  # two calls in a row share (and must re-clear) the scratch
         G.shade_backward_noalloc(gb, cam, lights, params, inten, dimg, dP, dI)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    fb.fire.fail_next_alloc(0)
+    assert G.info()["bytes"] == bytes_before
+    for dP, dI in outs:
         assert _close(dP.cpu(), dP_ref.cpu()) <= REL_TOL
         assert _close(dI.cpu(), dI_ref.cpu()) <= REL_TOL
     assert G.sync_status() == 0
