@@ -134,13 +134,41 @@ def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shad
 
 def committed_counter(kind: str, kernel: str):
     """Per-launch ncu counter of the current kernels from the committed
-    summary: kind "dram_bytes" (dram__bytes_read.sum + dram__bytes_write.sum)
-    or "warp_inst" (smsp__inst_executed.sum); None if not captured."""
+    summary: kind "dram_bytes" (dram__bytes_read.sum + dram__bytes_write.sum),
+    "warp_inst" (smsp__inst_executed.sum) or "l2_bytes" (lts__t_bytes.sum);
+    None if not captured."""
     p = os.path.join(ROOT, "profiles", "counters_frame7m.txt")
     if os.path.exists(p):
         lines = [l for l in open(p) if not l.startswith("#")]
         return json.loads("".join(lines)).get(kind, {}).get(kernel)
     return None
+
+
+def l2_read_probe(fb, torch, sizes_mb=(24, 48, 80), reps=40):
+    """L2 read bandwidth, measured the way the kernels are timed (CUDA events
+    on the launching stream, after a warm-up launch): fire_probe_read over a
+    buffer that fits in L2 (126 MB), `reps` reads per launch, best over the
+    buffer sizes and 5 launches each.  GB/s of bytes read."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(4 * sms, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    best, where = 0.0, None
+    for mb in sizes_mb:
+        buf = torch.ones(mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+        fb.fire.probe_read(buf, reps, sink)
+        for _ in range(5):
+            e0.record(stream)
+            fb.fire.probe_read(buf, reps, sink)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gbs = buf.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+            if gbs > best:
+                best, where = gbs, mb
+        del buf
+    return {"gbs": best, "buffer_mb": where, "reps": reps,
+            "how": "fire_probe_read: (SMs x 4) blocks x 256 threads, 16-B ld.global.cg loads of an "
+                   "L2-resident buffer, best of 5 launches per size, CUDA events"}
 
 
 def load_peaks():
@@ -152,13 +180,34 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------ CPU baseline
-def cpu_oracle_frame(w, xf_build, xf_frame, nsamples: int, seed: int = 7):
-    """The oracle as it stands on the host: one refit of the frame (timed)
-    plus a bounded random sample of the frame's samples (timed), scaled to a
-    whole frame.  Single-threaded."""
-    import oracle
-    S = oracle.OracleScene(w.scene)
-    S.update(xf_build, rebuild=True)
+def host_threads() -> int:
+    """Host threads for the oracle's split runs: std::thread::hardware_concurrency()
+    as Python sees it (os.cpu_count), limited to the cores this process may use."""
+    n = os.cpu_count() or 1
+    if hasattr(os, "sched_getaffinity"):
+        n = min(n, len(os.sched_getaffinity(0)))
+    return max(1, n)
+
+
+def oracle_samples(S, cam, lights, ids, threads: int):
+    """The oracle's sample renderer over `ids`, split into contiguous chunks
+    over `threads` host threads (ctypes releases the GIL; the oracle's render
+    only reads the scene)."""
+    if threads <= 1:
+        S.render_samples(cam, lights, ids, want_t2=False)
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(np.sort(ids), threads)
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda c: S.render_samples(cam, lights, c, want_t2=False), chunks))
+
+
+def cpu_oracle_frame(S, w, xf_frame, nsamples: int, threads: int, seed: int = 7):
+    """The oracle as it stands on the host (S: an oracle scene built at the
+    first pose): one refit of the frame (timed, single-threaded: the
+    oracle's refit is a serial post-order walk) plus a bounded random sample
+    of the frame's samples (timed), scaled to a whole frame, on `threads`
+    host threads."""
     t0 = time.perf_counter()
     S.update(xf_frame, rebuild=False)
     t_refit = time.perf_counter() - t0
@@ -166,10 +215,10 @@ def cpu_oracle_frame(w, xf_build, xf_frame, nsamples: int, seed: int = 7):
     n = cam.width * cam.height * cam.spp
     ids = np.random.default_rng(seed).choice(n, nsamples, replace=False)
     t0 = time.perf_counter()
-    S.render_samples(cam, w.lights, ids, want_t2=False)
+    oracle_samples(S, cam, w.lights, ids, threads)
     t_samp = time.perf_counter() - t0
     ms = 1e3 * (t_refit + t_samp * n / nsamples)
-    return ms, {"refit_s": t_refit, "sample_s": t_samp, "samples": nsamples}
+    return ms, {"refit_s": t_refit, "sample_s": t_samp, "samples": nsamples, "threads": threads}
 
 
 def reference_arm(args, rank, world):
@@ -184,7 +233,8 @@ def reference_arm(args, rank, world):
     S.update(xf0, rebuild=True)
     cam = w.camera
     n = cam.width * cam.height * cam.spp
-    per = max(200, args.ref_samples)
+    threads = host_threads()
+    per = max(200, args.ref_samples) * threads
     rng = np.random.default_rng(11)
     times = []
     for i, xf in enumerate(frames):
@@ -192,18 +242,18 @@ def reference_arm(args, rank, world):
         S.update(xf, rebuild=False)
         t1 = time.perf_counter()
         ids = rng.choice(n, per, replace=False)
-        S.render_samples(cam, w.lights, ids, want_t2=False)
+        oracle_samples(S, cam, w.lights, ids, threads)
         t2 = time.perf_counter()
         if i >= args.warmup:
             times.append(1e3 * ((t1 - t0) + (t2 - t1) * n / per))
     ms = float(np.mean(times))
-    sample = (f"each step: oracle refit of the frame + {per} random samples of its "
-              f"{n:,}, scaled to the frame; single thread")
+    sample = (f"each step: oracle refit of the frame (one thread) + {per} random samples of its "
+              f"{n:,} split over {threads} host threads, scaled to the frame")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w, args.steps),
-            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -286,8 +336,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-samples", type=int, default=6000, help="oracle samples for the CPU baseline")
-    ap.add_argument("--ref-samples", type=int, default=1500, help="oracle samples per reference step")
+    ap.add_argument("--cpu-samples", type=int, default=40000,
+                    help="oracle samples per host thread for the CPU baseline")
+    ap.add_argument("--ref-samples", type=int, default=4000,
+                    help="oracle samples per host thread per reference step")
     ap.add_argument("--no-side", action="store_true", help="skip the batched and backward side runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     ap.add_argument("--render-bps", type=int, default=7,
@@ -441,9 +493,33 @@ def main():
     G.profile_read()
 
     # --- the 100-frame sequence of the workload: build at frame 0, refit 1..99 --------
+    # In the headline's mode (pipelined, refit only): a frame's time is the
+    # interval between the ends of consecutive renders on the render stream,
+    # so the median and p95 cover the tree's decay under motion over the
+    # whole sequence, not only the first frames after the build.
     G.build(xf_build)
-    seq = []
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(100)]
+    ends[0].record(stream)
+    for i in range(99):
+        G.refit(xf_dev[i], stream=refit_stream)
+        G.render(cam, lights, out=out, opts=ropts)
+        ends[i + 1].record(stream)
+    stream.wait_stream(refit_stream)
+    torch.cuda.synchronize()
+    seqp = np.array([ends[i].elapsed_time(ends[i + 1]) for i in range(99)])
+    G.profile_read()
+
+    def seq_summary(x):
+        return {"median_ms": float(np.median(x)), "p95_ms": float(np.percentile(x, 95)), "mean_ms": float(x.mean()),
+                "first_ms": float(x[0]), "last_ms": float(x[-1])}
+
+    sequence = {"frames": 99, "mode": "pipelined, refit only (the mode of the headline value)", **seq_summary(seqp),
+                "by_decile_ms": [float(np.median(c)) for c in np.array_split(seqp, 10)],
+                "note": "frame time = interval between the ends of consecutive renders; refit + render per "
+                        "frame after a build at frame 0 (tree quality decays with motion)"}
+    # the same frames serially on one stream (refit, render, refit, ...)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(99)]
+    G.build(xf_build)
     for i in range(99):
         evs[i][0].record(stream)
         G.refit(xf_dev[i])
@@ -452,12 +528,10 @@ def main():
     torch.cuda.synchronize()
     seq = np.array([a.elapsed_time(b) for a, b in evs])
     G.profile_read()
-    sequence = {"frames": 99, "median_ms": float(np.median(seq)), "p95_ms": float(np.percentile(seq, 95)),
-                "mean_ms": float(seq.mean()), "first_ms": float(seq[0]), "last_ms": float(seq[-1]),
-                "note": "refit + render per frame after a build at frame 0 (tree quality decays with motion)"}
-    # the same sequence with a full rebuild (fire_bvh_build) in place of the
-    # refit every 25th frame: the rebuild frames cost more, the others stay
-    # near the frame-1 quality
+    sequence["serial"] = seq_summary(seq)
+    # serial, with a full rebuild (fire_bvh_build) in place of the refit every
+    # 25th frame: the rebuild frames cost more, the others stay near the
+    # frame-1 quality
     G.build(xf_build)
     for i in range(99):
         evs[i][0].record(stream)
@@ -470,9 +544,8 @@ def main():
     torch.cuda.synchronize()
     seq2 = np.array([a.elapsed_time(b) for a, b in evs])
     G.profile_read()
-    sequence["rebuild_every_25"] = {"median_ms": float(np.median(seq2)), "p95_ms": float(np.percentile(seq2, 95)),
-                                    "mean_ms": float(seq2.mean()), "last_ms": float(seq2[-1]),
-                                    "rebuild_frames_ms": [float(seq2[i]) for i in range(24, 99, 25)]}
+    sequence["serial_rebuild_every_25"] = {**seq_summary(seq2),
+                                           "rebuild_frames_ms": [float(seq2[i]) for i in range(24, 99, 25)]}
 
     # --- rays traced per frame (shadow rays counted from the G-buffer) ------------
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
@@ -499,6 +572,16 @@ def main():
                 "all_kernels": {k: {"ms": avg[k], "algorithmic_bytes": alg[k],
                                     "gbs": alg[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None}
                                 for k in avg}}
+    # the traversal kernels reuse the tree through L1 and L2: their L2 traffic
+    # (ncu lts__t_bytes.sum per launch) over the live launch time, against the
+    # L2 read bandwidth measured here with the same kind of timing
+    l2b = committed_counter("l2_bytes", dom)
+    if l2b:
+        probe = l2_read_probe(fb, torch)
+        got = l2b / (avg[dom] * 1e-3) / 1e9
+        roofline["l2"] = {"bytes_per_launch": l2b, "achieved": got, "peak": probe["gbs"], "unit": "GB/s",
+                          "frac": got / probe["gbs"], "peak_source": probe["how"],
+                          "peak_buffer_mb": probe["buffer_mb"]}
     # the traversal kernels are issue-bound: warp instructions per launch (ncu)
     # over the live launch time, against 4 schedulers x 1 warp-inst/clock per SM
     clocks = clk.summary()
@@ -530,10 +613,18 @@ def main():
         line["batched"] = batch_ratio(fb, torch)
         line["backward"] = backward_ratio(fb, torch)
     if rank == 0 and not args.no_cpu:
-        ms_cpu, info = cpu_oracle_frame(w, xf_build, frames[0], args.cpu_samples)
-        line["cpu_baseline"] = {"value": ms_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": (f"oracle refit of one frame + {info['samples']} random samples of "
-                                           f"its {primary_rays:,}, scaled to the frame; single thread")}
+        import oracle
+        threads = host_threads()
+        S = oracle.OracleScene(w.scene)
+        S.update(xf_build, rebuild=True)
+        ms_mt, info = cpu_oracle_frame(S, w, frames[0], args.cpu_samples * threads, threads)
+        ms_1, info1 = cpu_oracle_frame(S, w, frames[1], args.cpu_samples, 1)
+        line["cpu_baseline"] = {"value": ms_mt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": (f"oracle refit of one frame (one thread) + {info['samples']} random "
+                                           f"samples of its {primary_rays:,} split over {threads} host threads "
+                                           f"(hardware_concurrency), scaled to the frame"),
+                                "single_thread": {"value": ms_1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"the same with {info1['samples']} samples on one thread"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -362,6 +362,17 @@ int fire_profile_read(fire_scene s, double* ms8, int64_t* launches8);
  * ran during that call. */
 int fire_batch_last_config(int32_t* out4);
 
+/* Measurement aid (the paper has no counterpart): one launch of
+ * (SMs x 4) blocks of 256 threads that reads the `bytes` at `buf` `reps`
+ * times with 16-B loads cached in L2 only (not L1) and folds them into
+ * `sink` (device uint32[sink_words], sink_words >= 4 x SMs; its contents
+ * have no meaning).  Timed by the caller with events on `stream`: bytes x
+ * reps / time is the L2 read bandwidth for a buffer that fits in L2, the
+ * DRAM read bandwidth for one that does not.  buf must be 16-B aligned and
+ * bytes a positive multiple of 16, reps >= 1, else FIRE_ERR_INVALID_ARG. */
+int fire_probe_read(const void* buf, int64_t bytes, int32_t reps, uint32_t* sink, int32_t sink_words,
+                    void* stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* fire_last_error(void);
 

@@ -27,8 +27,8 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_shade_backward", "fire_debug_dump", "fire_sync_status",
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
-           "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_last_error",
-           "fire_version"]
+           "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_probe_read",
+           "fire_last_error", "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -93,6 +93,7 @@ def lib():
             "fire_display": [P, i32, i32, C.c_float, i32, P, P, P],
             "fire_scene_set_materials_ex": [P, P, i32, i32],
             "fire_scene_set_normals": [P, P, i32, P],
+            "fire_probe_read": [P, i64, i32, P, i32, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -345,3 +346,11 @@ def fail_next_alloc(nth: int = 1):
 
 def version() -> str:
     return lib().fire_version().decode()
+
+
+def probe_read(buf, reps: int, sink, stream=None):
+    """fire_probe_read over a contiguous device tensor `buf` (all of its
+    bytes, `reps` times); `sink` is a device int32/uint32 tensor of at least
+    4 words per SM."""
+    _check(lib().fire_probe_read(_ptr(buf), buf.numel() * buf.element_size(), int(reps), _ptr(sink),
+                                 int(sink.numel()), _stream(stream)))

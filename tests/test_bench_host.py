@@ -67,3 +67,24 @@ def test_workload_config_names_the_headline_frame():
     assert cfg["workload"].startswith("frame7m") and cfg["frames"] == 20
     assert cfg["parallelism"] == "replicas" and "L2" in cfg["l2"]
     json.dumps(cfg)
+
+
+def test_host_threads_and_split_sample():
+    """The CPU baseline's thread count is the cores this process may use, and
+    the split oracle run covers every requested sample once (chunks are
+    contiguous in sorted order)."""
+    n = bench.host_threads()
+    assert 1 <= n <= (os.cpu_count() or 1)
+    seen = []
+
+    class FakeScene:
+        def render_samples(self, cam, lights, ids, want_t2=False):
+            seen.append(list(ids))
+
+    import numpy as np
+    ids = np.random.default_rng(0).choice(1000, 97, replace=False)
+    bench.oracle_samples(FakeScene(), None, [], ids, 4)
+    assert sorted(sum(seen, [])) == sorted(ids.tolist()) and len(seen) == 4
+    seen.clear()
+    bench.oracle_samples(FakeScene(), None, [], ids, 1)
+    assert seen == [list(ids)]
