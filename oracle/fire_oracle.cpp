@@ -138,25 +138,39 @@ Box box_union(const Box& a, const Box& b) {
 }
 
 // ---------------------------------------------------------------------------
-// Morton code of a centroid: q_a = min(floor((c_a - lo_a) * s_a), 2^21 - 1),
-// s_a = 2^21 / (hi_a - lo_a) (0 if hi_a == lo_a); bit k of q_x -> bit 3k+2,
-// of q_y -> 3k+1, of q_z -> 3k.  Written as a plain per-bit loop.
+// Morton code of a centroid with m bits per axis:
+//   q_a = min(floor((c_a - lo_a) * s_a), 2^m - 1), s_a = 2^m / (hi_a - lo_a)
+//   (0 if hi_a == lo_a); bit k of q_x -> bit 3k+2, of q_y -> 3k+1, of q_z -> 3k.
+// Written as a plain per-bit loop.
+// Body prefix (scenes of several rigid bodies, §IV-C: each body moves as a
+// whole): key = body << 3m | code, with the body of the triangle's first
+// vertex, B = bits of (nbody - 1) and m = min(21, (63 - B) / 3); so all of a
+// body's triangles are consecutive in the sorted order and form one subtree
+// of the radix tree, like the paper's per-mesh bottom levels under a top
+// level (§IV-B-3).  One body: B = 0, m = 21.
 // ---------------------------------------------------------------------------
-uint32_t quantise(float c, float lo, float s) {
+uint32_t quantise(float c, float lo, float s, uint32_t qmax) {
   float f = (c - lo) * s;
   if (!(f > 0.0f)) return 0u;
-  if (f >= 2097151.0f) return 2097151u;
+  if (f >= (float)qmax) return qmax;
   return (uint32_t)f;
 }
 
-uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz) {
+uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz, int m) {
   uint64_t code = 0;
-  for (int k = 0; k < 21; ++k) {
+  for (int k = 0; k < m; ++k) {
     code |= (uint64_t)((qx >> k) & 1u) << (3 * k + 2);
     code |= (uint64_t)((qy >> k) & 1u) << (3 * k + 1);
     code |= (uint64_t)((qz >> k) & 1u) << (3 * k);
   }
   return code;
+}
+
+// Bits of the body prefix and Morton bits per axis for a scene of nbody bodies.
+void key_layout(int32_t nbody, int& B, int& m) {
+  B = 0;
+  while (nbody > 1 && (1 << B) < nbody) ++B;
+  m = std::min(21, (63 - B) / 3);
 }
 
 int clz64(uint64_t x) { int n = 0; for (int b = 63; b >= 0 && !((x >> b) & 1u); --b) ++n; return n; }
@@ -226,15 +240,22 @@ void build(orc_scene& S) {
       hi[a] = std::max(hi[a], c);
     }
   }
+  int B, m;
+  key_layout(S.nbody, B, m);
+  const float cells = (float)(1u << m);
+  const uint32_t qmax = (1u << m) - 1u;
   float s[3];
   for (int a = 0; a < 3; ++a) {
-    s[a] = (hi[a] > lo[a]) ? 2097152.0f / (hi[a] - lo[a]) : 0.0f;
+    s[a] = (hi[a] > lo[a]) ? cells / (hi[a] - lo[a]) : 0.0f;
     S.cb[a] = lo[a];
     S.cb[3 + a] = hi[a];
   }
-  for (int64_t t = 0; t < T; ++t)
-    S.morton[t] = interleave(quantise(cen[3 * t], lo[0], s[0]), quantise(cen[3 * t + 1], lo[1], s[1]),
-                             quantise(cen[3 * t + 2], lo[2], s[2]));
+  for (int64_t t = 0; t < T; ++t) {
+    const uint64_t body = B > 0 ? (uint64_t)S.vbody[S.idx[3 * t]] : 0u;
+    S.morton[t] = (body << (3 * m)) |
+                  interleave(quantise(cen[3 * t], lo[0], s[0], qmax), quantise(cen[3 * t + 1], lo[1], s[1], qmax),
+                             quantise(cen[3 * t + 2], lo[2], s[2], qmax), m);
+  }
   std::iota(S.order.begin(), S.order.end(), 0u);
   std::stable_sort(S.order.begin(), S.order.end(),
                    [&](uint32_t a, uint32_t b) { return S.morton[a] < S.morton[b]; });

@@ -1,6 +1,8 @@
 """Writes the closed-form fixtures of this folder (pure Python arithmetic;
 no renderer code is called).
 
+morton_body_prefix.txt -- see body_key_rows().
+
 brdf_normal_incidence.txt -- §IV-B-1 Cook-Torrance variant at l = v = n:
   h = n, so n.h = v.h = n.l = n.v = 1; D = 1/(pi a^2) with a = r^2 (GGX);
   F = F0 (Schlick at normal incidence); G = 1 (Schlick-GGX at x = 1);
@@ -26,6 +28,29 @@ def brdf_rows():
     return rows
 
 
+def body_key_rows():
+    """Body-prefixed Morton keys of centroids at lo / mid / hi of the bounds
+    [0, 8]^3 (§IV-C rigid bodies; the LBVH key layout of the acceleration
+    structure): B = bits of (nbody - 1), m = min(21, (63 - B) // 3) bits per
+    axis; per axis q = 0 at lo, 2^(m-1) at mid ((c - lo) 2^m / (hi - lo) is
+    exactly 2^(m-1)), 2^m - 1 at hi (clamped); x -> bit 3k+2, y -> 3k+1,
+    z -> 3k; key = body << 3m | code."""
+    rows = []
+    for nbody in (2, 3, 65):
+        B = (nbody - 1).bit_length()
+        m = min(21, (63 - B) // 3)
+        q = {"lo": 0, "mid": 1 << (m - 1), "hi": (1 << m) - 1}
+        for body, pt in ((0, ("hi", "hi", "hi")), (nbody - 1, ("lo", "lo", "lo")), (nbody - 1, ("hi", "mid", "lo")),
+                         (nbody // 2, ("mid", "mid", "mid")), (1, ("lo", "hi", "mid"))):
+            code = 0
+            for k in range(m):
+                code |= ((q[pt[0]] >> k) & 1) << (3 * k + 2)
+                code |= ((q[pt[1]] >> k) & 1) << (3 * k + 1)
+                code |= ((q[pt[2]] >> k) & 1) << (3 * k)
+            rows.append((nbody, body, pt, (body << (3 * m)) | code))
+    return rows
+
+
 def main():
     with open(os.path.join(HERE, "brdf_normal_incidence.txt"), "w") as f:
         f.write("# l = v = n: f_d = (1-F0)(1-m) albedo/pi, f_s = F0/(4 pi r^4), F0 = 0.04(1-m) + albedo m\n")
@@ -33,6 +58,13 @@ def main():
         f.write("# albedo roughness metallic f_d f_s\n")
         for row in brdf_rows():
             f.write(" ".join(repr(float(x)) for x in row) + "\n")
+    with open(os.path.join(HERE, "morton_body_prefix.txt"), "w") as f:
+        f.write("# Body-prefixed Morton keys: B = bits of (nbody-1), m = min(21, (63-B)//3) bits per axis,\n")
+        f.write("# key = body << 3m | interleave(q) (x -> 3k+2, y -> 3k+1, z -> 3k); centroid bounds [0,8]^3,\n")
+        f.write("# q = 0 at lo, 2^(m-1) at mid, 2^m - 1 at hi.  (Written by make_golden.py.)\n")
+        f.write("# nbody body x y z key\n")
+        for nbody, body, pt, key in body_key_rows():
+            f.write(f"{nbody} {body} {pt[0]} {pt[1]} {pt[2]} {key:#018x}\n")
 
 
 if __name__ == "__main__":

@@ -48,9 +48,75 @@ def test_morton_hand_codes():
         assert int(codes[2 + i]) == want, (i, hex(int(codes[2 + i])), hex(want))
 
 
-def _deinterleave(code: int):
+def test_morton_body_prefix_hand_codes():
+    """Scenes of several rigid bodies: keys carry the body id above the Morton
+    bits (tests/golden/morton_body_prefix.txt, derived from the key layout in
+    plain integer arithmetic); the body is that of the triangle's first
+    vertex."""
+    pos = {"lo": 0.0, "mid": 4.0, "hi": 8.0}
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "morton_body_prefix.txt")):
+        if line.strip() and not line.startswith("#"):
+            nb, body, x, y, z, key = line.split()
+            rows.setdefault(int(nb), []).append((int(body), [pos[x], pos[y], pos[z]], int(key, 16)))
+    assert sorted(rows) == [2, 3, 65]
+    for nbody, cases in rows.items():
+        tris = [_point_tri([0, 0, 0]), _point_tri([8, 8, 8])] + [_point_tri(p) for _, p, _ in cases]
+        vb = np.repeat([0, 0] + [b for b, _, _ in cases], 3).astype(np.uint16)
+        S = oracle.OracleScene(_scene_from_tris(np.array(tris), nbody=nbody, vbody=vb))
+        S.update(np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (nbody, 1)), rebuild=True)
+        codes = S.get("morton")
+        assert list(S.get("centroid_bounds")) == [0, 0, 0, 8, 8, 8]
+        for i, (_, _, want) in enumerate(cases):
+            assert int(codes[2 + i]) == want, (nbody, i, hex(int(codes[2 + i])), hex(want))
+    # a triangle whose vertices belong to different bodies takes its first vertex's
+    tris = [_point_tri([0, 0, 0]), _point_tri([8, 8, 8]), _point_tri([8, 8, 8])]
+    vb = np.array([0, 0, 0, 1, 1, 1, 2, 0, 1], np.uint16)
+    S = oracle.OracleScene(_scene_from_tris(np.array(tris), nbody=3, vbody=vb))
+    S.update(np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (3, 1)), rebuild=True)
+    assert [int(c) >> 60 for c in S.get("morton")] == [0, 1, 2]
+
+
+def test_each_body_is_one_subtree():
+    """With body-prefixed keys every body's triangles are consecutive in the
+    sorted order and are exactly the leaves of one node of the radix tree
+    (checked on a soup of interleaved bodies whose boxes overlap)."""
+    rng = sg.Rng(321)
+    nbody, n = 7, 700
+    tris = []
+    for _ in range(n):
+        c = np.array([rng.uniform(-3, 3) for _ in range(3)])
+        tris.append(np.stack([c, c + [0.2, 0.0, 0.05], c + [0.0, 0.15, 0.1]]))
+    body_of_tri = np.array([int(rng.u() * nbody) for _ in range(n)])
+    vb = np.repeat(body_of_tri, 3).astype(np.uint16)
+    S = oracle.OracleScene(_scene_from_tris(np.array(tris), nbody=nbody, vbody=vb))
+    S.update(np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (nbody, 1)), rebuild=True)
+    order, children = S.get("order"), S.get("children")
+    sorted_body = body_of_tri[order]
+    assert np.all(np.diff(sorted_body) >= 0)  # bodies in id order, each consecutive
+    T = n
+    leaves = {}
+
+    def rec(code):
+        if code >= T - 1:
+            leaves[code] = {code - (T - 1)}
+            return leaves[code]
+        a, b = int(children[code][0]), int(children[code][1])
+        leaves[code] = rec(a) | rec(b)
+        return leaves[code]
+
+    import sys
+    sys.setrecursionlimit(10000)
+    rec(0)
+    covers = [frozenset(v) for v in leaves.values()]
+    for b in range(nbody):
+        mine = frozenset(np.nonzero(sorted_body == b)[0].tolist())
+        assert len(mine) >= 2 and mine in covers, b
+
+
+def _deinterleave(code: int, m: int = 21):
     q = [0, 0, 0]
-    for k in range(21):
+    for k in range(m):
         for a in range(3):
             q[a] |= ((code >> (3 * k + 2 - a)) & 1) << k
     return q
@@ -79,6 +145,35 @@ def test_morton_decodes_to_quantised_centroid(tiny41k):
             assert q[a] <= 2 ** 21 - 1
             tol = 5 * 2.0 ** -24 * x + 0.1
             assert q[a] - tol <= x and (x < q[a] + 1 + tol or q[a] == 2 ** 21 - 1), (i, a, x, q[a])
+
+
+def test_body_keys_decode_to_body_and_quantised_centroid():
+    """Moving workload (65 bodies: B = 7 prefix bits, m = 18 bits per axis):
+    each key's top bits are the body of the triangle's first vertex and its
+    low 3m bits de-interleave to q <= 2^m (c - lo)/(hi - lo) < q + 1, up to the
+    FP32 quantiser's roundings."""
+    w = sg.workload_frame7m(nspheres=40, cells=16)
+    sc = w.scene
+    assert sc.nbody == 65
+    B, m = 7, 18
+    S = oracle.OracleScene(sc)
+    xf = w.motion.xforms()
+    S.update(xf, rebuild=True)
+    codes = S.get("morton")
+    world = S.get("world").astype(np.float64)
+    tri = world[sc.idx.astype(np.int64)]
+    c = 0.5 * (tri.min(1) + tri.max(1))
+    lo, hi = c.min(0), c.max(0)
+    body = sc.vert_body[sc.idx[:, 0]].astype(np.int64)
+    rng = np.random.default_rng(1)
+    for i in rng.choice(sc.nt, 500, replace=False):
+        code = int(codes[i])
+        assert code >> (3 * m) == body[i] and code >> 63 == 0
+        q = _deinterleave(code & ((1 << (3 * m)) - 1), m)
+        for a in range(3):
+            x = (c[i, a] - lo[a]) / (hi[a] - lo[a]) * 2 ** m
+            tol = 5 * 2.0 ** -24 * x + 0.1
+            assert q[a] - tol <= x and (x < q[a] + 1 + tol or q[a] == 2 ** m - 1), (i, a, x, q[a])
 
 
 def test_sort_is_stable_permutation(tiny41k):
