@@ -112,31 +112,42 @@ __device__ __forceinline__ uint64_t spread3(uint32_t x) {
   return v;
 }
 
-// q = min(floor((c - lo) * s), 2^21 - 1) with s = 2^21 / (hi - lo) (0 if
+// q = min(floor((c - lo) * s), 2^m - 1) with s = 2^m / (hi - lo) (0 if
 // hi == lo): FP32 subtract, FP32 multiply, truncation.
-__device__ __forceinline__ uint32_t quantise(float c, float lo, float s) {
+__device__ __forceinline__ uint32_t quantise(float c, float lo, float s, uint32_t qmax) {
   float f = (c - lo) * s;
   if (!(f > 0.0f)) return 0u;
-  if (f >= 2097151.0f) return 2097151u;
+  if (f >= (float)qmax) return qmax;
   return (uint32_t)f;
 }
 
-// Build step 2: 63-bit Morton code (x -> bit 3k+2, y -> 3k+1, z -> 3k).
+// Build step 2: Morton key with m bits per axis (x -> bit 3k+2, y -> 3k+1,
+// z -> 3k) below a body prefix: key = body << 3m | code, body = that of the
+// triangle's first vertex.  With more than one rigid body every body's
+// triangles are consecutive in the sorted order and form one subtree, so a
+// refit under the bodies' rigid motions never widens a node by the drift
+// between two bodies (only the nodes above the bodies mix them).  The host
+// picks B = bits of (nbody - 1) and m = min(21, (63 - B) / 3); one body:
+// B = 0, m = 21.
 __global__ void k_morton(const float4* __restrict__ cen, int64_t nt, const uint32_t* __restrict__ bounds,
-                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         const uint32_t* __restrict__ idx, const uint16_t* __restrict__ vb, int prefix_bits,
+                         int m, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                          uint64_t* __restrict__ keys_orig) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
+  const float cells = (float)(1u << m);
+  const uint32_t qmax = (1u << m) - 1u;
   float lo[3], s[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     lo[k] = ord2f(bounds[k]);
     float hi = ord2f(bounds[3 + k]);
-    s[k] = (hi > lo[k]) ? 2097152.0f / (hi - lo[k]) : 0.0f;
+    s[k] = (hi > lo[k]) ? cells / (hi - lo[k]) : 0.0f;
   }
   float4 c = cen[i];
-  uint64_t code = (spread3(quantise(c.x, lo[0], s[0])) << 2) | (spread3(quantise(c.y, lo[1], s[1])) << 1) |
-                  spread3(quantise(c.z, lo[2], s[2]));
+  uint64_t code = (spread3(quantise(c.x, lo[0], s[0], qmax)) << 2) |
+                  (spread3(quantise(c.y, lo[1], s[1], qmax)) << 1) | spread3(quantise(c.z, lo[2], s[2], qmax));
+  if (prefix_bits > 0) code |= (uint64_t)vb[idx[3 * i]] << (3 * m);
   keys[i] = code;
   keys_orig[i] = code;
   vals[i] = (uint32_t)i;
@@ -657,7 +668,11 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   prof_begin(s, kStageBuild, st);
   k_centroids<<<(int)std::min<int64_t>(grid_for(T, 256), (int64_t)sm_count() * 8), 256, 0, st>>>(
       s->rest, s->idx, s->vbody, s->xf, T, s->cen, bounds);
-  k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->keys, s->order, s->keys_orig);
+  int prefix_bits = 0;
+  while (s->nbody > 1 && (1 << prefix_bits) < s->nbody) ++prefix_bits;
+  const int mbits = std::min(21, (63 - prefix_bits) / 3);
+  k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->idx, s->vbody, prefix_bits, mbits, s->keys,
+                                             s->order, s->keys_orig);
   // sort (keys, order) with ping-pong through (keys_alt, vals_alt); 7 passes
   const int ntiles = (int)((T + kSortTile - 1) / kSortTile);
   uint32_t* totals = s->hist + (int64_t)kSortBins * ntiles;
