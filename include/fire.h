@@ -335,8 +335,51 @@ int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec* gbuf, cons
  *                                       (bits), e1 = v1-v0 xyz, material (bits),
  *                                       e2 = v2-v0 xyz, 0
  *  6 centroid bounds                    float[6]
+ *  7 4-wide nodes of the current buffer  128 B x (4-wide node count, fire_scene_info
+ *                                       out[6]); two-level: the bottom levels
+ * two-level scenes only (else FIRE_ERR_INVALID_ARG):
+ *  8 bottom-level root of each body      int32[nbody] (-1: no triangles)
+ *  9 top level of the current buffer    128 B x (nbody + 2) (4-wide nodes; leaf
+ *                                       link ~body; unused nodes undefined)
+ * 10 its record                         16 B: float eps, float span, int32 nodes
+ *                                       in use, int32 error (nonzero: not built)
+ * 11 body matrices of the current buffer float[nbody*12]
  * bytes must equal the exact size; otherwise FIRE_ERR_INVALID_ARG. */
 int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes);
+
+/* Two-level acceleration structure (§IV-B-3: a bottom level per mesh built
+ * once, a top level over the instances rebuilt every frame).  enable = 1:
+ * the next fire_bvh_build builds one bottom level per body over the REST
+ * pose (an LBVH with body-prefixed keys: each body's subtree, collapsed into
+ * its own 4-wide tree, never refit) and a top level over the bodies' world
+ * boxes (the 8 corners of the rest box through the body's matrix, widened by
+ * 2^-10 (1 + largest |coordinate|)); each fire_bvh_refit then only rebuilds
+ * the top level (one block) into the other frame buffer.  Rays meet a body's
+ * triangles in the body's frame, o' = R^T (o - t), d' = R^T d (R, t: the
+ * body's 3x4 matrix); hits rank by (t of that ray, original index); the hit
+ * normal is R (e1 x e2) of the rest triangle; the shadow-ray lift is 1e-4 x
+ * the diagonal of the union of the instances' world boxes.
+ * Requires every triangle's three vertices in one body and nbody <= 1024
+ * (else FIRE_ERR_INVALID_ARG); not available with smooth normals, the raster
+ * primary pass or fire_render_batch (FIRE_ERR_INVALID_ARG).  A top level
+ * deeper than 16 4-wide levels sets FIRE_ERR_STACK_OVERFLOW.  Changing the
+ * mode synchronises the device and leaves the scene unbuilt
+ * (FIRE_ERR_NOT_BUILT until the next fire_bvh_build). */
+int fire_scene_set_two_level(fire_scene s, int32_t enable);
+
+/* Check of the two-level traversal on the host (test hook; synchronises the
+ * device): the scene's current structures are copied to host memory and
+ * the traversal code of the render kernels, compiled for the host, runs the
+ * n rays o3/d3 (host float[n*3]; the direction need not be unit).  any = 0:
+ * nearest hit over (0, inf) -> prim (original index or -1) and t; any = 1:
+ * any hit in (0, tmax[i]) other than triangle skip[i] (skip may be NULL) ->
+ * hit[i].  Every load is checked to lie inside the copied arrays and be
+ * aligned for its width.  err_out: the traversal's error bits (1 stack,
+ * 2 iteration cap, 4 a link outside the structure) | 0x100 if any load
+ * failed the check.  Outputs may be NULL.  Single-level scene ->
+ * FIRE_ERR_INVALID_ARG. */
+int fire_debug_trace_host(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip,
+                          int64_t n, int32_t any, int32_t* prim, float* t, uint8_t* hit, uint32_t* err_out);
 
 /* Synchronise `stream`, then return and clear the scene's sticky device error
  * (FIRE_OK, FIRE_ERR_STACK_OVERFLOW or FIRE_ERR_TIMEOUT). */

@@ -211,7 +211,9 @@ void free_scene(fire_scene_s* s) {
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris_buf[0],
                   s->tris_buf[1], s->nodes4_buf[0], s->nodes4_buf[1], s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze};
+                  s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
+                  s->blas_root, s->body_box, s->body_range, s->xf_ident, s->tlas_buf[0], s->tlas_buf[1],
+                  s->tinfo_buf[0], s->tinfo_buf[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int b = 0; b < 2; ++b) {
@@ -261,8 +263,8 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
       {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
       {(void**)&s->lvl_aux, 12 * (size_t)kMaxDepth4 + 16},
-      {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
-      {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T - 1, 1)},
+      {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T, 1)},
+      {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T, 1)},
       {(void**)&s->q4, 16 * (size_t)std::max<int64_t>(T - 1, 1)},
   };
   for (auto& a : list)
@@ -277,13 +279,43 @@ int alloc_lbvh(fire_scene_s* s) {
   return FIRE_OK;
 }
 
+// Two-level buffers (first two-level build): bottom-level roots, rest boxes,
+// body ranges, identity matrices, and per frame buffer the top level and its
+// record.
+int alloc_two_level(fire_scene_s* s, cudaStream_t st) {
+  if (s->blas_root) return FIRE_OK;
+  const size_t nb = (size_t)s->nbody;
+  struct A { void** p; size_t b; } list[] = {
+      {(void**)&s->blas_root, 4 * nb},     {(void**)&s->body_box, 32 * nb},
+      {(void**)&s->body_range, 8 * nb},    {(void**)&s->xf_ident, 48 * nb},
+      {(void**)&s->tlas_buf[0], 128 * (nb + 2)}, {(void**)&s->tlas_buf[1], 128 * (nb + 2)},
+      {(void**)&s->tinfo_buf[0], sizeof(TlasInfo)}, {(void**)&s->tinfo_buf[1], sizeof(TlasInfo)},
+  };
+  for (auto& a : list)
+    if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "two-level buffers");
+  // every pointer the traversal reads with 16-B loads is 16-B aligned (cudaMalloc gives 256)
+  for (const void* p : {(const void*)s->tlas_buf[0], (const void*)s->tlas_buf[1], (const void*)s->tinfo_buf[0],
+                        (const void*)s->tinfo_buf[1], (const void*)s->body_box})
+    if (reinterpret_cast<uintptr_t>(p) & 15u) return set_error(FIRE_ERR_CUDA, "misaligned two-level buffer");
+  std::vector<float> id(12 * nb, 0.0f);
+  for (size_t b = 0; b < nb; ++b) id[12 * b] = id[12 * b + 5] = id[12 * b + 10] = 1.0f;
+  if (int e = cuda_check(cudaMemcpyAsync(s->xf_ident, id.data(), 48 * nb, cudaMemcpyHostToDevice, st), "copy"))
+    return e;
+  for (int b = 0; b < 2; ++b)
+    if (int e = cuda_check(cudaMemsetAsync(s->tinfo_buf[b], 0, sizeof(TlasInfo), st), "memset")) return e;
+  return cuda_check(cudaStreamSynchronize(st), "sync");  // id is a host vector
+}
+
 cudaStream_t as_stream(void* st) { return reinterpret_cast<cudaStream_t>(st); }
 
-// Point s->tris / s->nodes4 at buffer b.
+// Point the scene's current frame data at buffer b (two-level: the bottom
+// levels stay in buffer 0; the top level and its record follow b).
 void select_buffer(fire_scene_s* s, int b) {
   s->cur = b;
-  s->tris = s->tris_buf[b];
-  s->nodes4 = s->nodes4_buf[b];
+  s->tris = s->two_level ? s->tris_buf[0] : s->tris_buf[b];
+  s->nodes4 = s->two_level ? s->nodes4_buf[0] : s->nodes4_buf[b];
+  s->tlas = s->tlas_buf[b];
+  s->tinfo = s->tinfo_buf[b];
 }
 
 }  // namespace
@@ -469,8 +501,19 @@ int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
   // both buffers are rewritten: wait for their last users
   for (int b = 0; b < 2; ++b)
     if (s->used_rec[b]) cudaStreamWaitEvent(st, s->used_ev[b], 0);
+  if (s->two_level)
+    if (int e = alloc_two_level(s, st)) return e;
   select_buffer(s, 0);
   if (int e = lbvh_build(s, st)) return e;
+  if (s->two_level && s->nt > 0) {
+    // bottom levels done (rest pose, built once); the top level of this frame
+    if (int e = tlas_build(s, st)) return e;
+    for (int b = 0; b < 2; ++b) {
+      cudaEventRecord(s->ready_ev[b], st);
+      s->ready_rec[b] = true;
+    }
+    return FIRE_OK;
+  }
   if (s->nt > 0) {
     // buffer 1 gets the 4-wide links (a refit rewrites boxes and records only)
     if (int e = cuda_check(cudaMemcpyAsync(s->nodes4_buf[1], s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(s->n4, 1),
@@ -499,7 +542,8 @@ int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
   if (int e = load_xforms(s, body_xforms, xforms_on_device, st)) return e;
   const int prev = s->cur;
   select_buffer(s, target);
-  if (int e = lbvh_refit(s, st)) {
+  // two-level: only the top level is rebuilt (the bottom levels are at rest)
+  if (int e = s->two_level ? tlas_build(s, st) : lbvh_refit(s, st)) {
     select_buffer(s, prev);
     return e;
   }
@@ -527,6 +571,9 @@ static int fill_args(fire_scene s, const fire_camera* cam, const fire_light* lig
   a->iter_cap = s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64;
   a->ctrl = s->ctrl;
   set_smooth_args(a, s);
+  set_level_args(a, s);
+  if (s->two_level && s->vnrm)
+    return set_error(FIRE_ERR_INVALID_ARG, "smooth normals need the single-level structure");
   return FIRE_OK;
 }
 
@@ -562,6 +609,8 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
       (o.flags & ~(FIRE_RENDER_ALLOW_SHALLOW_STACK | FIRE_RENDER_TRACE_PRIMARY | FIRE_RENDER_RASTER_PRIMARY)) != 0 ||
       ((o.flags & FIRE_RENDER_TRACE_PRIMARY) && (o.flags & FIRE_RENDER_RASTER_PRIMARY)))
     return set_error(FIRE_ERR_INVALID_ARG, "invalid render options");
+  if (s->two_level && (o.flags & FIRE_RENDER_RASTER_PRIMARY))
+    return set_error(FIRE_ERR_INVALID_ARG, "the raster primary pass needs the single-level structure");
   if (o.stack_depth > 0 && o.stack_depth < std::min(stack_need(s), 128) &&
       !(o.flags & FIRE_RENDER_ALLOW_SHALLOW_STACK))
     return set_error(FIRE_ERR_INVALID_ARG, "stack_depth below the " + std::to_string(stack_need(s)) +
@@ -632,6 +681,7 @@ int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_came
   for (int i = 0; i < nscenes; ++i) {
     if (!scenes[i]) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene in batch");
     if (!scenes[i]->built) return set_error(FIRE_ERR_NOT_BUILT, "batch scene not built");
+    if (scenes[i]->two_level) return set_error(FIRE_ERR_INVALID_ARG, "the batch needs single-level scenes");
     if (light_off[i + 1] < light_off[i] || light_off[i + 1] - light_off[i] > kMaxLights)
       return set_error(FIRE_ERR_INVALID_ARG, "light_off not ascending or > 8 lights");
   }
@@ -789,10 +839,47 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
       for (int k = 0; k < 6; ++k) o[k] = ord2f(u[k]);
       return FIRE_OK;
     }
+    case 7:  // 4-wide nodes of the current buffer (two-level: the bottom levels)
+      if (!need(128 * (size_t)s->n4)) break;
+      return s->n4 ? get(host_dst, s->nodes4, 128 * (size_t)s->n4) : FIRE_OK;
+    case 8:
+    case 9:
+    case 10:
+    case 11: {
+      if (!s->two_level) return set_error(FIRE_ERR_INVALID_ARG, "two-level dump of a single-level scene");
+      const size_t nb = (size_t)s->nbody;
+      if (what == 8) return need(4 * nb) ? get(host_dst, s->blas_root, 4 * nb) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+      if (what == 9) return need(128 * (nb + 2)) ? get(host_dst, s->tlas, 128 * (nb + 2)) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+      if (what == 10) return need(sizeof(TlasInfo)) ? get(host_dst, s->tinfo, sizeof(TlasInfo)) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+      return need(48 * nb) ? get(host_dst, s->xf_buf[s->cur], 48 * nb) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+    }
     default:
       return set_error(FIRE_ERR_INVALID_ARG, "unknown dump selector");
   }
   return set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+}
+
+int fire_scene_set_two_level(fire_scene s, int32_t enable) {
+  g_err.clear();
+  if (!s) return set_error(FIRE_ERR_INVALID_ARG, "NULL scene");
+  if (enable != 0 && enable != 1) return set_error(FIRE_ERR_INVALID_ARG, "enable must be 0 or 1");
+  if ((bool)enable == s->two_level) return FIRE_OK;
+  if (enable) {
+    if (s->nbody > kMaxTlasBodies)
+      return set_error(FIRE_ERR_INVALID_ARG, "two-level mode supports at most " + std::to_string(kMaxTlasBodies) +
+                                                 " bodies");
+    uint32_t bad = 0;
+    if (int e = lbvh_count_mixed(s, s->last_stream, &bad)) return e;
+    if (bad)
+      return set_error(FIRE_ERR_INVALID_ARG, std::to_string(bad) + " triangles have vertices in different bodies");
+    if (s->vnrm) return set_error(FIRE_ERR_INVALID_ARG, "smooth normals need the single-level structure");
+  }
+  // renders in flight may read the old structure
+  if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
+  s->two_level = enable != 0;
+  s->built = false;
+  for (int b = 0; b < 2; ++b) s->ready_rec[b] = s->used_rec[b] = false;
+  return FIRE_OK;
 }
 
 int fire_sync_status(fire_scene s, void* stream) {

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -52,8 +53,29 @@ constexpr int kEmptyLink = (int)0x80000000;
 // Triangle record in leaf (sorted) order, 48 B:
 //   v0.xyz, w = original triangle index (bits)
 //   e1 = v1 - v0, w = material index (bits)
-//   e2 = v2 - v0, w = 0
+//   e2 = v2 - v0, w = 0 (two-level mode: the triangle's body, bits)
 // e1/e2 are the same FP32 differences the ray/triangle test and the normal use.
+// Single level: world coordinates of the frame; two-level: rest coordinates.
+
+// Two-level acceleration structure (§IV-B-3: one bottom level per mesh,
+// built once; a top level over the instances, rebuilt every frame).  The
+// bottom levels are the bodies' 4-wide subtrees of an LBVH built over the
+// rest pose with body-prefixed keys; the top level is a 4-wide tree over the
+// bodies' world boxes (the 8 transformed corners of the rest box), whose
+// leaf links are ~body.  Per frame buffer: the top-level nodes and this
+// record.
+struct __align__(16) TlasInfo {
+  float eps;    // shadow-ray lift: 1e-4 x diagonal of the union of the instances' world boxes
+  float span;   // largest |coordinate| of the instance world boxes and the rest boxes (box-test slack)
+  int32_t n;    // top-level 4-wide nodes in use (root = node 0; 0 = no instance)
+  int32_t err;  // nonzero: the top level was not built (deeper than kTlasMaxDepth4)
+};
+static_assert(sizeof(TlasInfo) == 16, "top-level record must be 16 bytes");
+static_assert(alignof(TlasInfo) == 16, "top-level record must be 16-byte aligned");
+static_assert(alignof(Node4) == 16 && sizeof(Node4) % 16 == 0, "4-wide nodes are read with 16-byte loads");
+constexpr int kMaxTlasBodies = 1024;   // bodies of a two-level scene (one block builds the top level)
+constexpr int kTlasMaxDepth4 = 16;     // top-level 4-wide depths
+constexpr int kExitInstance = 0x7ffffffe;  // traversal stack marker: back to the world ray
 
 constexpr int kMaxLights = 8;
 constexpr int kMaxHeight = 128;              // tree height is at most 97 (64 + 32 prefix bits + 1)
@@ -129,7 +151,7 @@ struct fire_scene_s {
                                 //   lengths (u32 [kMaxDepth4]) and the node counter (u32)
   std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
   int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf
-  fire::Node4* nodes4 = nullptr;// [max(nt-1, 1)] 4-wide traversal tree (current buffer)
+  fire::Node4* nodes4 = nullptr;// [max(nt, 1)] 4-wide traversal tree (current buffer)
   int64_t n4 = 0;               // 4-wide nodes in use
   int height4 = 0;              // 4-wide levels
   int32_t* q4 = nullptr;        // build queue: 2 x [nt] (binary node, 4-wide node) pairs
@@ -152,7 +174,8 @@ struct fire_scene_s {
   uint32_t* vals_alt = nullptr; // [nt]
   uint32_t* hist = nullptr;     // [kSortBins * nblocks]
   uint32_t* ctrl = nullptr;     // [32]: [0..7] task counters, [8] error word, [9..14] bounds,
-                                //       [16..22] raster pass, [24..31] shadow rays queued per light
+                                //       [15] mixed-body count, [16..22] raster pass,
+                                //       [24..31] shadow rays queued per light
   int32_t* rank = nullptr;      // [nt] original triangle -> sorted position
   // render scratch
   fire_gbuffer_rec* gscratch = nullptr;
@@ -168,6 +191,18 @@ struct fire_scene_s {
   size_t graze_n = 0;
   float4* jobs = nullptr;          // shadow-ray queue, 32 B per ray
   size_t jobs_n = 0;               // capacity in rays
+  // two-level mode (fire_scene_set_two_level): bottom levels in
+  // nodes4_buf[0] / tris_buf[0] (rest pose, built once), top level per frame
+  // buffer
+  bool two_level = false;
+  int32_t* blas_root = nullptr;   // [nbody] 4-wide node of each body's bottom level (-1: no triangles)
+  float4* body_box = nullptr;     // [2*nbody] rest box of each body (lo, hi; xyz)
+  int32_t* body_range = nullptr;  // [2*nbody] first and last sorted position of each body (build)
+  float* xf_ident = nullptr;      // [nbody*12] identity matrices (the bottom levels are built at rest)
+  fire::Node4* tlas_buf[2] = {nullptr, nullptr};       // [nbody + 2] each
+  fire::TlasInfo* tinfo_buf[2] = {nullptr, nullptr};
+  fire::Node4* tlas = nullptr;    // current frame buffer's top level
+  fire::TlasInfo* tinfo = nullptr;
   // batch cache (see batch.cu)
   void* batch = nullptr;
   int64_t iter_cap = 0;
@@ -205,6 +240,9 @@ void prof_end(fire_scene_s* s, int stage, cudaStream_t st, int launches = 1);
 // lbvh.cu
 int lbvh_build(fire_scene_s* s, cudaStream_t st);
 int lbvh_refit(fire_scene_s* s, cudaStream_t st);
+// two-level mode: top level of the current frame buffer from s->xf (one
+// block; also copies the matrices into the buffer's xf_buf)
+int tlas_build(fire_scene_s* s, cudaStream_t st);
 int lbvh_validate(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host);
 
 // trace.cu
@@ -229,6 +267,12 @@ struct RenderArgs {
   const uint16_t* vbody;
   fire_gbuffer_rec* g;          // per-sample records
   float* out;                   // [H*W*4]
+  // two-level mode (tlas != nullptr): top level, its record, each body's
+  // bottom-level root; bxf holds the frame's body matrices
+  const Node4* tlas;
+  const TlasInfo* tinfo;
+  const int32_t* blas_root;
+  int nbody;
 };
 // Raster primary pass (raster.cu).  Words of fire_scene_s::ctrl it uses:
 constexpr int kCtrlRasterPieces = 16;  // queued pieces
@@ -268,10 +312,22 @@ inline void set_smooth_args(RenderArgs* a, const fire_scene_s* s) {
   a->sidx = s->sidx;
   a->vbody = s->vbody;
 }
+// Two-level inputs of the scene's current frame buffer (tlas == nullptr: single level).
+inline void set_level_args(RenderArgs* a, const fire_scene_s* s) {
+  a->tlas = s->two_level ? s->tlas : nullptr;
+  a->tinfo = s->two_level ? s->tinfo : nullptr;
+  a->blas_root = s->blas_root;
+  a->nbody = s->nbody;
+}
+// lbvh.cu: number of triangles whose three vertices do not share one body
+int lbvh_count_mixed(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host);
 // display.cu: sRGB-encoded albedo of the [nmat*5] material table -> linear
 int srgb_decode_materials(float* mats, int nmat, cudaStream_t st);
-// stack entries the 4-wide traversal of this scene can need: 3 per level + sentinel
-inline int stack_need(const fire_scene_s* s) { return 3 * s->height4 + 1; }
+// stack entries the 4-wide traversal of this scene can need: 3 per level +
+// sentinel; two-level: 3 per bottom and top level + sentinel + exit marker
+inline int stack_need(const fire_scene_s* s) {
+  return s->two_level ? 3 * (s->height4 + kTlasMaxDepth4) + 2 : 3 * s->height4 + 1;
+}
 int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, float* dparams, float* dinten,
                       double* acc, cudaStream_t st);
 
@@ -289,21 +345,44 @@ int batch_last_info(int32_t* out4);
 //   cross(a,b) = (fma(ay,bz, -(az*by)), fma(az,bx, -(ax*bz)), fma(ax,by, -(ay*bx)))
 //   normalize(v) = v / sqrt(dot(v,v))
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
-__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 add3(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 neg3(float3 a) { return f3(-a.x, -a.y, -a.z); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) {
+// (host and device: the host build of this file runs with -ffp-contract=off,
+// and fmaf, '/' and sqrtf are correctly rounded on both, so a host call gives
+// the device's bits -- the host emulation of the traversal relies on it)
+__host__ __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ float3 add3(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ float3 neg3(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__host__ __device__ __forceinline__ float dot3(float3 a, float3 b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+__host__ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return f3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x)));
 }
-__device__ __forceinline__ float3 normalize3(float3 v) {
+__host__ __device__ __forceinline__ float3 normalize3(float3 v) {
   float len = sqrtf(dot3(v, v));
   return f3(v.x / len, v.y / len, v.z / len);
 }
-__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+__host__ __device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+
+// Bit casts (device intrinsics; memcpy on the host).
+__host__ __device__ __forceinline__ float bits_as_float(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ int float_as_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_int(f);
+#else
+  int i;
+  memcpy(&i, &f, 4);
+  return i;
+#endif
+}
 
 // Ordered-integer image of a float (monotone), for exact atomic min/max.
 __device__ __forceinline__ uint32_t f2ord(float f) {

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "fire_internal.cuh"
 
@@ -371,7 +372,7 @@ __global__ void k_refit_build(const float4* __restrict__ rest, const uint16_t* _
                               const uint32_t* __restrict__ smat, int64_t nt, float4* __restrict__ tris,
                               Node* nodes, const int32_t* __restrict__ leaf_slot,
                               const int32_t* __restrict__ node_slot, uint32_t* counters,
-                              float* __restrict__ xfb, int nxf) {
+                              float* __restrict__ xfb, int nxf, int body_in_w) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nxf) xfb[i] = xf[i];  // the frame buffer's copy of the body matrices
   const int lane = threadIdx.x & 31;
@@ -386,7 +387,7 @@ __global__ void k_refit_build(const float4* __restrict__ rest, const uint16_t* _
     float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
     tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
     tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
-    tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+    tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, body_in_w ? __uint_as_float((uint32_t)vb[id.x]) : 0.0f);
     lo = fmin3(w0, fmin3(w1, w2));
     hi = fmax3(w0, fmax3(w1, w2));
     slot = nt > 1 ? leaf_slot[i] : 0;
@@ -551,6 +552,416 @@ __global__ void __launch_bounds__(256) k_fill4(const Node* __restrict__ nodes, N
 }
 
 // ----------------------------------------------------------------------------
+// Two-level mode (§IV-B-3: a bottom level per mesh, a top level over the
+// instances rebuilt every frame).  The LBVH above is built over the rest
+// pose with body-prefixed keys, so each body's triangles are one sorted
+// range and one subtree; the 4-wide collapse starts from every body's
+// subtree root, which gives each body its own 4-wide bottom level.
+// ----------------------------------------------------------------------------
+// Sorted range [first, last] of every body (the key prefix above bit 3m).
+__global__ void k_body_ranges(const uint64_t* __restrict__ keys, int64_t nt, int shift, int nbody,
+                              int32_t* __restrict__ range, uint32_t* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const uint64_t b = keys[i] >> shift;
+  if (b >= (uint64_t)nbody) {  // never: the key prefix is a body id
+    atomicOr(err, kErrCorrupt);
+    return;
+  }
+  if (i == 0 || (keys[i - 1] >> shift) != b) range[2 * b] = (int32_t)i;
+  if (i == nt - 1 || (keys[i + 1] >> shift) != b) range[2 * b + 1] = (int32_t)i;
+}
+
+// One block (nbody <= kMaxTlasBodies threads).  Body b with triangles gets
+// the 4-wide node rank(b) (its rank among the bodies with triangles) as its
+// bottom-level root.  Its subtree root in the Karras tree covers exactly
+// [f, l]; a node is numbered by the end of its range that its parent's split
+// falls on, so it is node l when the parent extends to the right
+// (delta(l, l+1) > delta(f-1, f)) and node f otherwise, the tree's root if
+// [f, l] is everything.  A body of one triangle becomes a 4-wide node with
+// that leaf as its only member (its box copied from the leaf's slot);
+// the others are queued for the collapse.
+__global__ void __launch_bounds__(1024) k_body_roots(const uint64_t* __restrict__ keys, int64_t nt,
+                                                     const int32_t* __restrict__ range, int nbody,
+                                                     const int32_t* __restrict__ leaf_slot,
+                                                     int32_t* __restrict__ blas_root, int32_t* __restrict__ pairs,
+                                                     uint32_t* __restrict__ qlen, Node4* __restrict__ nodes4,
+                                                     int32_t* __restrict__ leaf_slot4) {
+  __shared__ int32_t scan_a[1024], scan_m[1024];
+  const int b = threadIdx.x;
+  int32_t f = -1, l = -1;
+  if (b < nbody) {
+    f = range[2 * b];
+    l = range[2 * b + 1];
+  }
+  const bool has = f >= 0 && l >= f;
+  const bool multi = has && l > f;
+  scan_a[b] = has ? 1 : 0;
+  scan_m[b] = multi ? 1 : 0;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive scans
+    const int32_t a = b >= off ? scan_a[b - off] : 0, m = b >= off ? scan_m[b - off] : 0;
+    __syncthreads();
+    scan_a[b] += a;
+    scan_m[b] += m;
+    __syncthreads();
+  }
+  if (b == 0) {
+    qlen[0] = (uint32_t)scan_m[1023];              // depth-0 collapse queue: the multi-triangle bodies
+    qlen[kMaxDepth4] = (uint32_t)scan_a[1023];     // 4-wide nodes allocated so far: every root
+    qlen[kMaxDepth4 + 1] = (uint32_t)scan_a[1023]; // number of bottom-level roots
+  }
+  if (b >= nbody) return;
+  if (!has) {
+    blas_root[b] = -1;
+    return;
+  }
+  const int32_t q = scan_a[b] - 1;
+  blas_root[b] = q;
+  if (!multi) {  // one triangle at sorted position f
+    const int32_t slot = nt > 1 ? leaf_slot[f] : 0;
+    const float inf = __int_as_float(0x7f800000);
+    Node4* n = nodes4 + q;
+    n->lox = make_float4(inf, inf, inf, inf);
+    n->loy = n->lox;
+    n->loz = n->lox;
+    n->hix = make_float4(-inf, -inf, -inf, -inf);
+    n->hiy = n->hix;
+    n->hiz = n->hix;
+    n->link = make_int4(~f, kEmptyLink, kEmptyLink, kEmptyLink);
+    n->src = make_int4(slot, -1, -1, -1);
+    leaf_slot4[f] = 4 * q;
+    return;
+  }
+  int32_t root;
+  if (f == 0 && l == nt - 1) {
+    root = 0;
+  } else {
+    // (both positions checked: f - 1 is -1 for the first body)
+    auto delta = [&](int64_t i, int64_t j) -> int {
+      if (i < 0 || i >= nt || j < 0 || j >= nt) return -1;
+      const uint64_t x = keys[i], y = keys[j];
+      if (x != y) return __clzll((long long)(x ^ y));
+      return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+    };
+    root = delta(l, l + 1) > delta(f - 1, f) ? l : f;
+  }
+  const int32_t k = scan_m[b] - 1;
+  pairs[2 * k] = root;
+  pairs[2 * k + 1] = q;
+}
+
+// Rest box of every body: the union of its bottom-level root's members.
+__global__ void k_body_boxes(const Node4* __restrict__ nodes4, int64_t n4, const int32_t* __restrict__ blas_root,
+                             int nbody, float4* __restrict__ body_box) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbody) return;
+  const int32_t q = blas_root[b];
+  const float inf = __int_as_float(0x7f800000);
+  float3 lo = f3(inf, inf, inf), hi = f3(-inf, -inf, -inf);
+  if (q >= 0 && q < n4) {
+    const Node4& n = nodes4[q];
+    const int l[4] = {n.link.x, n.link.y, n.link.z, n.link.w};
+    const float LX[4] = {n.lox.x, n.lox.y, n.lox.z, n.lox.w}, LY[4] = {n.loy.x, n.loy.y, n.loy.z, n.loy.w};
+    const float LZ[4] = {n.loz.x, n.loz.y, n.loz.z, n.loz.w}, HX[4] = {n.hix.x, n.hix.y, n.hix.z, n.hix.w};
+    const float HY[4] = {n.hiy.x, n.hiy.y, n.hiy.z, n.hiy.w}, HZ[4] = {n.hiz.x, n.hiz.y, n.hiz.z, n.hiz.w};
+    for (int k = 0; k < 4; ++k) {
+      if (l[k] == kEmptyLink) continue;
+      lo = f3(fminf(lo.x, LX[k]), fminf(lo.y, LY[k]), fminf(lo.z, LZ[k]));
+      hi = f3(fmaxf(hi.x, HX[k]), fmaxf(hi.y, HY[k]), fmaxf(hi.z, HZ[k]));
+    }
+  }
+  body_box[2 * b] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+  body_box[2 * b + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+}
+
+// ----------------------------------------------------------------------------
+// Top level of one frame (one block of 1024 threads, nbody <= 1024).
+//   1. world box of every body with triangles: the 8 corners of its rest box
+//      through its matrix, x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row;
+//      their union gives the frame's shadow-ray lift eps = 1e-4 |hi - lo|;
+//      span = largest |coordinate| of the union and of the rest boxes
+//   2. the boxes widened by 2^-10 (1 + span) on every side (the body-frame
+//      ray's rounding against the world box test), keyed by the 30-bit Morton
+//      code of their centres (10 bits per axis) above the instance index,
+//      sorted (bitonic), Karras topology, node boxes by range union
+//   3. collapse into 4-wide nodes (thread 0, breadth first, opening the
+//      member of largest surface area), leaf links ~body
+// Also copies the matrices into the frame buffer (xfb).
+// ----------------------------------------------------------------------------
+struct TlasSmem {
+  float lo[3][kMaxTlasBodies], hi[3][kMaxTlasBodies];    // widened instance boxes
+  float nlo[3][kMaxTlasBodies], nhi[3][kMaxTlasBodies];  // binary node boxes
+  unsigned long long key[kMaxTlasBodies];
+  int32_t body[kMaxTlasBodies];
+  int32_t child[2][kMaxTlasBodies];
+  int32_t rng[2][kMaxTlasBodies];
+  int32_t queue[3][kMaxTlasBodies];  // collapse queue: binary node, 4-wide node, depth
+  int32_t scan[kMaxTlasBodies];
+  uint32_t red[8];
+};
+
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__global__ void __launch_bounds__(1024) k_tlas(const float* __restrict__ xf, int nbody,
+                                               const int32_t* __restrict__ blas_root,
+                                               const float4* __restrict__ body_box, Node4* __restrict__ tlas,
+                                               TlasInfo* __restrict__ info, float* __restrict__ xfb,
+                                               uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TlasSmem& S = *reinterpret_cast<TlasSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 12 * nbody; i += blockDim.x) xfb[i] = xf[i];
+  if (tid < 8) S.red[tid] = tid < 3 ? 0xffffffffu : 0u;  // [0..2] min lo, [3..5] max hi, [6] span, [7] unused
+  const bool has = tid < nbody && blas_root[tid] >= 0;
+  float3 wlo = f3(0, 0, 0), whi = f3(0, 0, 0);
+  float rspan = 0.0f;
+  if (has) {
+    const float* m = xf + 12 * tid;
+    const float4 rl = body_box[2 * tid], rh = body_box[2 * tid + 1];
+    rspan = fmaxf(fmaxf(fmaxf(fabsf(rl.x), fabsf(rh.x)), fmaxf(fabsf(rl.y), fabsf(rh.y))),
+                  fmaxf(fabsf(rl.z), fabsf(rh.z)));
+    for (int c = 0; c < 8; ++c) {
+      const float x = (c & 1) ? rh.x : rl.x, y = (c & 2) ? rh.y : rl.y, z = (c & 4) ? rh.z : rl.z;
+      const float3 p = f3(fmaf(m[0], x, fmaf(m[1], y, fmaf(m[2], z, m[3]))),
+                          fmaf(m[4], x, fmaf(m[5], y, fmaf(m[6], z, m[7]))),
+                          fmaf(m[8], x, fmaf(m[9], y, fmaf(m[10], z, m[11]))));
+      wlo = c ? f3(fminf(wlo.x, p.x), fminf(wlo.y, p.y), fminf(wlo.z, p.z)) : p;
+      whi = c ? f3(fmaxf(whi.x, p.x), fmaxf(whi.y, p.y), fmaxf(whi.z, p.z)) : p;
+    }
+  }
+  // compaction: instance index = rank among the bodies with triangles
+  S.scan[tid] = has ? 1 : 0;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int32_t a = tid >= off ? S.scan[tid - off] : 0;
+    __syncthreads();
+    S.scan[tid] += a;
+    __syncthreads();
+  }
+  const int ninst = S.scan[1023];
+  if (has) {
+    atomicMin(&S.red[0], f2ord(wlo.x));
+    atomicMin(&S.red[1], f2ord(wlo.y));
+    atomicMin(&S.red[2], f2ord(wlo.z));
+    atomicMax(&S.red[3], f2ord(whi.x));
+    atomicMax(&S.red[4], f2ord(whi.y));
+    atomicMax(&S.red[5], f2ord(whi.z));
+    atomicMax(&S.red[6], __float_as_uint(rspan));  // non-negative: bits order as values
+  }
+  __syncthreads();
+  const float3 ulo = f3(ord2f(S.red[0]), ord2f(S.red[1]), ord2f(S.red[2]));
+  const float3 uhi = f3(ord2f(S.red[3]), ord2f(S.red[4]), ord2f(S.red[5]));
+  const float span = fmaxf(__uint_as_float(S.red[6]),
+                           fmaxf(fmaxf(fmaxf(fabsf(ulo.x), fabsf(uhi.x)), fmaxf(fabsf(ulo.y), fabsf(uhi.y))),
+                                 fmaxf(fabsf(ulo.z), fabsf(uhi.z))));
+  if (tid == 0) {
+    TlasInfo ti;
+    const float3 ext = sub3(uhi, ulo);
+    ti.eps = ninst > 0 ? 1e-4f * sqrtf(dot3(ext, ext)) : 0.0f;
+    ti.span = ninst > 0 ? span : 0.0f;
+    ti.n = 0;
+    ti.err = 0;
+    *info = ti;
+  }
+  if (ninst == 0) return;
+  const float margin = (1.0f + span) * (1.0f / 1024.0f);
+  const int i = S.scan[tid] - 1;
+  if (has) {
+    S.lo[0][i] = wlo.x - margin;
+    S.lo[1][i] = wlo.y - margin;
+    S.lo[2][i] = wlo.z - margin;
+    S.hi[0][i] = whi.x + margin;
+    S.hi[1][i] = whi.y + margin;
+    S.hi[2][i] = whi.z + margin;
+    S.body[i] = tid;
+  }
+  __syncthreads();
+  // keys: Morton code of the widened box centre over the union box
+  int n2 = 1;
+  while (n2 < ninst) n2 <<= 1;
+  if (tid < n2) {
+    unsigned long long k = ~0ull;
+    if (tid < ninst) {
+      uint32_t q[3];
+      const float L[3] = {ulo.x, ulo.y, ulo.z}, H[3] = {uhi.x, uhi.y, uhi.z};
+      for (int a = 0; a < 3; ++a) {
+        const float c = 0.5f * (S.lo[a][tid] + S.hi[a][tid]);
+        const float ext = H[a] - L[a];
+        const float f = ext > 0.0f ? (c - L[a]) * (1024.0f / ext) : 0.0f;
+        q[a] = f > 0.0f ? (f >= 1023.0f ? 1023u : (uint32_t)f) : 0u;
+      }
+      const uint32_t code = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+      k = ((unsigned long long)code << 10) | (unsigned long long)tid;
+    }
+    S.key[tid] = k;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= n2; kk <<= 1) {  // bitonic sort, ascending
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (tid < n2) {
+        const int x = tid ^ j;
+        if (x > tid) {
+          const unsigned long long a = S.key[tid], b = S.key[x];
+          const bool up = (tid & kk) == 0;
+          if ((a > b) == up) {
+            S.key[tid] = b;
+            S.key[x] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // Karras topology over the sorted keys (unique: the index is in the low bits)
+  const int n = ninst;
+  auto kdel = [&](int a, int b) -> int {
+    if (b < 0 || b >= n) return -1;
+    return __clzll((long long)(S.key[a] ^ S.key[b]));
+  };
+  if (tid < n - 1) {
+    const int d = (kdel(tid, tid + 1) - kdel(tid, tid - 1)) >= 0 ? 1 : -1;
+    const int dmin = kdel(tid, tid - d);
+    int lmax = 2;
+    while (kdel(tid, tid + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (kdel(tid, tid + (l + t) * d) > dmin) l += t;
+    const int j = tid + l * d;
+    const int dnode = kdel(tid, j);
+    int sp = 0, t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (kdel(tid, tid + (sp + t) * d) > dnode) sp += t;
+    } while (t > 1);
+    const int gamma = tid + sp * d + (d < 0 ? -1 : 0);
+    const int lo = min(tid, j), hi = max(tid, j);
+    // child codes: internal node index, or n - 1 + sorted position for a leaf
+    S.child[0][tid] = lo == gamma ? n - 1 + gamma : gamma;
+    S.child[1][tid] = hi == gamma + 1 ? n - 1 + gamma + 1 : gamma + 1;
+    S.rng[0][tid] = lo;
+    S.rng[1][tid] = hi;
+  }
+  __syncthreads();
+  if (tid < n - 1) {  // node box = union of the instances of its range
+    float bl[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+    float bh[3] = {-bl[0], -bl[0], -bl[0]};
+    for (int p = S.rng[0][tid]; p <= S.rng[1][tid]; ++p) {
+      const int ii = (int)(S.key[p] & 1023ull);
+      for (int a = 0; a < 3; ++a) {
+        bl[a] = fminf(bl[a], S.lo[a][ii]);
+        bh[a] = fmaxf(bh[a], S.hi[a][ii]);
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      S.nlo[a][tid] = bl[a];
+      S.nhi[a][tid] = bh[a];
+    }
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  // collapse (serial, breadth first): member code c < n-1 is a binary node,
+  // c >= n-1 the instance at sorted position c - (n-1)
+  auto box_of = [&](int c, float* bl, float* bh) {
+    if (c < n - 1) {
+      for (int a = 0; a < 3; ++a) { bl[a] = S.nlo[a][c]; bh[a] = S.nhi[a][c]; }
+    } else {
+      const int ii = (int)(S.key[c - (n - 1)] & 1023ull);
+      for (int a = 0; a < 3; ++a) { bl[a] = S.lo[a][ii]; bh[a] = S.hi[a][ii]; }
+    }
+  };
+  auto area = [&](int c) {
+    float bl[3], bh[3];
+    box_of(c, bl, bh);
+    const float dx = bh[0] - bl[0], dy = bh[1] - bl[1], dz = bh[2] - bl[2];
+    return dx * dy + dy * dz + dz * dx;
+  };
+  const float inf = __int_as_float(0x7f800000);
+  int nn = 1, head = 0, tail = 0, maxdep = 1;
+  if (n == 1) {
+    S.queue[0][0] = -1;  // a single instance: one node holding it
+  } else {
+    S.queue[0][0] = 0;
+  }
+  S.queue[1][0] = 0;
+  S.queue[2][0] = 1;
+  tail = 1;
+  while (head < tail) {
+    const int x = S.queue[0][head], q = S.queue[1][head], dep = S.queue[2][head];
+    ++head;
+    int mem[4] = {0, 0, 0, 0}, cnt;
+    if (x < 0) {
+      mem[0] = n - 1;  // code of the single leaf (sorted position 0)
+      cnt = 1;
+    } else {
+      mem[0] = S.child[0][x];
+      mem[1] = S.child[1][x];
+      cnt = 2;
+      while (cnt < 4) {
+        int best = -1;
+        float ba = -1.0f;
+        for (int k = 0; k < cnt; ++k)
+          if (mem[k] < n - 1) {
+            const float a = area(mem[k]);
+            if (a > ba) { ba = a; best = k; }
+          }
+        if (best < 0) break;
+        const int c = mem[best];
+        mem[best] = S.child[0][c];
+        mem[cnt++] = S.child[1][c];
+      }
+    }
+    float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
+    int link[4];
+    for (int k = 0; k < 4; ++k) {
+      if (k >= cnt) {
+        lx[k] = ly[k] = lz[k] = inf;
+        hx[k] = hy[k] = hz[k] = -inf;
+        link[k] = kEmptyLink;
+        continue;
+      }
+      float bl[3], bh[3];
+      box_of(mem[k], bl, bh);
+      lx[k] = bl[0]; ly[k] = bl[1]; lz[k] = bl[2];
+      hx[k] = bh[0]; hy[k] = bh[1]; hz[k] = bh[2];
+      if (mem[k] < n - 1) {
+        link[k] = nn;
+        S.queue[0][tail] = mem[k];
+        S.queue[1][tail] = nn;
+        S.queue[2][tail] = dep + 1;
+        ++tail;
+        ++nn;
+        maxdep = max(maxdep, dep + 1);
+      } else {
+        link[k] = ~S.body[(int)(S.key[mem[k] - (n - 1)] & 1023ull)];
+      }
+    }
+    Node4* o = tlas + q;
+    o->lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
+    o->loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
+    o->loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
+    o->hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
+    o->hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
+    o->hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
+    o->link = make_int4(link[0], link[1], link[2], link[3]);
+    o->src = make_int4(-1, -1, -1, -1);
+  }
+  if (maxdep > kTlasMaxDepth4) {  // the traversal stack is sized for kTlasMaxDepth4 top-level depths
+    info->err = 1;
+    atomicOr(err, kErrStack);
+    return;
+  }
+  info->n = nn;
+}
+
+// ----------------------------------------------------------------------------
 // Per-frame refit of the 4-wide tree.  The collapse numbers the 4-wide nodes
 // depth by depth, so each depth is a contiguous index range whose children
 // all lie in the next one.
@@ -657,6 +1068,30 @@ int lbvh_validate(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host) {
   return cuda_check(cudaMemsetAsync(bad, 0, 4, st), "memset");
 }
 
+namespace {
+__global__ void k_count_mixed(const uint32_t* __restrict__ idx, const uint16_t* __restrict__ vb, int64_t nt,
+                              uint32_t* bad) {
+  uint32_t n = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint16_t b = vb[idx[3 * i]];
+    n += vb[idx[3 * i + 1]] != b || vb[idx[3 * i + 2]] != b;
+  }
+  if (n) atomicAdd(bad, n);
+}
+}  // namespace
+
+int lbvh_count_mixed(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host) {
+  uint32_t* bad = s->ctrl + 15;
+  if (int e = cuda_check(cudaMemsetAsync(bad, 0, 4, st), "memset")) return e;
+  if (s->nt > 0) {
+    const int g = (int)std::min<int64_t>(grid_for(s->nt, 256), 4 * 148 * 8);
+    k_count_mixed<<<g, 256, 0, st>>>(s->idx, s->vbody, s->nt, bad);
+    if (int e = cuda_check(cudaGetLastError(), "k_count_mixed")) return e;
+  }
+  if (int e = cuda_check(cudaMemcpyAsync(bad_host, bad, 4, cudaMemcpyDeviceToHost, st), "copy")) return e;
+  return cuda_check(cudaStreamSynchronize(st), "sync");
+}
+
 int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) { s->built = true; s->height = 0; return FIRE_OK; }
@@ -665,9 +1100,11 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   for (int k = 0; k < 3; ++k) { init[k] = 0xffffffffu; init[3 + k] = 0u; }
   if (int e = cuda_check(cudaMemcpyAsync(s->ctrl + 9, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy")) return e;
   uint32_t* bounds = s->ctrl + 9;
+  // two-level mode: the bottom levels are built over the rest pose
+  const float* xf_geom = s->two_level ? s->xf_ident : s->xf;
   prof_begin(s, kStageBuild, st);
   k_centroids<<<(int)std::min<int64_t>(grid_for(T, 256), (int64_t)sm_count() * 8), 256, 0, st>>>(
-      s->rest, s->idx, s->vbody, s->xf, T, s->cen, bounds);
+      s->rest, s->idx, s->vbody, xf_geom, T, s->cen, bounds);
   int prefix_bits = 0;
   while (s->nbody > 1 && (1 << prefix_bits) < s->nbody) ++prefix_bits;
   const int mbits = std::min(21, (63 - prefix_bits) / 3);
@@ -699,8 +1136,8 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
     if (int e = cuda_check(cudaMemsetAsync(s->counters, 0, 4 * (T - 1), st), "memset")) return e;
   const int nxf = 12 * s->nbody;
   k_refit_build<<<grid_for(std::max<int64_t>(T, nxf), 256), 256, 0, st>>>(
-      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes, s->leaf_slot, s->node_slot, s->counters,
-      s->xf_buf[s->cur], nxf);
+      s->rest, s->vbody, xf_geom, s->sidx, s->smat, T, s->tris, s->nodes, s->leaf_slot, s->node_slot, s->counters,
+      s->xf_buf[s->cur], nxf, s->two_level ? 1 : 0);
   prof_end(s, kStageBuild, st, 2 + 3 * kSortPasses + (T > 1 ? 1 : 0) + 2);
   if (int e = cuda_check(cudaGetLastError(), "build kernels")) return e;
   Node n0;
@@ -716,21 +1153,42 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   // nodes at depth d); a 4-wide depth consumes at least one binary level,
   // so `height` launches suffice, and the lengths are read back once.
   {
-    const int64_t cap4 = std::max<int64_t>(T - 1, 1);
+    // queue halves hold one pair per binary internal node (T - 1); the
+    // 4-wide nodes number at most T (two-level: a root per body, and every
+    // further node consumes a binary node of its body)
+    const int64_t capq = std::max<int64_t>(T - 1, 1);
+    const int64_t cap4 = std::max<int64_t>(T, 1);
     int32_t* qa = s->q4;
-    int32_t* qb = s->q4 + 2 * cap4;
+    int32_t* qb = s->q4 + 2 * capq;
     uint32_t* qlen = reinterpret_cast<uint32_t*>(s->lvl_aux + 8 * kMaxDepth4);  // [kMaxDepth4]
     uint32_t* alloc = qlen + kMaxDepth4;                                         // 4-wide nodes allocated
     const int32_t root[2] = {0, 0};
     const int L = std::max(1, std::min(s->height, kMaxDepth4 - 1));
-    std::vector<uint32_t> h(kMaxDepth4 + 1, 0u);
-    h[0] = 1u;           // depth 0: the root
-    h[kMaxDepth4] = 1u;  // the root is allocated
-    if (int e = cuda_check(cudaMemcpyAsync(qa, root, sizeof(root), cudaMemcpyHostToDevice, st), "copy")) return e;
+    // h[d]: 4-wide nodes at depth d; h[kMaxDepth4]: nodes allocated;
+    // h[kMaxDepth4 + 1]: depth-0 nodes (the roots)
+    std::vector<uint32_t> h(kMaxDepth4 + 2, 0u);
+    if (!s->two_level) {
+      h[0] = 1u;               // depth 0: the root
+      h[kMaxDepth4] = 1u;      // the root is allocated
+      h[kMaxDepth4 + 1] = 1u;
+      if (int e = cuda_check(cudaMemcpyAsync(qa, root, sizeof(root), cudaMemcpyHostToDevice, st), "copy")) return e;
+    }
     if (int e = cuda_check(cudaMemcpyAsync(qlen, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, st), "copy"))
       return e;
     if (int e = cuda_check(cudaMemsetAsync(s->leaf_slot4, 0xff, 4 * T, st), "memset")) return e;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(cap4, 256), (int64_t)sm_count() * 8));
+    if (s->two_level) {
+      // every body's subtree root starts a bottom level (key prefix above bit 3m)
+      int prefix_bits = 0;
+      while (s->nbody > 1 && (1 << prefix_bits) < s->nbody) ++prefix_bits;
+      const int shift = 3 * std::min(21, (63 - prefix_bits) / 3);
+      if (s->nbody > kMaxTlasBodies) return set_error(FIRE_ERR_INVALID_ARG, "two-level mode: too many bodies");
+      if (int e = cuda_check(cudaMemsetAsync(s->body_range, 0xff, 8 * (size_t)s->nbody, st), "memset")) return e;
+      k_body_ranges<<<grid_for(T, 256), 256, 0, st>>>(s->keys, T, prefix_bits > 0 ? shift : 63, s->nbody,
+                                                       s->body_range, s->ctrl + 8);
+      k_body_roots<<<1, 1024, 0, st>>>(s->keys, T, s->body_range, s->nbody, s->leaf_slot, s->blas_root, qa, qlen,
+                                       s->nodes4, s->leaf_slot4);
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(capq, 256), (int64_t)sm_count() * 8));
     for (int d = 0; d < L; ++d) {
       k_collapse<<<grid, 256, 0, st>>>(s->nodes, qa, qlen + d, qb, qlen + d + 1, alloc, s->nodes4, cap4,
                                        s->leaf_slot4, T);
@@ -741,6 +1199,7 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
       return e;
     if (int e = cuda_check(cudaStreamSynchronize(st), "collapse")) return e;
     if (h[L] != 0u) return set_error(FIRE_ERR_CUDA, "4-wide collapse deeper than supported");
+    h[0] = h[kMaxDepth4 + 1];  // depth 0 also holds the one-triangle bottom levels (not queued)
     s->lvl4.assign(1, 0);
     for (int d = 0; d < L && h[d] > 0; ++d) s->lvl4.push_back(std::min<int64_t>(s->lvl4.back() + h[d], cap4));
     s->n4 = s->lvl4.back();
@@ -749,11 +1208,26 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
                            "copy"))
       return e;
     k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
+    if (s->two_level)
+      k_body_boxes<<<grid_for(s->nbody, 256), 256, 0, st>>>(s->nodes4, s->n4, s->blas_root, s->nbody, s->body_box);
     if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
     if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // lvl4 host vector copied
   }
   s->built = true;
   return FIRE_OK;
+}
+
+int tlas_build(fire_scene_s* s, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_tlas, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TlasSmem));
+  });
+  if (int e = cuda_check(attr, "top-level shared memory")) return e;
+  if (s->nbody > kMaxTlasBodies) return set_error(FIRE_ERR_INVALID_ARG, "two-level mode: too many bodies");
+  k_tlas<<<1, 1024, sizeof(TlasSmem), st>>>(s->xf, s->nbody, s->blas_root, s->body_box, s->tlas_buf[s->cur],
+                                            s->tinfo_buf[s->cur], s->xf_buf[s->cur], s->ctrl + 8);
+  return cuda_check(cudaGetLastError(), "k_tlas");
 }
 
 int lbvh_refit(fire_scene_s* s, cudaStream_t st) {

@@ -91,6 +91,7 @@ extern "C" int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec*
   a.row_end = cam->height;
   a.iter_cap = 2 * s->nt + 64;
   set_smooth_args(&a, s);
+  set_level_args(&a, s);
   a.g = const_cast<fire_gbuffer_rec*>(gbuf);
   unsigned char* base = nullptr;
   if (int e = scratch_address(&base)) return e;

@@ -16,10 +16,39 @@
 #include <cstdio>
 #include <mutex>
 
-#include "trace_device.cuh"
+#include "trace2.cuh"
 
 namespace fire {
 namespace {
+
+// Two-level mode: the view of the traversal, and the frame's lift and slack
+// from the top level's record (single level: from the tree's root box).
+__device__ __forceinline__ Trace2View view2(const RenderArgs& a) {
+  const TlasInfo ti = *a.tinfo;
+  return Trace2View{a.tlas, ti.n, a.nodes4, a.n4, a.tris, a.nt, a.blas_root, a.bxf, a.nbody, ti.span,
+                    a.iter_cap, a.ctrl + 8};
+}
+__device__ __forceinline__ float frame_eps(const RenderArgs& a) {
+  return a.tlas ? __ldg(&a.tinfo->eps) : scene_eps(a.nodes4, a.nt);
+}
+
+// Hit frame of the record's triangle (B = e1, C = e2): the single-level
+// world record, or a two-level rest record turned by its body's rotation
+// (body id in C.w).
+__device__ __forceinline__ void hit_frame_of(const RenderArgs& a, float4 B, float4 C, float3 o, float3 d, float t,
+                                             float eps, float3& n, float3& po) {
+  if (a.tlas) {
+    const uint32_t b = __float_as_uint(C.w);
+    float m[12];
+    const bool ok = b < (uint32_t)a.nbody;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m[k] = ok ? __ldg(a.bxf + 12 * b + k) : 0.0f;
+    if (!ok) atomicOr(a.ctrl + 8, kErrCorrupt);
+    hit_frame2(B, C, m, o, d, t, eps, n, po);
+  } else {
+    hit_frame(B, C, o, d, t, eps, n, po);
+  }
+}
 
 // Nearest hit per sample; writes the sample's record (prim, t, cast bits,
 // leaf position) and, for every light with n.l > 0 at the hit, appends a
@@ -29,13 +58,15 @@ namespace {
 // MODE 0: traversal.  After a raster pass (raster.cu): MODE 1 traverses only
 // if that pass fell back, MODE 2 takes each sample's hit from its key
 // otherwise; exactly one of the two does the work.
-template <int STACK, int MODE>
+template <int STACK, int MODE, bool TWO>
 __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
   if (MODE != 0 && (MODE == 1) != (a.ctrl[kCtrlRasterFlag] != 0u)) return;
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;
-  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
-  const float eps = scene_eps(a.nodes4, a.nt);
+  TraceCtx c{a.nodes4, a.n4, TWO ? 0.0f : scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  Trace2View c2{};
+  if (TWO) c2 = view2(a);
+  const float eps = frame_eps(a);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 0, 1);
@@ -57,12 +88,14 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
           t = __uint_as_float((uint32_t)(key >> 32));
           pos = __ldg(a.rank + prim);
         }
+      } else if (TWO) {
+        traverse2<DeviceLoads, STACK, false>(c2, o, d, 0.0f, -1, prim, pos, t);
       } else {
         trace_nearest<STACK>(c, o, d, prim, pos, t);
       }
       if (prim >= 0) {
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
-        hit_frame(B, C, o, d, t, eps, n, po);
+        hit_frame_of(a, B, C, o, d, t, eps, n, po);
         if (a.vnrm)
           n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, pos, __ldg(a.tris + 3 * (int64_t)pos), B,
                              C, o, d, n);
@@ -102,10 +135,12 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
 // sample's record.  (A lane-level ray pool -- refilling idle lanes
 // every 16 node visits -- measured 7% slower: the idle lanes come from the
 // branches inside each node step, not from rays of different lengths.)
-template <int STACK>
+template <int STACK, bool TWO>
 __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs) {
   const int lane = threadIdx.x & 31;
-  TraceCtx c{a.nodes4, a.n4, scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  TraceCtx c{a.nodes4, a.n4, TWO ? 0.0f : scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
+  Trace2View c2{};
+  if (TWO) c2 = view2(a);
   uint32_t cnt[8];
   uint32_t njobs = 0;
   for (int j = 0; j < 8; ++j) {
@@ -133,8 +168,15 @@ __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __re
       int64_t sid = sj >> 3;
       int light = sj & 7;
       int skip = rec[sid].x;
-      if (!trace_any<STACK>(c, f3(A.x, A.y, A.z), f3(B.x, B.y, B.z), A.w, skip))
-        atomicOr(reinterpret_cast<unsigned*>(&rec[sid].z), 1u << light);
+      bool occ;
+      if (TWO) {
+        int prim, pos;
+        float tb;
+        occ = traverse2<DeviceLoads, STACK, true>(c2, f3(A.x, A.y, A.z), f3(B.x, B.y, B.z), A.w, skip, prim, pos, tb);
+      } else {
+        occ = trace_any<STACK>(c, f3(A.x, A.y, A.z), f3(B.x, B.y, B.z), A.w, skip);
+      }
+      if (!occ) atomicOr(reinterpret_cast<unsigned*>(&rec[sid].z), 1u << light);
     }
   }
 }
@@ -168,7 +210,7 @@ __device__ __forceinline__ void resolve_write(const RenderArgs& a, int lane, boo
 // intensities or nullptr (the lights' own).
 __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int ntasks, const float* inten) {
   const int lane = threadIdx.x & 31;
-  const float eps = scene_eps(a.nodes4, a.nt);
+  const float eps = frame_eps(a);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 1, 1);
@@ -190,7 +232,7 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
         float3 d = cam_dir(a.cam, x, y, k);
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);
         float3 n, po;
-        hit_frame(B, C, o, d, t, eps, n, po);
+        hit_frame_of(a, B, C, o, d, t, eps, n, po);
         if (a.vnrm)
           n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, pos, __ldg(a.tris + 3 * (int64_t)pos), B,
                              C, o, d, n);
@@ -240,7 +282,7 @@ __global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, 
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const float eps = scene_eps(a.nodes4, a.nt);
+  const float eps = frame_eps(a);
   while (true) {
     int task = 0;
     if (lane == 0) task = atomicAdd(a.ctrl + 2, 1);
@@ -264,7 +306,7 @@ __global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, 
         float3 d = cam_dir(a.cam, x, y, k);
         float4 B = __ldg(a.tris + 3 * (int64_t)rr.w + 1), C = __ldg(a.tris + 3 * (int64_t)rr.w + 2);
         float3 n, po;
-        hit_frame(B, C, o, d, __int_as_float(rr.y), eps, n, po);
+        hit_frame_of(a, B, C, o, d, __int_as_float(rr.y), eps, n, po);
         if (a.vnrm)
           n = shading_normal(SmoothCtx{a.vnrm, a.bxf, a.sidx, a.vbody}, rr.w, __ldg(a.tris + 3 * (int64_t)rr.w), B,
                              C, o, d, n);
@@ -366,15 +408,15 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
   return n;
 }
 
-template <int STACK>
+template <int STACK, bool TWO>
 int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int ntasks,
                   const fire_render_opts& o, bool raster, cudaStream_t st) {
   const int threads = 128;
   static int occ_p = 0, occ_s = 0, occ_r = 0;
   static std::once_flag once;
   std::call_once(once, [] {
-    occ_p = occupancy_blocks(k_primary<STACK, 0>, 128, 0);
-    occ_s = occupancy_blocks(k_shadow<STACK>, 128, 0);
+    occ_p = occupancy_blocks(k_primary<STACK, 0, TWO>, 128, 0);
+    occ_s = occupancy_blocks(k_shadow<STACK, TWO>, 128, 0);
     occ_r = occupancy_blocks(k_shade, 128, 0);
   });
   int sms = sm_count();
@@ -400,15 +442,15 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
     RenderArgs ak = a;
     ak.rkeys = s->rkeys;
     ak.rank = s->rank;
-    k_primary<STACK, 1><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
-    k_primary<STACK, 2><<<gp, threads, 0, st>>>(ak, g, ntasks, s->jobs);
+    k_primary<STACK, 1, false><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
+    k_primary<STACK, 2, false><<<gp, threads, 0, st>>>(ak, g, ntasks, s->jobs);
   } else {
-    k_primary<STACK, 0><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
+    k_primary<STACK, 0, TWO><<<gp, threads, 0, st>>>(a, g, ntasks, s->jobs);
   }
   prof_end(s, kStagePrimary, st, raster ? (a.nt > 0 ? 6 : 3) : 1);
   if (a.lights.n > 0) {
     prof_begin(s, kStageShadow, st);
-    k_shadow<STACK><<<gs, threads, 0, st>>>(a, s->jobs);
+    k_shadow<STACK, TWO><<<gs, threads, 0, st>>>(a, s->jobs);
     prof_end(s, kStageShadow, st);
   }
   prof_begin(s, kStageResolve, st);
@@ -442,11 +484,19 @@ int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o
   raster = raster && s->rkeys && s->pieces && s->graze && a.cam.W < 65536 && a.cam.H < 65536;
   s->rendered = true;
   s->last_raster = raster;
+  if (a.tlas) {  // two-level (no raster pass: fire_render refuses the flag)
+    switch (stack_for_height(stack_need(s), o.stack_depth)) {
+      case 8: return launch_render<8, true>(s, a, g, ntasks, o, false, st);
+      case 32: return launch_render<32, true>(s, a, g, ntasks, o, false, st);
+      case 64: return launch_render<64, true>(s, a, g, ntasks, o, false, st);
+      default: return launch_render<128, true>(s, a, g, ntasks, o, false, st);
+    }
+  }
   switch (stack_for_height(stack_need(s), o.stack_depth)) {
-    case 8: return launch_render<8>(s, a, g, ntasks, o, raster, st);
-    case 32: return launch_render<32>(s, a, g, ntasks, o, raster, st);
-    case 64: return launch_render<64>(s, a, g, ntasks, o, raster, st);
-    default: return launch_render<128>(s, a, g, ntasks, o, raster, st);
+    case 8: return launch_render<8, false>(s, a, g, ntasks, o, raster, st);
+    case 32: return launch_render<32, false>(s, a, g, ntasks, o, raster, st);
+    case 64: return launch_render<64, false>(s, a, g, ntasks, o, raster, st);
+    default: return launch_render<128, false>(s, a, g, ntasks, o, raster, st);
   }
 }
 

@@ -18,7 +18,7 @@ constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kBoxSlack = 1.0f + 1.0f / 65536.0f;
 constexpr uint32_t kFull = 0xffffffffu;
 
-__device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
+__host__ __device__ __forceinline__ float inf_f() { return bits_as_float(0x7f800000u); }
 
 // ---------------------------------------------------------------------------
 // Camera: sample k of pixel (x, y):
@@ -50,8 +50,15 @@ __device__ __forceinline__ float3 cam_dir(const CamParams& c, int x, int y, int 
 
 // Reciprocal direction for the slab test; components below 1e-30 in
 // magnitude become +-1e30 so that no 0 * inf appears.
-__device__ __forceinline__ float safe_rcp(float d) {
-  return fabsf(d) < 1e-30f ? (d >= 0.0f ? 1e30f : -1e30f) : __frcp_rn(d);
+__host__ __device__ __forceinline__ float rcp_rn(float d) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(d);
+#else
+  return 1.0f / d;  // IEEE division: the correctly rounded reciprocal, as __frcp_rn
+#endif
+}
+__host__ __device__ __forceinline__ float safe_rcp(float d) {
+  return fabsf(d) < 1e-30f ? (d >= 0.0f ? 1e30f : -1e30f) : rcp_rn(d);
 }
 
 // Conservative slab test of the box [lo, hi] against [0, tmax]; returns the
@@ -74,12 +81,12 @@ __device__ __forceinline__ bool slab(float3 o, float3 inv, float lox, float loy,
 //   fl(u + v) <= 1.  (u > 1 is rejected early: with v >= 0 it implies
 //   fl(u + v) > 1, so the decision is the same.)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool mt_t(float3 o, float3 d, float4 A, float4 B, float4 C, float& t) {
+__host__ __device__ __forceinline__ bool mt_t(float3 o, float3 d, float4 A, float4 B, float4 C, float& t) {
   float3 v0 = xyz(A), e1 = xyz(B), e2 = xyz(C);
   float3 p = cross3(d, e2);
   float det = dot3(e1, p);
   if (det == 0.0f) return false;
-  float inv = __frcp_rn(det);
+  float inv = rcp_rn(det);
   float3 s = sub3(o, v0);
   float u = dot3(s, p) * inv;
   if (!(u >= 0.0f && u <= 1.0f)) return false;
@@ -123,16 +130,25 @@ __device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o,
   return false;
 }
 
-// Three-input min / max (one instruction each on sm_100-class GPUs).
-__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+// Three-input min / max (one instruction each on sm_100-class GPUs; two
+// calls on the host).
+__host__ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
   float r;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
+#else
+  return fmaxf(fmaxf(a, b), c);
+#endif
 }
-__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+__host__ __device__ __forceinline__ float fmin3f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
   float r;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
+#else
+  return fminf(fminf(a, b), c);
+#endif
 }
 
 // Per-ray data of the 4-wide box test: for each axis the member (0..5 =
@@ -152,7 +168,7 @@ struct RaySetup {
   int nx, ny, nz, fx, fy, fz;
 };
 
-__device__ __forceinline__ RaySetup ray_setup(float3 o, float3 d, float span) {
+__host__ __device__ __forceinline__ RaySetup ray_setup(float3 o, float3 d, float span) {
   RaySetup r;
   r.inv = f3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
   const float k = 1.0f / 524288.0f;  // 2^-19
@@ -177,7 +193,7 @@ __device__ __forceinline__ RaySetup ray_setup(float3 o, float3 d, float span) {
 
 // Entry/exit test of one child against [0, tmax].  Unused slots hold the
 // inverted infinite box (lo = +inf, hi = -inf): entry +inf, exit -inf, never hit.
-__device__ __forceinline__ bool slab4(const RaySetup& r, float nx, float ny, float nz, float fx, float fy, float fz,
+__host__ __device__ __forceinline__ bool slab4(const RaySetup& r, float nx, float ny, float nz, float fx, float fy, float fz,
                                       float tmax, float& tnear) {
   float tnx = fmaf(nx, r.inv.x, r.cnx), tny = fmaf(ny, r.inv.y, r.cny), tnz = fmaf(nz, r.inv.z, r.cnz);
   float tfx = fmaf(fx, r.inv.x, r.cfx), tfy = fmaf(fy, r.inv.y, r.cfy), tfz = fmaf(fz, r.inv.z, r.cfz);
@@ -187,7 +203,7 @@ __device__ __forceinline__ bool slab4(const RaySetup& r, float nx, float ny, flo
   return tn <= tf;
 }
 
-__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
+__host__ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
   const bool s = kb < ka;
   const float tk = s ? kb : ka;
   kb = s ? ka : kb;

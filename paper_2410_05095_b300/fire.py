@@ -20,7 +20,7 @@ ERRORS = {-1: "FIRE_ERR_INVALID_ARG", -2: "FIRE_ERR_OOM", -3: "FIRE_ERR_CUDA",
           -4: "FIRE_ERR_STACK_OVERFLOW", -5: "FIRE_ERR_TIMEOUT", -6: "FIRE_ERR_NOT_BUILT"}
 
 DUMP = {"morton": 0, "order": 1, "children": 2, "parent": 3, "boxes": 4, "tris": 5,
-        "centroid_bounds": 6}
+        "centroid_bounds": 6, "nodes4": 7, "blas_root": 8, "tlas": 9, "tlas_info": 10, "body_xforms": 11}
 
 EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials", "fire_scene_info",
            "fire_bvh_build", "fire_bvh_refit", "fire_render", "fire_render_batch", "fire_shade",
@@ -28,7 +28,7 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
            "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_probe_read",
-           "fire_last_error", "fire_version"]
+           "fire_scene_set_two_level", "fire_debug_trace_host", "fire_last_error", "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -94,6 +94,8 @@ def lib():
             "fire_scene_set_materials_ex": [P, P, i32, i32],
             "fire_scene_set_normals": [P, P, i32, P],
             "fire_probe_read": [P, i64, i32, P, i32, P],
+            "fire_scene_set_two_level": [P, i32],
+            "fire_debug_trace_host": [P, P, P, P, P, i64, i32, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -275,12 +277,35 @@ class Scene:
                                                  len(lights), _ptr(params), _ptr(inten), _ptr(dL),
                                                  _ptr(dparams), _ptr(dinten), _stream(stream)))
 
+    def set_two_level(self, enable: bool = True):
+        """Two-level acceleration structure (bottom level per body at rest,
+        top level rebuilt every frame); takes effect at the next build."""
+        _check(lib().fire_scene_set_two_level(self.h, int(bool(enable))))
+
+    def trace_host(self, o, d, tmax=None, skip=None, any_hit=False):
+        """Host emulation of the two-level traversal (fire_debug_trace_host):
+        returns (prim, t, hit, error bits) for rays o, d [n, 3]."""
+        o = np.ascontiguousarray(o, np.float32)
+        d = np.ascontiguousarray(d, np.float32)
+        n = len(o)
+        prim, t = np.zeros(n, np.int32), np.zeros(n, np.float32)
+        hit = np.zeros(n, np.uint8)
+        err = C.c_uint32(0)
+        tm = None if tmax is None else np.ascontiguousarray(tmax, np.float32)
+        sk = None if skip is None else np.ascontiguousarray(skip, np.int32)
+        _check(lib().fire_debug_trace_host(self.h, _ptr(o), _ptr(d), _ptr(tm), _ptr(sk), n, int(bool(any_hit)),
+                                           _ptr(prim), _ptr(t), _ptr(hit), C.byref(err)))
+        return prim, t, hit.astype(bool), int(err.value)
+
     def dump(self, what: str) -> np.ndarray:
         T = self.nt
+        nb = self.nbody
         shapes = {"morton": (np.uint64, (T,)), "order": (np.uint32, (T,)),
                   "children": (np.int32, (max(T - 1, 0), 2)), "parent": (np.int32, (max(2 * T - 1, 0),)),
                   "boxes": (np.float32, (max(2 * T - 1, 0), 6)), "tris": (np.float32, (T, 12)),
-                  "centroid_bounds": (np.float32, (6,))}
+                  "centroid_bounds": (np.float32, (6,)), "nodes4": (np.float32, (self.info()["n4"], 32)),
+                  "blas_root": (np.int32, (nb,)), "tlas": (np.float32, (nb + 2, 32)),
+                  "tlas_info": (np.float32, (4,)), "body_xforms": (np.float32, (nb, 12))}
         dt, shp = shapes[what]
         out = np.zeros(shp, dt)
         _check(lib().fire_debug_dump(self.h, DUMP[what], _ptr(out), out.nbytes))

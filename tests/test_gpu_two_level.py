@@ -1,0 +1,244 @@
+"""The two-level acceleration structure on the GPU (fire_scene_set_two_level:
+a bottom level per rigid body built once over the rest pose, a top level
+over the bodies rebuilt every frame, §IV-B-3) against the oracle's
+two-level mode (bodies as instances of rest-space geometry, rays met in
+each body's frame).
+
+Order matters in this file: the first tests build the structure on the GPU
+and run the traversal code on the host (fire_debug_trace_host: every load
+checked against the copied arrays' bounds and alignment) before any test
+launches the two-level render kernels; run with -x, a failure there stops
+the file before the device traversal runs."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from gpu_common import (THREADS, TIE_REL, assert_radiance_close, compare_samples, gbuf_of, pixel_ok_mask,
+                        torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fb():
+    import paper_2410_05095_b300 as fb
+    torch_cuda()
+    return fb
+
+
+def _moving(nspheres=120, cells=64, frames=4):
+    w = sg.workload_frame7m(nspheres=nspheres, cells=cells)
+    poses = [w.motion.step() for _ in range(frames)]
+    return w, poses
+
+
+def _pair2(fb, sc, xf):
+    G = fb.Scene.from_numpy(sc)
+    G.set_two_level(True)
+    G.build(xf)
+    S = oracle.OracleScene(sc)
+    S.set_two_level(True)
+    S.update(xf, rebuild=True)
+    return G, S
+
+
+def _camera_rays(cam):
+    n = cam.width * cam.height * cam.spp
+    o = np.zeros((n, 3), np.float32)
+    d = np.zeros((n, 3), np.float32)
+    for i in range(n):
+        k, p = i % cam.spp, i // cam.spp
+        o[i], d[i] = oracle.camera_ray(cam, p % cam.width, p // cam.width, k)
+    return o, d
+
+
+def _segments(rng, n, lo, hi):
+    o = rng.uniform(lo, hi, (n, 3)).astype(np.float32)
+    e = rng.uniform(lo, hi, (n, 3)).astype(np.float32)
+    v = e - o
+    L = np.linalg.norm(v, axis=1).astype(np.float32)
+    d = (v / L[:, None]).astype(np.float32)
+    return o, d, L
+
+
+# ------------------------------------------------------------- host emulation first
+def test_emulated_traversal_matches_oracle(fb):
+    """Built on the GPU (bottom levels at rest, top level for frame 3's
+    poses), walked on the host by the render kernels' traversal code: every
+    load in bounds and aligned, no error bit, nearest hits equal to the
+    oracle's (up to near ties), any-hit answers equal."""
+    w, poses = _moving()
+    G, S = _pair2(fb, w.scene, poses[0])
+    for xf in poses[1:]:
+        G.refit(xf)
+        S.update(xf, rebuild=False)
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 96, 54, 4)
+    o, d = _camera_rays(cam)
+    prim, t, _, err = G.trace_host(o, d)
+    assert err == 0, hex(err)
+    rp, rt, _, _, rt2 = S.trace(o, d, want_t2=True)
+    bad = (prim != rp) | ((prim >= 0) & (t != rt))
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))
+    assert bad.mean() <= 1e-4 and not (bad & ~tie).any(), int(bad.sum())
+    assert (rp >= 0).mean() > 0.2
+    # any hit: segments across the scene, with and without a skipped triangle
+    rng = np.random.default_rng(5)
+    so, sd, sl = _segments(rng, 6000, [-12, -3, -12], [12, 5, 12])
+    skip = np.where(rng.uniform(size=6000) < 0.5, rng.integers(0, w.scene.nt, 6000), -1).astype(np.int32)
+    _, _, hit, err = G.trace_host(so, sd, tmax=sl, skip=skip, any_hit=True)
+    assert err == 0, hex(err)
+    ref = S.occluded(so, sd, sl, skip)
+    assert np.array_equal(hit, ref), int((hit != ref).sum())
+    assert 0.1 < ref.mean() < 0.95
+
+
+def test_emulated_degenerate_bodies(fb):
+    """Bodies of one triangle, bodies without triangles, and a scene whose
+    triangles are all in one body: the host walk stays in bounds and
+    matches the oracle."""
+    rng = sg.Rng(17)
+    tris, vb = [], []
+    for b in range(9):
+        if b in (2, 5):
+            continue  # bodies without triangles
+        n = 1 if b in (0, 7) else 40
+        for _ in range(n):
+            c = np.array([rng.uniform(-3, 3), rng.uniform(-1, 1), rng.uniform(-3, 3)])
+            tris.append(np.stack([c, c + [0.3, 0.0, 0.1], c + [0.0, 0.25, 0.2]]))
+            vb += [b] * 3
+    from test_oracle_lbvh import _scene_from_tris
+    for nbody, vbody in ((9, np.array(vb, np.uint16)), (1, np.zeros(len(vb), np.uint16))):
+        sc = _scene_from_tris(np.array(tris), nbody=nbody, vbody=vbody)
+        xf = np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (nbody, 1))
+        xf[:, 3] += np.linspace(0, 0.5, nbody, dtype=np.float32)
+        G, S = _pair2(fb, sc, xf)
+        rr = np.random.default_rng(nbody)
+        o, d, L = _segments(rr, 3000, [-4, -2, -4], [4, 2, 4])
+        prim, t, _, err = G.trace_host(o, d)
+        assert err == 0
+        rp, rt, _, _ = S.trace(o, d)
+        assert np.array_equal(prim, rp) and np.array_equal(t[rp >= 0], rt[rp >= 0])
+        _, _, hit, err = G.trace_host(o, d, tmax=L, any_hit=True)
+        assert err == 0 and np.array_equal(hit, S.occluded(o, d, L))
+
+
+# --------------------------------------------------------------- device kernels
+def _render(fb, G, cam, lights, **opts):
+    torch = torch_cuda()
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    out = torch.zeros((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
+    G.render(cam, lights, out=out, gbuf=gb, opts=fb.fire.make_opts(**opts) if opts else None)
+    assert G.sync_status() == 0
+    return out.cpu().numpy(), gbuf_of(gb)
+
+
+def test_two_level_render_matches_oracle(fb):
+    """Frames 1-3 of the moving workload (reduced), 4 spp, two point lights:
+    hits and visibility by the agreement rule, radiance within 1e-4."""
+    w, poses = _moving()
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 192, 108, 4)
+    G, S = _pair2(fb, w.scene, poses[0])
+    for xf in poses[1:]:
+        G.refit(xf)
+        S.update(xf, rebuild=False)
+        img, g = _render(fb, G, cam, w.lights)
+        ref = S.render_all_samples(cam, w.lights, threads=THREADS)
+        _, bad = compare_samples(g, ref)
+        img_ref = S.render_image(cam, w.lights, threads=THREADS)
+        assert_radiance_close(img, img_ref, pixel_ok_mask(bad, cam.width, cam.height, 4))
+    assert (ref["prim"] >= 0).mean() > 0.2 and ((ref["vis"] >> 8) & ~ref["vis"] & 3).any()
+
+
+def test_two_level_single_body_and_directional_light(fb):
+    """A static single-body scene (tiny41k) in two-level mode with a point
+    and a directional light, ragged 4-spp image."""
+    w = sg.workload_tiny41k()
+    lights = [sg.LIGHTS_MAIN[0], sg.LIGHTS_MAIN[2]]
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 77, 45, 4)
+    xf = w.scene.identity_xforms()
+    G, S = _pair2(fb, w.scene, xf)
+    img, g = _render(fb, G, cam, lights)
+    ref = S.render_all_samples(cam, lights)
+    _, bad = compare_samples(g, ref)
+    assert_radiance_close(img, S.render_image(cam, lights), pixel_ok_mask(bad, cam.width, cam.height, 4))
+
+
+def test_two_level_pipelined_frames_and_shading(fb):
+    """Top levels rebuilt on their own stream into the second frame buffer
+    while the previous frame renders: frames 2 and 4 against the oracle; the
+    G-buffer shading and its backward run on the two-level hit frame."""
+    torch = torch_cuda()
+    w, poses = _moving(frames=4)
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 160, 90, 4)
+    G = fb.Scene.from_numpy(w.scene)
+    G.set_two_level(True)
+    G.build(poses[0])
+    n = cam.width * cam.height * cam.spp
+    gbs = [torch.zeros((n, 4), dtype=torch.int32, device="cuda") for _ in poses]
+    outs = [torch.zeros((cam.height, cam.width, 4), device="cuda") for _ in poses]
+    side = torch.cuda.Stream(priority=-1)
+    dev = [torch.from_numpy(x).cuda() for x in poses]
+    torch.cuda.synchronize()
+    for i in range(1, len(poses)):
+        G.refit(dev[i], stream=side)
+        G.render(cam, w.lights, out=outs[i], gbuf=gbs[i], opts=fb.fire.make_opts(blocks_per_sm=6))
+    torch.cuda.synchronize()
+    assert G.sync_status() == 0
+    S = oracle.OracleScene(w.scene)
+    S.set_two_level(True)
+    S.update(poses[0], rebuild=True)
+    for i in range(1, len(poses)):
+        S.update(poses[i], rebuild=False)
+        if i % 2:
+            continue
+        ref = S.render_all_samples(cam, w.lights, threads=THREADS)
+        _, bad = compare_samples(gbuf_of(gbs[i]), ref)
+        assert_radiance_close(outs[i].cpu().numpy(), S.render_image(cam, w.lights, threads=THREADS),
+                              pixel_ok_mask(bad, cam.width, cam.height, 4))
+    # shading of the last G-buffer with the scene's own parameters = the render
+    params = torch.from_numpy(oracle.params_of(w.scene.mats).astype(np.float32)).cuda()
+    inten = torch.tensor([l.intensity for l in w.lights], dtype=torch.float32, device="cuda")
+    img2 = G.shade(gbs[-1], cam, w.lights, params, inten)
+    assert torch.equal(img2, outs[-1])
+    dP, dI = torch.zeros_like(params), torch.zeros_like(inten)
+    G.shade_backward(gbs[-1], cam, w.lights, params, inten, torch.ones_like(img2), dP, dI)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(dP).all()) and float(dI.abs().sum()) > 0
+
+
+def test_two_level_error_paths(fb):
+    torch = torch_cuda()
+    w = sg.workload_tiny41k(32, 32)
+    G = fb.Scene.from_numpy(w.scene)
+    G.build(w.scene.identity_xforms())
+    G.set_two_level(True)
+    with pytest.raises(fb.FireError) as e:
+        G.render(w.camera, w.lights)
+    assert e.value.code == -6                          # mode change leaves the scene unbuilt
+    G.build(w.scene.identity_xforms())
+    with pytest.raises(fb.FireError) as e:
+        G.render(w.camera, w.lights, opts=fb.fire.make_opts(flags=4))
+    assert e.value.code == -1                          # no raster pass in two-level mode
+    out = torch.zeros((32, 32, 4), device="cuda")
+    with pytest.raises(fb.FireError) as e:
+        fb.render_batch([G], [w.camera], [0], [w.lights], [out])
+    assert e.value.code == -1                          # no batch in two-level mode
+    with pytest.raises(fb.FireError) as e:
+        G.set_normals(sg.vertex_normals(w.scene))
+        G.render(w.camera, w.lights)
+    assert e.value.code == -1                          # no smooth normals in two-level mode
+    G.set_normals(None)
+    G.set_two_level(False)
+    G.build(w.scene.identity_xforms())
+    G.render(w.camera, w.lights)
+    # a triangle across two bodies cannot be an instance's
+    sc = sg.assemble([(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.0]]), np.array([[0, 1, 2]]))], 1,
+                     sg.random_materials(sg.Rng(3), 1))
+    sc.vert_body[:] = [0, 1, 0]
+    sc.nbody = 2
+    G2 = fb.Scene.from_numpy(sc)
+    with pytest.raises(fb.FireError) as e:
+        G2.set_two_level(True)
+    assert e.value.code == -1
