@@ -142,12 +142,18 @@ Box box_union(const Box& a, const Box& b) {
 //   q_a = min(floor((c_a - lo_a) * s_a), 2^m - 1), s_a = 2^m / (hi_a - lo_a)
 //   (0 if hi_a == lo_a); bit k of q_x -> bit 3k+2, of q_y -> 3k+1, of q_z -> 3k.
 // Written as a plain per-bit loop.
-// Body prefix (scenes of several rigid bodies, §IV-C: each body moves as a
-// whole): key = body << 3m | code, with the body of the triangle's first
-// vertex, B = bits of (nbody - 1) and m = min(21, (63 - B) / 3); so all of a
-// body's triangles are consecutive in the sorted order and form one subtree
-// of the radix tree, like the paper's per-mesh bottom levels under a top
-// level (§IV-B-3).  One body: B = 0, m = 21.
+// Body field (scenes of several rigid bodies, §IV-C: each body moves as a
+// whole), with B = bits of (nbody - 1), m = min(21, (63 - B) / 3) and the
+// body of the triangle's first vertex:
+//   key = coarse << (B + 3(m-c)) | body << 3(m-c) | fine
+// where coarse = the code's top 3c bits (the top c bits of each q_a) and fine
+// = its low 3(m-c) bits.  Inside each coarse cell (1/2^c of the bounds per
+// axis) a body's triangles are consecutive in the sorted order and form one
+// subtree, so only the nodes of the coarse levels mix bodies, like the
+// paper's per-mesh bottom levels under a top level (§IV-B-3).  c = 4 for the
+// single-level tree; c = 0 (the body above everything: one subtree per body)
+// for the bottom levels of the two-level mode.  One body: B = 0, m = 21, and
+// the key is the plain Morton code.
 // ---------------------------------------------------------------------------
 uint32_t quantise(float c, float lo, float s, uint32_t qmax) {
   float f = (c - lo) * s;
@@ -166,11 +172,19 @@ uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz, int m) {
   return code;
 }
 
-// Bits of the body prefix and Morton bits per axis for a scene of nbody bodies.
+// Bits of the body field and Morton bits per axis for a scene of nbody bodies.
 void key_layout(int32_t nbody, int& B, int& m) {
   B = 0;
   while (nbody > 1 && (1 << B) < nbody) ++B;
   m = std::min(21, (63 - B) / 3);
+}
+
+constexpr int kCoarseBits = 4;  // c of the single-level tree
+
+uint64_t body_key(uint64_t code, uint64_t body, int B, int m, int c) {
+  const int fine = 3 * (m - c);
+  const uint64_t low = fine > 0 ? code & ((1ull << fine) - 1) : 0;
+  return ((code >> fine) << (B + fine)) | (body << fine) | low;
 }
 
 int clz64(uint64_t x) { int n = 0; for (int b = 63; b >= 0 && !((x >> b) & 1u); --b) ++n; return n; }
@@ -252,9 +266,10 @@ void build(orc_scene& S) {
   }
   for (int64_t t = 0; t < T; ++t) {
     const uint64_t body = B > 0 ? (uint64_t)S.vbody[S.idx[3 * t]] : 0u;
-    S.morton[t] = (body << (3 * m)) |
-                  interleave(quantise(cen[3 * t], lo[0], s[0], qmax), quantise(cen[3 * t + 1], lo[1], s[1], qmax),
-                             quantise(cen[3 * t + 2], lo[2], s[2], qmax), m);
+    const uint64_t code =
+        interleave(quantise(cen[3 * t], lo[0], s[0], qmax), quantise(cen[3 * t + 1], lo[1], s[1], qmax),
+                   quantise(cen[3 * t + 2], lo[2], s[2], qmax), m);
+    S.morton[t] = B > 0 ? body_key(code, body, B, m, kCoarseBits) : code;
   }
   std::iota(S.order.begin(), S.order.end(), 0u);
   std::stable_sort(S.order.begin(), S.order.end(),

@@ -29,25 +29,32 @@ def brdf_rows():
 
 
 def body_key_rows():
-    """Body-prefixed Morton keys of centroids at lo / mid / hi of the bounds
-    [0, 8]^3 (§IV-C rigid bodies; the LBVH key layout of the acceleration
-    structure): B = bits of (nbody - 1), m = min(21, (63 - B) // 3) bits per
-    axis; per axis q = 0 at lo, 2^(m-1) at mid ((c - lo) 2^m / (hi - lo) is
-    exactly 2^(m-1)), 2^m - 1 at hi (clamped); x -> bit 3k+2, y -> 3k+1,
-    z -> 3k; key = body << 3m | code."""
+    """Morton keys with a body field, of centroids at lo / mid / hi of the
+    bounds [0, 8]^3 (§IV-C rigid bodies; the LBVH key layout of the
+    acceleration structure): B = bits of (nbody - 1), m = min(21, (63 - B)
+    // 3) bits per axis; per axis q = 0 at lo, 2^(m-1) at mid ((c - lo) 2^m /
+    (hi - lo) is exactly 2^(m-1)), 2^m - 1 at hi (clamped); x -> bit 3k+2,
+    y -> 3k+1, z -> 3k; the top c = 4 bits of each q (coarse) above the body,
+    the rest (fine) below it:
+      key = coarse << (B + 3(m-4)) | body << 3(m-4) | fine."""
     rows = []
+    c = 4
     for nbody in (2, 3, 65):
         B = (nbody - 1).bit_length()
         m = min(21, (63 - B) // 3)
         q = {"lo": 0, "mid": 1 << (m - 1), "hi": (1 << m) - 1}
         for body, pt in ((0, ("hi", "hi", "hi")), (nbody - 1, ("lo", "lo", "lo")), (nbody - 1, ("hi", "mid", "lo")),
                          (nbody // 2, ("mid", "mid", "mid")), (1, ("lo", "hi", "mid"))):
-            code = 0
+            coarse = fine = 0
             for k in range(m):
-                code |= ((q[pt[0]] >> k) & 1) << (3 * k + 2)
-                code |= ((q[pt[1]] >> k) & 1) << (3 * k + 1)
-                code |= ((q[pt[2]] >> k) & 1) << (3 * k)
-            rows.append((nbody, body, pt, (body << (3 * m)) | code))
+                bits = [(q[pt[a]] >> k) & 1 for a in range(3)]  # x, y, z
+                for a in range(3):
+                    if k >= m - c:
+                        coarse |= bits[a] << (3 * (k - (m - c)) + 2 - a)
+                    else:
+                        fine |= bits[a] << (3 * k + 2 - a)
+            f = 3 * (m - c)
+            rows.append((nbody, body, pt, (coarse << (B + f)) | (body << f) | fine))
     return rows
 
 
@@ -59,8 +66,9 @@ def main():
         for row in brdf_rows():
             f.write(" ".join(repr(float(x)) for x in row) + "\n")
     with open(os.path.join(HERE, "morton_body_prefix.txt"), "w") as f:
-        f.write("# Body-prefixed Morton keys: B = bits of (nbody-1), m = min(21, (63-B)//3) bits per axis,\n")
-        f.write("# key = body << 3m | interleave(q) (x -> 3k+2, y -> 3k+1, z -> 3k); centroid bounds [0,8]^3,\n")
+        f.write("# Morton keys with a body field: B = bits of (nbody-1), m = min(21, (63-B)//3) bits per axis,\n")
+        f.write("# key = coarse << (B + 3(m-4)) | body << 3(m-4) | fine, coarse/fine = the top 4 / the other\n")
+        f.write("# bits of each axis, interleaved (x -> 3k+2, y -> 3k+1, z -> 3k); centroid bounds [0,8]^3,\n")
         f.write("# q = 0 at lo, 2^(m-1) at mid, 2^m - 1 at hi.  (Written by make_golden.py.)\n")
         f.write("# nbody body x y z key\n")
         for nbody, body, pt, key in body_key_rows():

@@ -69,18 +69,30 @@ def test_morton_body_prefix_hand_codes():
         assert list(S.get("centroid_bounds")) == [0, 0, 0, 8, 8, 8]
         for i, (_, _, want) in enumerate(cases):
             assert int(codes[2 + i]) == want, (nbody, i, hex(int(codes[2 + i])), hex(want))
-    # a triangle whose vertices belong to different bodies takes its first vertex's
+    # a triangle whose vertices belong to different bodies takes its first
+    # vertex's (nbody 3: B = 2, m = 20, the body field at bits 48..49)
     tris = [_point_tri([0, 0, 0]), _point_tri([8, 8, 8]), _point_tri([8, 8, 8])]
     vb = np.array([0, 0, 0, 1, 1, 1, 2, 0, 1], np.uint16)
     S = oracle.OracleScene(_scene_from_tris(np.array(tris), nbody=3, vbody=vb))
     S.update(np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (3, 1)), rebuild=True)
-    assert [int(c) >> 60 for c in S.get("morton")] == [0, 1, 2]
+    assert [(int(c) >> 48) & 3 for c in S.get("morton")] == [0, 1, 2]
 
 
-def test_each_body_is_one_subtree():
-    """With body-prefixed keys every body's triangles are consecutive in the
-    sorted order and are exactly the leaves of one node of the radix tree
-    (checked on a soup of interleaved bodies whose boxes overlap)."""
+def _split_key(key: int, B: int, m: int, c: int = 4):
+    """(coarse cell, body, plain m-bit Morton code) of a key with a body field."""
+    f = 3 * (m - c)
+    fine = key & ((1 << f) - 1)
+    body = (key >> f) & ((1 << B) - 1)
+    coarse = key >> (B + f)
+    return coarse, body, (coarse << f) | fine
+
+
+def test_each_body_is_one_subtree_per_coarse_cell():
+    """With a body field below the coarse cell bits, the triangles of one
+    body inside one coarse cell (1/16 of the bounds per axis) are
+    consecutive in the sorted order and are exactly the leaves of one node
+    of the radix tree (checked on a soup of interleaved bodies whose boxes
+    overlap); cells come in Morton order, bodies in id order inside a cell."""
     rng = sg.Rng(321)
     nbody, n = 7, 700
     tris = []
@@ -91,9 +103,12 @@ def test_each_body_is_one_subtree():
     vb = np.repeat(body_of_tri, 3).astype(np.uint16)
     S = oracle.OracleScene(_scene_from_tris(np.array(tris), nbody=nbody, vbody=vb))
     S.update(np.tile(np.eye(3, 4, dtype=np.float32).reshape(1, 12), (nbody, 1)), rebuild=True)
-    order, children = S.get("order"), S.get("children")
-    sorted_body = body_of_tri[order]
-    assert np.all(np.diff(sorted_body) >= 0)  # bodies in id order, each consecutive
+    order, children, keys = S.get("order"), S.get("children"), S.get("morton")
+    B, m = 3, 20
+    parts = [_split_key(int(keys[t]), B, m) for t in order]
+    assert [p[1] for p in parts] == body_of_tri[order].tolist()
+    cell_body = [(p[0], p[1]) for p in parts]
+    assert cell_body == sorted(cell_body)  # cells in order, bodies in id order inside a cell
     T = n
     leaves = {}
 
@@ -108,10 +123,13 @@ def test_each_body_is_one_subtree():
     import sys
     sys.setrecursionlimit(10000)
     rec(0)
-    covers = [frozenset(v) for v in leaves.values()]
-    for b in range(nbody):
-        mine = frozenset(np.nonzero(sorted_body == b)[0].tolist())
-        assert len(mine) >= 2 and mine in covers, b
+    covers = set(frozenset(v) for v in leaves.values())
+    groups = {}
+    for p, cb in enumerate(cell_body):
+        groups.setdefault(cb, []).append(p)
+    assert len(groups) > nbody  # bodies do span several cells
+    for cb, ps in groups.items():
+        assert ps == list(range(ps[0], ps[-1] + 1)) and frozenset(ps) in covers, cb
 
 
 def _deinterleave(code: int, m: int = 21):
@@ -148,10 +166,10 @@ def test_morton_decodes_to_quantised_centroid(tiny41k):
 
 
 def test_body_keys_decode_to_body_and_quantised_centroid():
-    """Moving workload (65 bodies: B = 7 prefix bits, m = 18 bits per axis):
-    each key's top bits are the body of the triangle's first vertex and its
-    low 3m bits de-interleave to q <= 2^m (c - lo)/(hi - lo) < q + 1, up to the
-    FP32 quantiser's roundings."""
+    """Moving workload (65 bodies: B = 7 body bits, m = 18 bits per axis):
+    each key's body field is the body of the triangle's first vertex and its
+    coarse and fine bits together de-interleave to q <= 2^m (c - lo)/(hi - lo)
+    < q + 1, up to the FP32 quantiser's roundings."""
     w = sg.workload_frame7m(nspheres=40, cells=16)
     sc = w.scene
     assert sc.nbody == 65
@@ -167,9 +185,10 @@ def test_body_keys_decode_to_body_and_quantised_centroid():
     body = sc.vert_body[sc.idx[:, 0]].astype(np.int64)
     rng = np.random.default_rng(1)
     for i in rng.choice(sc.nt, 500, replace=False):
-        code = int(codes[i])
-        assert code >> (3 * m) == body[i] and code >> 63 == 0
-        q = _deinterleave(code & ((1 << (3 * m)) - 1), m)
+        key = int(codes[i])
+        _, b, code = _split_key(key, B, m)
+        assert b == body[i] and key >> 63 == 0
+        q = _deinterleave(code, m)
         for a in range(3):
             x = (c[i, a] - lo[a]) / (hi[a] - lo[a]) * 2 ** m
             tol = 5 * 2.0 ** -24 * x + 0.1
