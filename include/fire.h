@@ -198,12 +198,15 @@ int fire_render_info(fire_scene s, int64_t* out4);
  * 2012): transform every vertex by its body's row-major 3x4 world matrix
  * (x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row), Morton keys of
  * triangle-box centroids over the centroid bounds, stable radix sort,
- * radix-tree topology, bottom-up boxes.  Key = body << 3m | Morton code with
- * m bits per axis, body = that of the triangle's first vertex, B = bits of
- * (nbody - 1) and m = min(21, (63 - B) / 3): one body gives plain 63-bit
- * Morton codes; with several, each body's triangles form one subtree (the
- * paper's per-mesh bottom levels under a top level, §IV-B-3), so a refit
- * under rigid motion widens only the nodes above the bodies.
+ * radix-tree topology, bottom-up boxes.  With several rigid bodies the key
+ * holds a body field (body = that of the triangle's first vertex, B = bits
+ * of (nbody - 1), m = min(21, (63 - B) / 3) Morton bits per axis) between
+ * the Morton code's top 4 bits per axis and the rest:
+ *   key = coarse << (B + 3(m-4)) | body << 3(m-4) | fine,
+ * so inside each of the 16^3 coarse cells a body's triangles form one
+ * subtree (the paper's per-mesh bottom levels under a top level, §IV-B-3)
+ * and a refit under rigid motion widens only the nodes of the coarse levels
+ * by the bodies' drift.  One body: the plain 63-bit Morton code.
  *   body_xforms [nbody*12] float, device if xforms_on_device else host
  * Non-finite matrices -> FIRE_ERR_INVALID_ARG (host check only for host
  * matrices; device matrices are the caller's responsibility). */

@@ -80,6 +80,7 @@ constexpr int kExitInstance = 0x7ffffffe;  // traversal stack marker: back to th
 constexpr int kMaxLights = 8;
 constexpr int kMaxHeight = 128;              // tree height is at most 97 (64 + 32 prefix bits + 1)
 constexpr int kMaxDepth4 = 2 * kMaxHeight;   // 4-wide depths (each consumes >= 1 binary level)
+constexpr int kCoarseBits = 4;               // Morton bits per axis above the body field (single level)
 constexpr int kSortBits = 9;                 // 7 passes x 9 bits = 63-bit keys
 constexpr int kSortBins = 1 << kSortBits;
 constexpr int kSortPasses = 7;

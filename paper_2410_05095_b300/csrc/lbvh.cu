@@ -122,17 +122,20 @@ __device__ __forceinline__ uint32_t quantise(float c, float lo, float s, uint32_
   return (uint32_t)f;
 }
 
-// Build step 2: Morton key with m bits per axis (x -> bit 3k+2, y -> 3k+1,
-// z -> 3k) below a body prefix: key = body << 3m | code, body = that of the
-// triangle's first vertex.  With more than one rigid body every body's
-// triangles are consecutive in the sorted order and form one subtree, so a
-// refit under the bodies' rigid motions never widens a node by the drift
-// between two bodies (only the nodes above the bodies mix them).  The host
-// picks B = bits of (nbody - 1) and m = min(21, (63 - B) / 3); one body:
-// B = 0, m = 21.
+// Build step 2: Morton code with m bits per axis (x -> bit 3k+2, y -> 3k+1,
+// z -> 3k) and, with more than one rigid body, a body field of B bits
+// (body = that of the triangle's first vertex) between its top 3c bits
+// (coarse) and the rest (fine):
+//   key = coarse << (B + 3(m-c)) | body << 3(m-c) | fine.
+// Inside each coarse cell (1/2^c of the bounds per axis) a body's triangles
+// are consecutive in the sorted order and form one subtree, so a refit under
+// the bodies' rigid motions only widens the nodes of the coarse levels by
+// the drift between bodies.  The host picks B = bits of (nbody - 1),
+// m = min(21, (63 - B) / 3), c = 4 (two-level bottom levels: c = 0, one
+// subtree per body); one body: B = 0, m = 21, the plain Morton code.
 __global__ void k_morton(const float4* __restrict__ cen, int64_t nt, const uint32_t* __restrict__ bounds,
                          const uint32_t* __restrict__ idx, const uint16_t* __restrict__ vb, int prefix_bits,
-                         int m, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         int m, int coarse_bits, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                          uint64_t* __restrict__ keys_orig) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
@@ -148,7 +151,11 @@ __global__ void k_morton(const float4* __restrict__ cen, int64_t nt, const uint3
   float4 c = cen[i];
   uint64_t code = (spread3(quantise(c.x, lo[0], s[0], qmax)) << 2) |
                   (spread3(quantise(c.y, lo[1], s[1], qmax)) << 1) | spread3(quantise(c.z, lo[2], s[2], qmax));
-  if (prefix_bits > 0) code |= (uint64_t)vb[idx[3 * i]] << (3 * m);
+  if (prefix_bits > 0) {
+    const int fine = 3 * (m - coarse_bits);
+    const uint64_t low = fine > 0 ? code & ((1ull << fine) - 1) : 0ull;
+    code = ((code >> fine) << (prefix_bits + fine)) | ((uint64_t)vb[idx[3 * i]] << fine) | low;
+  }
   keys[i] = code;
   keys_orig[i] = code;
   vals[i] = (uint32_t)i;
@@ -1108,8 +1115,9 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   int prefix_bits = 0;
   while (s->nbody > 1 && (1 << prefix_bits) < s->nbody) ++prefix_bits;
   const int mbits = std::min(21, (63 - prefix_bits) / 3);
-  k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->idx, s->vbody, prefix_bits, mbits, s->keys,
-                                             s->order, s->keys_orig);
+  const int coarse_bits = s->two_level ? 0 : std::min(kCoarseBits, mbits);
+  k_morton<<<grid_for(T, 256), 256, 0, st>>>(s->cen, T, bounds, s->idx, s->vbody, prefix_bits, mbits, coarse_bits,
+                                             s->keys, s->order, s->keys_orig);
   // sort (keys, order) with ping-pong through (keys_alt, vals_alt); 7 passes
   const int ntiles = (int)((T + kSortTile - 1) / kSortTile);
   uint32_t* totals = s->hist + (int64_t)kSortBins * ntiles;
