@@ -271,6 +271,7 @@ def batch_ratio(fb, torch, reps=5):
     outs = [torch.zeros((c.height, c.width, 4), device="cuda") for c in cams]
     fb.render_batch(G, cams, cam_scene, lights, outs)  # autotune + capture
     cfg = fb.batch_last_config()
+    tuning = fb.fire.batch_last_tuning()
     for _ in range(2):
         fb.render_batch(G, cams, cam_scene, lights, outs)
     seq = [torch.zeros_like(o) for o in outs]
@@ -295,7 +296,8 @@ def batch_ratio(fb, torch, reps=5):
     tris = [s.nt for s in scenes]
     return {"batched_ms": t_batch, "sequential_ms": t_seq, "ratio": t_seq / t_batch, "identical": bool(same),
             "cameras": len(cams), "scenes": len(scenes), "tris_min": min(tris), "tris_max": max(tris),
-            "tuned": cfg}
+            "tuned": cfg, "tuning": tuning,
+            "tuning_spread": tuning["worst_ms"] / tuning["best_ms"] if tuning["best_ms"] > 0 else None}
 
 
 def two_level_compare(fb, torch, w, xf_build, xf_dev, ropts, single_seq):

@@ -243,10 +243,19 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
                 const fire_render_opts* opts, float* out_rgba, fire_gbuffer_rec* gbuf,
                 void* stream);
 
+/* Test hooks of fire_render_batch (with block_threads or blocks_per_sm set,
+ * which skips the search): FIRE_BATCH_TILE(n), n = 1..3, forces the tile
+ * shape n of fire_batch_last_tuning's list; FIRE_BATCH_GRAB2 makes a warp
+ * grab 2 tasks per atomic.  No other flag bit is accepted by the batch. */
+#define FIRE_BATCH_TILE(n) ((n) << 8)
+#define FIRE_BATCH_GRAB2 1024
+
 /* Render many cameras over many scenes with three launches for the whole
  * batch (primary rays of every camera, one shared shadow-ray queue, shading
  * and resolve), replayed as one CUDA graph while the batch's shape and
  * buffers are unchanged (descriptor changes are re-uploaded before replay).
+ * Unless opts fixes threads / blocks per SM, the first call of each batch
+ * shape times candidate configurations (fire_batch_last_tuning).
  * Batch-wide limit: sum of W*H*spp below 2^28, else FIRE_ERR_INVALID_ARG.
  *   scenes     host fire_scene[nscenes] (each built)
  *   cams       host fire_camera[ncams]; cam_scene host int32[ncams] (< nscenes)
@@ -423,6 +432,17 @@ int fire_batch_last_config(int32_t* out4);
  * bytes a positive multiple of 16, reps >= 1, else FIRE_ERR_INVALID_ARG. */
 int fire_probe_read(const void* buf, int64_t bytes, int32_t reps, uint32_t* sink, int32_t sink_words,
                     void* stream);
+
+/* The autotuner's record for the configuration of the last fire_render_batch
+ * launch.  out8: threads per block, blocks per SM (0 = occupancy limit),
+ * stack depth, task width in pixels at 1 spp, at 4 spp (a task is 32 / 8
+ * pixels), tasks a warp grabs per atomic, candidates timed (0 if the caller
+ * fixed the configuration), 1 if the search ran during that call.  ms2:
+ * the best and the worst candidate's time (ms; 0 if none was timed).  The
+ * search is coordinate-wise: threads x blocks per SM, then the tile shape
+ * (8x4 / 4x2, 4x8 / 2x4, 16x2 / 8x1 pixels at 1 / 4 spp), then 2 tasks per
+ * grab, then twice the stack the trees need. */
+int fire_batch_last_tuning(int32_t* out8, float* ms2);
 
 /* Thread-local message of the last failed call ("" if none). */
 const char* fire_last_error(void);

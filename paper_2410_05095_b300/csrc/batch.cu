@@ -57,19 +57,30 @@ __device__ __forceinline__ int find_sample_cam(const BatchCam* __restrict__ cams
   return lo;
 }
 
+// Work shape chosen by the autotuner: log2 of the task width at 1 and 4 spp
+// and the tasks a warp takes per atomic grab.
+struct BatchShape {
+  int lw1, lw4, grab;
+};
+
 template <int STACK>
 __global__ void __launch_bounds__(128) k_bprimary(const BatchCam* __restrict__ cams, int ncams, int ntasks,
                                                   uint32_t* ctrl, int4* __restrict__ gbuf, float4* __restrict__ jobs,
-                                                  int64_t cap) {
+                                                  int64_t cap, BatchShape sh) {
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;
+  int grabbed = 0, left = 0;
   while (true) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(ctrl + 0, 1);
-    task = __shfl_sync(kFull, task, 0);
+    if (left == 0) {
+      if (lane == 0) grabbed = atomicAdd(ctrl + 0, sh.grab);
+      grabbed = __shfl_sync(kFull, grabbed, 0);
+      left = sh.grab;
+    }
+    const int task = grabbed++;
+    --left;
     if (task >= ntasks) return;
     const BatchCam& bc = cams[find_task_cam(cams, ncams, task)];
-    TaskGrid g = make_grid(bc.cam.W, 0, bc.cam.H, bc.cam.spp);
+    TaskGrid g = make_grid_w(bc.cam.W, 0, bc.cam.H, bc.cam.spp, bc.cam.spp == 4 ? sh.lw4 : sh.lw1);
     int x, y, k;
     const bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
     TraceCtx c{bc.nodes4, bc.n4, scene_span(bc.nodes4, bc.nt), bc.tris, bc.nt, cap, bc.err};
@@ -138,15 +149,20 @@ __global__ void __launch_bounds__(128) k_bshadow(const BatchCam* __restrict__ ca
 }
 
 __global__ void __launch_bounds__(128) k_bresolve(const BatchCam* __restrict__ cams, int ncams, int ntasks,
-                                                  uint32_t* ctrl, const int4* __restrict__ gbuf) {
+                                                  uint32_t* ctrl, const int4* __restrict__ gbuf, BatchShape sh) {
   const int lane = threadIdx.x & 31;
+  int grabbed = 0, left = 0;
   while (true) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(ctrl + 1, 1);
-    task = __shfl_sync(kFull, task, 0);
+    if (left == 0) {
+      if (lane == 0) grabbed = atomicAdd(ctrl + 1, sh.grab);
+      grabbed = __shfl_sync(kFull, grabbed, 0);
+      left = sh.grab;
+    }
+    const int task = grabbed++;
+    --left;
     if (task >= ntasks) return;
     const BatchCam& bc = cams[find_task_cam(cams, ncams, task)];
-    TaskGrid g = make_grid(bc.cam.W, 0, bc.cam.H, bc.cam.spp);
+    TaskGrid g = make_grid_w(bc.cam.W, 0, bc.cam.H, bc.cam.spp, bc.cam.spp == 4 ? sh.lw4 : sh.lw1);
     int x, y, k;
     const bool valid = task_sample(g, task - bc.task_begin, lane, x, y, k);
     float3 rad = f3(0.0f, 0.0f, 0.0f);
@@ -201,8 +217,13 @@ __global__ void __launch_bounds__(128) k_bresolve(const BatchCam* __restrict__ c
   }
 }
 
+// Tile shapes: log2 task width at (1 spp, 4 spp): 8 x 4 / 4 x 2 pixels
+// (the single-frame path's), 4 x 8 / 2 x 4, 16 x 2 / 8 x 1.
+constexpr int kTileLw[3][2] = {{3, 2}, {2, 1}, {4, 3}};
+
 struct TuneCfg {
-  int threads = 128, bps = 0, stack = 64;
+  int threads = 128, bps = 0, stack = 64, tile = 0, grab = 1;
+  BatchShape shape() const { return BatchShape{kTileLw[tile][0], kTileLw[tile][1], grab}; }
 };
 
 struct BatchCache {
@@ -223,13 +244,20 @@ struct BatchCache {
     const void* ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
     bool operator==(const Key& k) const {
       return cfg.threads == k.cfg.threads && cfg.bps == k.cfg.bps && cfg.stack == k.cfg.stack &&
-             ncams == k.ncams && ntasks == k.ntasks && maxjobs == k.maxjobs && cap == k.cap &&
-             memcmp(ptrs, k.ptrs, sizeof(ptrs)) == 0;
+             cfg.tile == k.cfg.tile && cfg.grab == k.cfg.grab && ncams == k.ncams && ntasks == k.ntasks &&
+             maxjobs == k.maxjobs && cap == k.cap && memcmp(ptrs, k.ptrs, sizeof(ptrs)) == 0;
     }
   } last_key;
   cudaGraphExec_t exec = nullptr;
-  std::map<std::vector<int64_t>, TuneCfg> tuned;
+  struct Tuned {
+    TuneCfg cfg;
+    int tried = 0;
+    float best_ms = 0, worst_ms = 0;
+  };
+  std::map<std::vector<int64_t>, Tuned> tuned;
   int32_t info[4] = {0, 0, 0, 0};
+  Tuned last_tuning;
+  bool last_tuned_now = false;
 };
 
 BatchCache& cache() {
@@ -250,12 +278,13 @@ template <int STACK>
 void launch_batch(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, int64_t maxjobs, uint32_t* ctrl,
                   int4* gbuf, float4* jobs, int64_t cap, cudaStream_t st) {
   cudaMemsetAsync(ctrl, 0, 32, st);
+  const BatchShape sh = t.shape();
   k_bprimary<STACK><<<grid_of(k_bprimary<STACK>, t, ntasks), t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, gbuf,
-                                                                                   jobs, cap);
+                                                                                   jobs, cap, sh);
   if (maxjobs > 0)
     k_bshadow<STACK><<<grid_of(k_bshadow<STACK>, t, (maxjobs + 31) / 32), t.threads, 0, st>>>(cams, ncams, ctrl, gbuf,
                                                                                              jobs, cap);
-  k_bresolve<<<grid_of(k_bresolve, t, ntasks), t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, gbuf);
+  k_bresolve<<<grid_of(k_bresolve, t, ntasks), t.threads, 0, st>>>(cams, ncams, ntasks, ctrl, gbuf, sh);
 }
 
 void launch_cfg(const TuneCfg& t, const BatchCam* cams, int ncams, int ntasks, int64_t maxjobs, uint32_t* ctrl,
@@ -286,6 +315,23 @@ int batch_last_info(int32_t* out4) {
   return FIRE_OK;
 }
 
+int batch_last_tuning(int32_t* out8, float* ms2) {
+  BatchCache& C = cache();
+  std::lock_guard<std::mutex> lk(C.mu);
+  const BatchCache::Tuned& t = C.last_tuning;
+  out8[0] = t.cfg.threads;
+  out8[1] = t.cfg.bps;
+  out8[2] = t.cfg.stack;
+  out8[3] = 1 << kTileLw[t.cfg.tile][0];
+  out8[4] = 1 << kTileLw[t.cfg.tile][1];
+  out8[5] = t.cfg.grab;
+  out8[6] = t.tried;
+  out8[7] = C.last_tuned_now ? 1 : 0;
+  ms2[0] = t.best_ms;
+  ms2[1] = t.worst_ms;
+  return FIRE_OK;
+}
+
 int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams, const int32_t* cam_scene,
                  int ncams, const fire_light* lights, const int32_t* light_off, float* const* outs,
                  const fire_render_opts* opts, cudaStream_t st) {
@@ -311,10 +357,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     int e = make_lights(lights + light_off[sc], light_off[sc + 1] - light_off[sc], &b.lights);
     if (e) return e;
     b.err = s->ctrl + 8;
-    b.task_begin = ntasks;
     b.sample_base = nsamples;
-    TaskGrid g = make_grid(b.cam.W, 0, b.cam.H, b.cam.spp);
-    ntasks += g.tiles_x * g.tiles_y;
     nsamples += (int64_t)b.cam.W * b.cam.H * b.cam.spp;
     maxh = std::max(maxh, stack_need(s));
     maxl = std::max(maxl, b.lights.n);
@@ -325,6 +368,17 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     shape.push_back(b.cam.spp);
     shape.push_back(b.lights.n);
   }
+  // tasks of every camera for a tile shape (task_begin prefix sums)
+  auto layout = [&](int tile) {
+    int n = 0;
+    for (int i = 0; i < ncams; ++i) {
+      const TaskGrid g = make_grid_w(h[i].cam.W, 0, h[i].cam.H, h[i].cam.spp, kTileLw[tile][h[i].cam.spp == 4 ? 1 : 0]);
+      h[i].task_begin = n;
+      n += g.tiles_x * g.tiles_y;
+    }
+    return n;
+  };
+  ntasks = layout(0);
   if (ncams == 0 || ntasks == 0) return FIRE_OK;
   if (nsamples >= ((int64_t)1 << 28)) return set_error(FIRE_ERR_INVALID_ARG, "batch has 2^28 samples or more");
   const int64_t maxjobs = nsamples * maxl;
@@ -338,13 +392,15 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
     cudaMemsetAsync(C.d_ctrl, 0, 64, st);
   }
   const size_t nbytes = sizeof(BatchCam) * ncams;
-  bool same = C.last_bytes.size() == nbytes && memcmp(C.last_bytes.data(), h.data(), nbytes) == 0;
-  if (!same) {
+  auto upload = [&]() -> int {
+    bool same = C.last_bytes.size() == nbytes && memcmp(C.last_bytes.data(), h.data(), nbytes) == 0;
+    if (same) return FIRE_OK;
     if (int e = cuda_check(cudaMemcpyAsync(C.d_cams, h.data(), nbytes, cudaMemcpyHostToDevice, st), "upload"))
       return e;
     // the pageable copy is staged before cudaMemcpyAsync returns
     C.last_bytes.assign((unsigned char*)h.data(), (unsigned char*)h.data() + nbytes);
-  }
+    return FIRE_OK;
+  };
   // the scenes' current frame buffers: wait for their build/refit (the
   // tuning launches below read them too)
   for (int i = 0; i < nscenes; ++i) frame_acquire(scenes[i], st);
@@ -357,41 +413,88 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
   TuneCfg cfg;
   cfg.stack = need;
   bool tuned_now = false;
+  BatchCache::Tuned record;
   if (o.block_threads > 0 || o.blocks_per_sm > 0) {
     cfg.threads = o.block_threads > 0 ? o.block_threads : 128;
     cfg.bps = o.blocks_per_sm;
+    const int tile_sel = (o.flags >> 8) & 3;  // FIRE_BATCH_TILE(n): shape n - 1
+    cfg.tile = tile_sel > 0 ? tile_sel - 1 : 0;
+    cfg.grab = (o.flags & FIRE_BATCH_GRAB2) ? 2 : 1;
+    record.cfg = cfg;
   } else {
     auto it = C.tuned.find(shape);
     if (it != C.tuned.end()) {
-      cfg = it->second;
+      record = it->second;
+      cfg = record.cfg;
     } else {
+      // coordinate search, each candidate timed once after a warm launch:
+      // threads x persistent blocks per SM, then the task tile shape, then
+      // the tasks a warp grabs at once, then a deeper stack than the trees
+      // need (every candidate gives the same images)
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
-      float best = 1e30f;
+      float best = 1e30f, worst = 0.0f;
+      int tried = 0;
       TuneCfg bestc = cfg;
-      const int thr_list[2] = {64, 128};
-      const int bps_list[4] = {2, 4, 8, 0};
-      for (int thr : thr_list)
-        for (int bps : bps_list) {
-          TuneCfg t{thr, bps, need};
-          launch_cfg(t, C.d_cams, ncams, ntasks, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);  // warm
-          cudaEventRecord(e0, st);
-          launch_cfg(t, C.d_cams, ncams, ntasks, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best) { best = ms; bestc = t; }
+      auto time_cfg = [&](const TuneCfg& t) -> int {
+        const int n = layout(t.tile);
+        if (int e = upload()) return e;
+        launch_cfg(t, C.d_cams, ncams, n, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);  // warm
+        cudaEventRecord(e0, st);
+        launch_cfg(t, C.d_cams, ncams, n, maxjobs, C.d_ctrl, C.d_gbuf, C.d_jobs, cap, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ++tried;
+        worst = std::max(worst, ms);
+        if (ms < best) {
+          best = ms;
+          bestc = t;
         }
+        return FIRE_OK;
+      };
+      for (int thr : {64, 128})
+        for (int bps : {2, 4, 8, 0}) {
+          TuneCfg t = cfg;
+          t.threads = thr;
+          t.bps = bps;
+          if (int e = time_cfg(t)) return e;
+        }
+      const TuneCfg base1 = bestc;
+      for (int tile : {1, 2}) {
+        TuneCfg t = base1;
+        t.tile = tile;
+        if (int e = time_cfg(t)) return e;
+      }
+      const TuneCfg base2 = bestc;
+      {
+        TuneCfg t = base2;
+        t.grab = 2;
+        if (int e = time_cfg(t)) return e;
+      }
+      if (need < 128) {
+        TuneCfg t = bestc;
+        t.stack = need * 2 > 128 ? 128 : need * 2;
+        if (int e = time_cfg(t)) return e;
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       if (int e = cuda_check(cudaGetLastError(), "autotune")) return e;
       cfg = bestc;
-      C.tuned[shape] = cfg;
+      record.cfg = cfg;
+      record.tried = tried;
+      record.best_ms = best;
+      record.worst_ms = worst;
+      C.tuned[shape] = record;
       tuned_now = true;
     }
   }
+  ntasks = layout(cfg.tile);
+  if (int e = upload()) return e;
+  C.last_tuning = record;
+  C.last_tuned_now = tuned_now;
   C.info[0] = cfg.threads;
   C.info[1] = cfg.bps;
   C.info[2] = cfg.stack;

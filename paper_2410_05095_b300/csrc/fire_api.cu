@@ -692,7 +692,8 @@ int fire_render_batch(const fire_scene* scenes, int32_t nscenes, const fire_came
     if (int e = check_cam(&cams[i])) return e;
     if (!outs[i]) return set_error(FIRE_ERR_INVALID_ARG, "NULL output");
   }
-  if (opts && (opts->row_begin || opts->row_end || opts->flags || opts->stack_depth < 0 || opts->stack_depth > 128 ||
+  if (opts && (opts->row_begin || opts->row_end || (opts->flags & ~(FIRE_BATCH_TILE(3) | FIRE_BATCH_GRAB2)) ||
+               opts->stack_depth < 0 || opts->stack_depth > 128 ||
                opts->blocks_per_sm < 0 || opts->block_threads < 0 || opts->block_threads > 128 ||
                (opts->block_threads % 32) != 0))
     return set_error(FIRE_ERR_INVALID_ARG, "invalid batch options");
@@ -934,6 +935,12 @@ int fire_batch_last_config(int32_t* out4) {
   g_err.clear();
   if (!out4) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
   return batch_last_info(out4);
+}
+
+int fire_batch_last_tuning(int32_t* out8, float* ms2) {
+  g_err.clear();
+  if (!out8 || !ms2) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  return batch_last_tuning(out8, ms2);
 }
 
 }  // extern "C"

@@ -339,6 +339,7 @@ int render_batch(const fire_scene* scenes, int nscenes, const fire_camera* cams,
                  cudaStream_t st);
 void batch_free(fire_scene_s* s);
 int batch_last_info(int32_t* out4);
+int batch_last_tuning(int32_t* out8, float* ms2);
 
 // ---------------------------------------------------------------------------
 // Device math with the fixed operation order

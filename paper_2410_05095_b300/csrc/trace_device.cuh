@@ -484,33 +484,38 @@ __device__ __forceinline__ void hit_frame(float4 B, float4 C, float3 o, float3 d
 // block x 4 samples (lanes 4q..4q+3 hold pixel q; the compact block keeps a
 // warp's rays closer than 8 pixels of a row: primary 1.09 -> 1.04 ms, shadow
 // 1.37 -> 1.34 ms on the 7.3M-triangle frame), spp 1 -> an 8 x 4 pixel block.
+// The batch's autotuner may pick another task width (a power of two: 2, 4 or
+// 8 pixels at 4 spp, 4, 8, 16 or 32 at 1 spp); lanes 4q..4q+3 always hold
+// pixel q's four samples.
 struct TaskGrid {
-  int tiles_x, tiles_y, row_begin, rows_per_task, W, row_end, spp;
+  int tiles_x, tiles_y, row_begin, rows_per_task, W, row_end, spp, lw;  // lw = log2(task width)
 };
 
-__host__ __device__ __forceinline__ TaskGrid make_grid(int W, int row_begin, int row_end, int spp) {
+__host__ __device__ __forceinline__ TaskGrid make_grid_w(int W, int row_begin, int row_end, int spp, int lw) {
   TaskGrid g;
   g.W = W;
   g.spp = spp;
   g.row_begin = row_begin;
   g.row_end = row_end;
-  g.rows_per_task = spp == 4 ? 2 : 4;
-  g.tiles_x = spp == 4 ? (W + 3) / 4 : (W + 7) / 8;
+  g.lw = lw;
+  const int px = spp == 4 ? 8 : 32;  // pixels per task
+  const int tw = 1 << lw;
+  g.rows_per_task = px / tw;
+  g.tiles_x = (W + tw - 1) / tw;
   g.tiles_y = (row_end - row_begin + g.rows_per_task - 1) / g.rows_per_task;
   return g;
 }
 
+__host__ __device__ __forceinline__ TaskGrid make_grid(int W, int row_begin, int row_end, int spp) {
+  return make_grid_w(W, row_begin, row_end, spp, spp == 4 ? 2 : 3);  // 4 x 2 or 8 x 4 pixels
+}
+
 __device__ __forceinline__ bool task_sample(const TaskGrid& g, int task, int lane, int& x, int& y, int& k) {
-  int tx = task % g.tiles_x, ty = task / g.tiles_x;
-  if (g.spp == 4) {
-    x = tx * 4 + ((lane >> 2) & 3);
-    y = g.row_begin + ty * 2 + (lane >> 4);
-    k = lane & 3;
-  } else {
-    x = tx * 8 + (lane & 7);
-    y = g.row_begin + ty * 4 + (lane >> 3);
-    k = 0;
-  }
+  const int tx = task % g.tiles_x, ty = task / g.tiles_x;
+  const int q = g.spp == 4 ? lane >> 2 : lane;  // pixel of the task
+  x = (tx << g.lw) + (q & ((1 << g.lw) - 1));
+  y = g.row_begin + ty * g.rows_per_task + (q >> g.lw);
+  k = g.spp == 4 ? lane & 3 : 0;
   return x < g.W && y < g.row_end;
 }
 

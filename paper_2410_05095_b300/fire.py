@@ -28,7 +28,8 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_debug_set_iteration_cap", "fire_debug_fail_alloc", "fire_batch_last_config",
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
            "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_probe_read",
-           "fire_scene_set_two_level", "fire_debug_trace_host", "fire_last_error", "fire_version"]
+           "fire_scene_set_two_level", "fire_debug_trace_host", "fire_batch_last_tuning", "fire_last_error",
+           "fire_version"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
 
@@ -96,6 +97,7 @@ def lib():
             "fire_probe_read": [P, i64, i32, P, i32, P],
             "fire_scene_set_two_level": [P, i32],
             "fire_debug_trace_host": [P, P, P, P, P, i64, i32, P, P, P, P],
+            "fire_batch_last_tuning": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -363,6 +365,15 @@ def batch_last_config() -> dict:
     out = (C.c_int32 * 4)()
     _check(lib().fire_batch_last_config(out))
     return dict(threads=out[0], blocks_per_sm=out[1], stack=out[2], tuned=out[3])
+
+
+def batch_last_tuning() -> dict:
+    """The autotuner's record for the last batch launch (fire_batch_last_tuning)."""
+    out = (C.c_int32 * 8)()
+    ms = (C.c_float * 2)()
+    _check(lib().fire_batch_last_tuning(out, ms))
+    return dict(threads=out[0], blocks_per_sm=out[1], stack=out[2], tile_w_1spp=out[3], tile_w_4spp=out[4],
+                grab=out[5], tried=out[6], tuned_now=bool(out[7]), best_ms=ms[0], worst_ms=ms[1])
 
 
 def fail_next_alloc(nth: int = 1):

@@ -254,9 +254,25 @@ def test_batch_equals_sequential(fb):
     fb.render_batch(G, cams, cam_scene, lights, outs)
     cfg = fb.batch_last_config()
     assert cfg["tuned"] == 1 and cfg["threads"] in (64, 128, 256)
+    tun = fb.fire.batch_last_tuning()
+    assert tun["tuned_now"] and tun["tried"] >= 11 and 0 < tun["best_ms"] <= tun["worst_ms"]
+    assert (tun["tile_w_1spp"], tun["tile_w_4spp"]) in ((8, 4), (4, 2), (16, 8)) and tun["grab"] in (1, 2)
     for c, si, o in zip(cams, cam_scene, outs):
         ref = G[si].render(c, lights[si])
         assert torch.equal(o, ref)
+    # every tile shape and grab size the search may pick gives the same
+    # images (fixed threads / blocks per SM skip the search; the flags force
+    # the shape)
+    for tile in (1, 2, 3):
+        for grab in (0, 1024):
+            outs_fixed = [torch.zeros_like(o) for o in outs]
+            fb.render_batch(G, cams, cam_scene, lights, outs_fixed,
+                            opts=fb.fire.make_opts(block_threads=64, blocks_per_sm=2, flags=(tile << 8) | grab))
+            t = fb.fire.batch_last_tuning()
+            assert t["tried"] == 0 and t["grab"] == (2 if grab else 1)
+            assert t["tile_w_1spp"] == (8, 4, 16)[tile - 1] and t["tile_w_4spp"] == (4, 2, 8)[tile - 1]
+            for a, b in zip(outs, outs_fixed):
+                assert torch.equal(a, b), (tile, grab)
     # graph replay gives the same images
     outs2 = [o.clone().fill_(-1) for o in outs]
     fb.render_batch(G, cams, cam_scene, lights, outs2)
