@@ -124,7 +124,80 @@ def test_emulated_degenerate_bodies(fb):
         assert err == 0 and np.array_equal(hit, S.occluded(o, d, L))
 
 
+def test_emulated_fullsize(fb, frame7m_two):
+    """The headline workload at full size (7,299,072 triangles, 65 bodies),
+    frame 2: 2,000 sampled camera rays and 2,000 segments walked on the
+    host, in bounds, equal to the oracle."""
+    w, G, S, _ = frame7m_two
+    cam = w.camera
+    rng = np.random.default_rng(77)
+    ids = rng.choice(cam.width * cam.height * cam.spp, 2000, replace=False)
+    o = np.zeros((len(ids), 3), np.float32)
+    d = np.zeros((len(ids), 3), np.float32)
+    for i, sid in enumerate(ids):
+        k, p = int(sid % 4), int(sid // 4)
+        o[i], d[i] = oracle.camera_ray(cam, p % cam.width, p // cam.width, k)
+    prim, t, _, err = G.trace_host(o, d)
+    assert err == 0, hex(err)
+    rp, rt, _, _, rt2 = S.trace(o, d, want_t2=True)
+    bad = (prim != rp) | ((prim >= 0) & (t != rt))
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))
+    assert not (bad & ~tie).any()
+    so, sd, sl = _segments(rng, 2000, [-12, -3, -12], [12, 5, 12])
+    _, _, hit, err = G.trace_host(so, sd, tmax=sl, any_hit=True)
+    assert err == 0 and np.array_equal(hit, S.occluded(so, sd, sl))
+
+
+@pytest.fixture(scope="module")
+def frame7m_two():
+    """The full-size moving workload in two-level mode on both sides, two
+    frames after the build (top level rebuilt per frame)."""
+    import paper_2410_05095_b300 as fb
+    torch_cuda()
+    w = sg.workload_frame7m()
+    G, S = _pair2(fb, w.scene, w.motion.xforms())
+    poses = []
+    for _ in range(2):
+        xf = w.motion.step()
+        poses.append(xf)
+        G.refit(xf)
+        S.update(xf, rebuild=False)
+    return w, G, S, poses
+
+
 # --------------------------------------------------------------- device kernels
+def test_fullsize_two_level_sampled_render(fb, frame7m_two):
+    """The GPU two-level render of that frame: 20,000 sampled samples by the
+    agreement rule, 2,000 sampled pixels' radiance within 1e-4."""
+    torch = torch_cuda()
+    w, G, S, _ = frame7m_two
+    cam = w.camera
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    img = G.render(cam, w.lights, gbuf=gb).cpu().numpy()
+    assert G.sync_status() == 0
+    g = gbuf_of(gb)
+    rng = np.random.default_rng(2411)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def ref_of(ids):
+        chunks = np.array_split(np.asarray(ids, np.int64), THREADS * 2)
+        with ThreadPoolExecutor(THREADS) as ex:
+            parts = list(ex.map(lambda c: S.render_samples(cam, w.lights, c), chunks))
+        return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    ids = rng.choice(cam.width * cam.height * cam.spp, 20000, replace=False)
+    compare_samples(g, ref_of(ids), ids)
+    pix = rng.choice(cam.width * cam.height, 2000, replace=False)
+    pid = (pix[:, None] * 4 + np.arange(4)[None, :]).ravel()
+    rs = ref_of(pid)
+    _, bad = compare_samples(g, rs, pid)
+    acc = np.zeros((len(pix), 3), np.float32)
+    for k in range(4):
+        acc = acc + rs["rgb"][k::4]
+    ref_px = np.concatenate([acc / np.float32(4), (rs["prim"].reshape(-1, 4) >= 0).mean(1, keepdims=True)], 1)
+    ok = ~bad.reshape(-1, 4).any(1)
+    assert_radiance_close(img.reshape(-1, 4)[pix][None], ref_px[None].astype(np.float32), ok[None])
+    assert (g["prim"] >= 0).mean() > 0.3
 def _render(fb, G, cam, lights, **opts):
     torch = torch_cuda()
     gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
