@@ -381,6 +381,51 @@ def frame_filling_view(fb, torch, G, w, xf_dev, first, reps=10):
             "hit_fraction": hits / prim_rays, "grays_per_s": (prim_rays + shadow) / (trace * 1e-3) / 1e9}
 
 
+def static_workloads(fb, torch):
+    """The static workloads of the measurement plan: tiny41k (40,962
+    triangles, 256^2, 1 spp, 1 light; 100 renders after 10 warm-up renders)
+    and mid1m (1,155,072 triangles, 1280x720, 4 spp, 3 lights; build time
+    reported separately, then 100 renders): median and p95 ms per render
+    (CUDA events around each render), and the one-time build (GPU time of
+    a second build, and wall clock of the first with its allocations)."""
+    res = {}
+    for name in ("tiny41k", "mid1m"):
+        w = sg.WORKLOADS[name]()
+        cam, lights = w.camera, w.lights
+        G = fb.Scene.from_numpy(w.scene)
+        xf = w.scene.identity_xforms()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.build(xf)
+        torch.cuda.synchronize()
+        first_build = (time.perf_counter() - t0) * 1e3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        G.build(xf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build = e0.elapsed_time(e1)
+        out = torch.zeros((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
+        for _ in range(10):
+            G.render(cam, lights, out=out)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(100)]
+        for a, b in evs:
+            a.record(stream)
+            G.render(cam, lights, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        assert G.sync_status() == 0
+        t = np.array([a.elapsed_time(b) for a, b in evs])
+        res[name] = {"triangles": w.scene.nt, "image": f"{cam.width}x{cam.height}x{cam.spp}spp",
+                     "lights": len(lights), "render_median_ms": float(np.median(t)),
+                     "render_p95_ms": float(np.percentile(t, 95)), "build_ms": build,
+                     "first_build_wall_ms": first_build,
+                     "mrays_primary_per_s": cam.width * cam.height * cam.spp / (np.median(t) * 1e-3) / 1e6}
+        G.destroy()
+    return res
+
+
 def backward_ratio(fb, torch, reps=20):
     """Backward of the shading stage vs its forward (512x512, 1 spp, 32
     materials, 2 lights, 499,712 triangles)."""
@@ -700,6 +745,7 @@ def main():
         line["batched"] = batch_ratio(fb, torch)
         line["backward"] = backward_ratio(fb, torch)
         line["two_level"] = two_level_compare(fb, torch, w, xf_build, xf_dev, ropts, sequence)
+        line["static_workloads"] = static_workloads(fb, torch)
     if rank == 0 and not args.no_cpu:
         import oracle
         threads = host_threads()
