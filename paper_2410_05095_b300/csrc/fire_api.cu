@@ -213,7 +213,7 @@ void free_scene(fire_scene_s* s) {
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
                   s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
                   s->blas_root, s->body_box, s->body_range, s->xf_ident, s->tlas_buf[0], s->tlas_buf[1],
-                  s->tinfo_buf[0], s->tinfo_buf[1]};
+                  s->tinfo_buf[0], s->tinfo_buf[1], s->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int b = 0; b < 2; ++b) {
@@ -262,6 +262,7 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
       {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
+      {(void**)&s->stage, 24 * (size_t)T},
       {(void**)&s->lvl_aux, 12 * (size_t)kMaxDepth4 + 16},
       {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T, 1)},
       {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T, 1)},

@@ -49,6 +49,9 @@ struct __align__(16) Node4 {
 };
 static_assert(sizeof(Node4) == 128, "4-wide node must be 128 bytes");
 constexpr int kEmptyLink = (int)0x80000000;
+// leaf_slot4 flag: the leaf's 4-wide node also has internal members (the
+// refit stages the leaf's box; 4 x node + lane stays below 2^30)
+constexpr int32_t kSlotMixed = 1 << 30;
 
 // Triangle record in leaf (sorted) order, 48 B:
 //   v0.xyz, w = original triangle index (bits)
@@ -151,7 +154,8 @@ struct fire_scene_s {
   uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]), collapse queue
                                 //   lengths (u32 [kMaxDepth4]) and the node counter (u32)
   std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
-  int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf
+  int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf (| kSlotMixed)
+  float* stage = nullptr;       // [nt*6] refit: boxes of the leaves in mixed nodes (sorted order)
   fire::Node4* nodes4 = nullptr;// [max(nt, 1)] 4-wide traversal tree (current buffer)
   int64_t n4 = 0;               // 4-wide nodes in use
   int height4 = 0;              // 4-wide levels

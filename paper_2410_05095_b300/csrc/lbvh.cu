@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict_
                                                        const uint32_t* __restrict__ smat, int64_t nt,
                                                        float4* __restrict__ tris, Node4* __restrict__ nodes4,
                                                        const int32_t* __restrict__ leaf_slot4, int64_t n4,
-                                                       float* __restrict__ xfb, int nxf) {
+                                                       float* __restrict__ xfb, int nxf, float* __restrict__ stage) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nxf) xfb[i] = xf[i];  // the frame buffer's copy of the body matrices
   if (i >= nt) return;
@@ -1002,7 +1002,21 @@ __global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict_
   tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
   float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
   const int32_t ls = leaf_slot4[i];
-  if (ls < 0 || (ls >> 2) >= n4) return;  // never for a complete collapse
+  if (ls < 0) return;  // never for a complete collapse
+  if (ls & kSlotMixed) {
+    // a node with internal members too: its level pass writes it whole,
+    // taking this box from the staging array (6 consecutive floats per
+    // leaf, coalesced) -- no partial sector of the node is written here
+    float* b = stage + 6 * i;
+    b[0] = lo.x;
+    b[1] = lo.y;
+    b[2] = lo.z;
+    b[3] = hi.x;
+    b[4] = hi.y;
+    b[5] = hi.z;
+    return;
+  }
+  if ((ls >> 2) >= n4) return;  // never for a complete collapse
   float* n = reinterpret_cast<float*>(nodes4 + (ls >> 2));
   const int lanes = nt == 1 ? 2 : 1;  // a single triangle sits in two slots of the root
   for (int k = 0; k < lanes; ++k) {
@@ -1016,18 +1030,34 @@ __global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict_
   }
 }
 
-__device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4) {
+// A node with at least one internal member, written whole: an internal
+// member's box is the union of its child's four boxes (unused slots hold
+// the inverted infinite box, neutral for min/max), a leaf member's box
+// comes from the staging array (its leaf was marked kSlotMixed at build),
+// an unused slot keeps the inverted infinite box.
+__device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4, const float* __restrict__ stage,
+                                            int64_t nt) {
   Node4* n = nodes4 + q;
   const int4 lk = n->link;
   const int l[4] = {lk.x, lk.y, lk.z, lk.w};
   if (l[0] < 0 && l[1] < 0 && l[2] < 0 && l[3] < 0) return;  // leaves only: written by the leaf kernel
+  const float inf = __int_as_float(0x7f800000);
   float4 m[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) m[j] = __ldcg(&n->lox + j);
+  for (int j = 0; j < 6; ++j) m[j] = j < 3 ? make_float4(inf, inf, inf, inf) : make_float4(-inf, -inf, -inf, -inf);
   float* f = reinterpret_cast<float*>(m);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    if (l[c] < 0 || l[c] >= n4) continue;
+    if (l[c] == kEmptyLink) continue;
+    if (l[c] < 0) {
+      const int64_t p = ~(int64_t)l[c];
+      if (p >= nt) continue;  // never for a complete collapse
+      const float* b = stage + 6 * p;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) f[j * 4 + c] = __ldcg(b + j);
+      continue;
+    }
+    if (l[c] >= n4) continue;  // never for a complete collapse
     const Node4* ch = nodes4 + l[c];
     float4 a[6];
 #pragma unroll
@@ -1043,18 +1073,33 @@ __device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4
   for (int j = 0; j < 6; ++j) (&n->lox)[j] = m[j];
 }
 
-__global__ void __launch_bounds__(128) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4) {
+__global__ void __launch_bounds__(128) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4,
+                                                      const float* __restrict__ stage, int64_t nt) {
   const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q < end) refit4_node(nodes4, q, n4);
+  if (q < end) refit4_node(nodes4, q, n4, stage, nt);
 }
 
 // depths lvl[d0] .. lvl[d1], deepest (d1) first
 __global__ void __launch_bounds__(1024) k_refit4_small(Node4* nodes4, const int64_t* __restrict__ lvl, int d0, int d1,
-                                                       int64_t n4) {
+                                                       int64_t n4, const float* __restrict__ stage, int64_t nt) {
   for (int dth = d1; dth >= d0; --dth) {
-    for (int64_t q = lvl[dth] + threadIdx.x; q < lvl[dth + 1]; q += blockDim.x) refit4_node(nodes4, q, n4);
+    for (int64_t q = lvl[dth] + threadIdx.x; q < lvl[dth + 1]; q += blockDim.x) refit4_node(nodes4, q, n4, stage, nt);
     __syncthreads();
   }
+}
+
+// Build: mark the leaves of nodes that also have internal members
+// (kSlotMixed in their leaf_slot4): the per-frame refit stages their boxes.
+__global__ void k_mark_mixed(const Node4* __restrict__ nodes4, int64_t n4, int32_t* __restrict__ leaf_slot4,
+                             int64_t nt) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const int4 lk = nodes4[q].link;
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  const bool internal = l[0] >= 0 || l[1] >= 0 || l[2] >= 0 || l[3] >= 0;
+  if (!internal) return;
+  for (int c = 0; c < 4; ++c)
+    if (l[c] < 0 && l[c] != kEmptyLink && ~(int64_t)l[c] < nt) leaf_slot4[~l[c]] |= kSlotMixed;
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -1216,6 +1261,8 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
                            "copy"))
       return e;
     k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
+    if (!s->two_level && s->n4 > 0)
+      k_mark_mixed<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes4, s->n4, s->leaf_slot4, T);
     if (s->two_level)
       k_body_boxes<<<grid_for(s->nbody, 256), 256, 0, st>>>(s->nodes4, s->n4, s->blas_root, s->nbody, s->body_box);
     if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
@@ -1246,7 +1293,8 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   // kernels' blocks when a refit overlaps the previous frame's render
   const int nxf = 12 * s->nbody;
   k_refit4_leaves<<<grid_for(std::max<int64_t>(T, nxf), 128), 128, 0, st>>>(
-      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes4, s->leaf_slot4, s->n4, s->xf_buf[s->cur], nxf);
+      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes4, s->leaf_slot4, s->n4, s->xf_buf[s->cur], nxf,
+      s->stage);
   // depths, deepest first: runs of small depths go to one block, large ones get their own launch
   const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
   const int64_t* lvl_dev = reinterpret_cast<const int64_t*>(s->lvl_aux);
@@ -1255,13 +1303,13 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
     const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
     ++launches;
     if (n > 8192) {
-      k_refit4_level<<<grid_for(n, 128), 128, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4);
+      k_refit4_level<<<grid_for(n, 128), 128, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4, s->stage, T);
       --d;
       continue;
     }
     int d0 = d;
     while (d0 > 0 && s->lvl4[d0] - s->lvl4[d0 - 1] <= 8192) --d0;
-    k_refit4_small<<<1, 1024, 0, st>>>(s->nodes4, lvl_dev, d0, d, s->n4);
+    k_refit4_small<<<1, 1024, 0, st>>>(s->nodes4, lvl_dev, d0, d, s->n4, s->stage, T);
     d = d0 - 1;
   }
   prof_end(s, kStageRefit, st, launches);
