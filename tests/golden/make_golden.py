@@ -39,7 +39,7 @@ def body_key_rows():
       key = coarse << (B + 3(m-4)) | body << 3(m-4) | fine."""
     rows = []
     c = 4
-    for nbody in (2, 3, 65):
+    for nbody in (2, 3, 65, 1025, 65536):
         B = (nbody - 1).bit_length()
         m = min(21, (63 - B) // 3)
         q = {"lo": 0, "mid": 1 << (m - 1), "hi": (1 << m) - 1}

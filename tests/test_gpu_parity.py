@@ -57,6 +57,45 @@ def test_lbvh_duplicate_keys_and_tiny_counts(fb):
         assert_lbvh_equal(G, S, sc)
 
 
+@pytest.mark.parametrize("nbody", [1000, 65536])
+def test_lbvh_many_bodies_bitexact(fb, nbody):
+    """Keys with a wide body field (B = 10 and 16 bits, m = 17 and 15 bits per
+    axis): a soup of small triangles spread over the bodies, posed by random
+    rigid matrices -- build, refit, sampled render, all against the oracle."""
+    rng = np.random.default_rng(nbody)
+    nt = 3000 if nbody == 1000 else 70000
+    c = rng.uniform(-4, 4, (nt, 3))
+    tris = np.stack([c, c + rng.uniform(-0.2, 0.2, (nt, 3)), c + rng.uniform(-0.2, 0.2, (nt, 3))], 1)
+    body = rng.integers(0, nbody, nt)
+    from test_oracle_lbvh import _scene_from_tris
+    sc = _scene_from_tris(tris, nbody=nbody, vbody=np.repeat(body, 3).astype(np.uint16))
+
+    def poses(seed):
+        r = np.random.default_rng(seed)
+        xf = np.zeros((nbody, 12), np.float32)
+        for b in range(nbody):
+            q = r.normal(size=4)
+            q /= np.linalg.norm(q)
+            w, x, y, z = q
+            R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                          [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                          [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]]) if b % 7 else np.eye(3)
+            xf[b] = np.concatenate([R, r.uniform(-0.5, 0.5, (3, 1))], 1).reshape(12)
+        return xf
+    G, S = build_pair(sc, poses(1))
+    assert_lbvh_equal(G, S, sc)
+    xf = poses(2)
+    G.refit(xf)
+    S.update(xf, rebuild=False)
+    assert np.array_equal(G.dump("boxes"), S.get("boxes"))
+    cam = sg.Camera((0.5, 9.0, 11.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 50.0, 64, 48, 4)
+    img, g = _render(G, cam, [sg.LIGHTS_MAIN[0]])
+    ref = S.render_all_samples(cam, [sg.LIGHTS_MAIN[0]], threads=THREADS)
+    _, bad = compare_samples(g, ref)
+    assert_radiance_close(img, S.render_image(cam, [sg.LIGHTS_MAIN[0]], threads=THREADS), pixel_ok_mask(bad, 64, 48, 4))
+    assert (ref["prim"] >= 0).mean() > 0.03
+
+
 def test_refit_frames_bitexact(fb):
     w = sg.workload_frame7m(nspheres=120, cells=64)
     sc = w.scene

@@ -59,7 +59,7 @@ def test_morton_body_prefix_hand_codes():
         if line.strip() and not line.startswith("#"):
             nb, body, x, y, z, key = line.split()
             rows.setdefault(int(nb), []).append((int(body), [pos[x], pos[y], pos[z]], int(key, 16)))
-    assert sorted(rows) == [2, 3, 65]
+    assert sorted(rows) == [2, 3, 65, 1025, 65536]
     for nbody, cases in rows.items():
         tris = [_point_tri([0, 0, 0]), _point_tri([8, 8, 8])] + [_point_tri(p) for _, p, _ in cases]
         vb = np.repeat([0, 0] + [b for b, _, _ in cases], 3).astype(np.uint16)
