@@ -108,27 +108,38 @@ class Clocks:
 
 # ----------------------------------------------------------------------- roofline
 KERNEL_NAMES = {"refit": "k_refit4_leaves+k_refit4_level+k_refit4_small", "primary": "k_primary",
-                "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
+                "queue": "k_qsum+k_qperm", "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
 
 
-def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shadow_rays: int):
-    """Minimum bytes each kernel family must move per frame:
+def render_tasks(width: int, height: int, spp: int) -> int:
+    """Warp tasks of one image: 4 x 2 pixels at 4 spp, 8 x 4 at 1 spp."""
+    tw, th = (4, 2) if spp == 4 else (8, 4)
+    return -(-width // tw) * -(-height // th)
+
+
+def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shadow_rays: int,
+                      queue_counts: int = 0):
+    """Minimum bytes each kernel family must move per frame
+    (queue_counts = lights x tasks):
     refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, the
                sorted index record (16 B), material (4 B) and 4-wide lane
                (4 B) per triangle; write the 48-B triangle record and the
                24-B leaf box; per 4-wide node read its 112-B boxes+links once
                (by its parent) and write its 96 B of boxes once
     primary -- read the traversal tree once (128 B per 4-wide node + 48 B
-               per triangle) + write a 16-B record per sample + a 32-B
-               queued shadow ray
-    shadow  -- read the traversal tree once + each 32-B queued ray, its 4-B
-               skip id and a 4-B visibility update
+               per triangle) + write a 16-B record per sample, a 32-B
+               queued shadow ray and a 4-B ray count per task and light
+    queue   -- read the counts twice (block sums, then the scan) and write a
+               4-B slot per shadow ray
+    shadow  -- read the traversal tree once + each ray's 4-B slot, its 32-B
+               queue entry, its 4-B skip id and a 4-B visibility update
     resolve -- read the 16-B record per sample + 32 B of its triangle for the
                hit frame + write a 16-B pixel."""
     tree = 128 * n4 + 48 * nt
     return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48 + 24) + n4 * (112 + 96),
-            "primary": tree + 16 * samples + 32 * shadow_rays,
-            "shadow": tree + 40 * shadow_rays,
+            "primary": tree + 16 * samples + 32 * shadow_rays + 4 * queue_counts,
+            "queue": 8 * queue_counts + 4 * shadow_rays,
+            "shadow": tree + 44 * shadow_rays,
             "resolve": 16 * samples + 32 * samples + 16 * pixels}
 
 
@@ -324,7 +335,7 @@ def two_level_compare(fb, torch, w, xf_build, xf_dev, ropts, single_seq):
         G.render(cam, lights, out=out)
     p = G.profile_read()
     G.profile(False)
-    stages = {k: p[k][0] / 20 for k in ("primary", "shadow", "resolve")}
+    stages = {k: p[k][0] / 20 for k in ("primary", "queue", "shadow", "resolve")}
     G.build(xf_build)
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(100)]
     ends[0].record(stream)
@@ -374,8 +385,8 @@ def frame_filling_view(fb, torch, G, w, xf_dev, first, reps=10):
     shadow = int(sum(((vis >> (8 + j)) & 1).sum().item() for j in range(len(lights))))
     hits = int((gb[:, 0] >= 0).sum().item())
     prim_rays = cam.width * cam.height * cam.spp
-    st = {k: p[k][0] / reps for k in ("refit", "primary", "shadow", "resolve")}
-    trace = st["primary"] + st["shadow"] + st["resolve"]
+    st = {k: p[k][0] / reps for k in ("refit", "primary", "queue", "shadow", "resolve")}
+    trace = st["primary"] + st["queue"] + st["shadow"] + st["resolve"]
     return {"camera": {"pos": list(cam.pos), "target": list(cam.target)}, "ms_per_frame_serial": e0.elapsed_time(e1) / reps,
             "stages_ms": st, "rays": {"primary": prim_rays, "shadow": shadow, "hit_samples": hits},
             "hit_fraction": hits / prim_rays, "grays_per_s": (prim_rays + shadow) / (trace * 1e-3) / 1e9}
@@ -687,12 +698,12 @@ def main():
     hits = int((gb[:, 0] >= 0).sum().item())
     del gb
 
-    avg = {k: stages[k][0] / K for k in ("refit", "primary", "shadow", "resolve")}  # one of each per frame
-    trace_ms = avg["primary"] + avg["shadow"] + avg["resolve"]
+    avg = {k: stages[k][0] / K for k in ("refit", "primary", "queue", "shadow", "resolve")}  # one of each per frame
+    trace_ms = avg["primary"] + avg["queue"] + avg["shadow"] + avg["resolve"]
     grays = (primary_rays + shadow_rays) / (trace_ms * 1e-3) / 1e9
     grays_frame = (primary_rays + shadow_rays) / (ms_frame_rank * 1e-3) / 1e9
     alg = algorithmic_bytes(w.scene.nt, w.scene.nv, G.info()["n4"], primary_rays, cam.width * cam.height,
-                            shadow_rays)
+                            shadow_rays, len(lights) * render_tasks(cam.width, cam.height, cam.spp))
     dom = max(avg, key=avg.get)
     peak, peak_kind = load_peaks()
     achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9

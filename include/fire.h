@@ -410,7 +410,8 @@ int fire_debug_fail_alloc(int32_t nth);
  * stage of the scene's calls (off by default; negligible cost when on).
  * Stages: 0 refit, 1 primary pass (raster or traversal), 2 shadow rays,
  * 3 build (up to the binary tree; the 4-wide collapse is not included),
- * 4 G-buffer shading, 5 shading backward, 6 shading + resolve.
+ * 4 G-buffer shading, 5 shading backward, 6 shading + resolve, 7 shadow
+ * queue ordering (between 1 and 2: the rays put in task order).
  * fire_profile_read synchronises the pending events and returns, per stage,
  * the summed milliseconds and the number of kernel launches since the last
  * read (then resets). */

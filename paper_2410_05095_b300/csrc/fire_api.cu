@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "fire_internal.cuh"
+#include "trace_device.cuh"
 
 namespace fire {
 
@@ -213,7 +213,7 @@ void free_scene(fire_scene_s* s) {
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
                   s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
                   s->blas_root, s->body_box, s->body_range, s->xf_ident, s->tlas_buf[0], s->tlas_buf[1],
-                  s->tinfo_buf[0], s->tinfo_buf[1], s->stage};
+                  s->tinfo_buf[0], s->tinfo_buf[1], s->stage, s->qperm, s->qaux};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int b = 0; b < 2; ++b) {
@@ -625,17 +625,39 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     if (int e = ensure_scratch(s, nsamp)) return e;
     a.g = s->gscratch;
   }
-  size_t njobs = nsamp * (size_t)std::max(1, nlights);
+  // shadow-ray queue: per light one segment of 32 slots per task of the
+  // full image (sparse, written by the primary pass), the dense order of its
+  // rays (task order, as slots), counts and offsets per task
+  const TaskGrid tg = make_grid(cam->width, 0, cam->height, cam->spp);
+  const size_t ntask_full = (size_t)tg.tiles_x * tg.tiles_y;
+  const size_t qseg = 32 * ntask_full;
+  size_t njobs = qseg * (size_t)std::max(1, nlights);
   if (s->jobs_n < njobs) {
     if (s->jobs) {
       cudaFree(s->jobs);
-      s->bytes -= s->jobs_n * 32;
+      cudaFree(s->qperm);
+      s->bytes -= s->jobs_n * 36;
     }
     s->jobs = nullptr;
+    s->qperm = nullptr;
     s->jobs_n = 0;
     if (cudaError_t e = dev_alloc((void**)&s->jobs, njobs * 32, &s->bytes)) return cuda_check(e, "shadow queue");
+    if (cudaError_t e = dev_alloc((void**)&s->qperm, njobs * 4, &s->bytes)) return cuda_check(e, "shadow queue order");
     s->jobs_n = njobs;
   }
+  const size_t nq = (size_t)std::max(1, nlights) * (ntask_full + (ntask_full + 1023) / 1024);
+  if (s->qaux_n < nq) {
+    if (s->qaux) {
+      cudaFree(s->qaux);
+      s->bytes -= s->qaux_n * 4;
+    }
+    s->qaux = nullptr;
+    s->qaux_n = 0;
+    if (cudaError_t e = dev_alloc((void**)&s->qaux, nq * 4, &s->bytes)) return cuda_check(e, "shadow queue counts");
+    s->qaux_n = nq;
+  }
+  a.qcnt = s->qaux;
+  a.qseg = (int64_t)qseg;
   // raster primary pass scratch: one key and one direction per sample, a
   // piece queue, a deferred-triangle list
   if ((o.flags & FIRE_RENDER_RASTER_PRIMARY) && s->rkeys_n < nsamp) {

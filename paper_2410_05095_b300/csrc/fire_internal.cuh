@@ -194,8 +194,11 @@ struct fire_scene_s {
   size_t pieces_n = 0;
   int32_t* graze = nullptr;        // raster deferred-triangle list
   size_t graze_n = 0;
-  float4* jobs = nullptr;          // shadow-ray queue, 32 B per ray
-  size_t jobs_n = 0;               // capacity in rays
+  float4* jobs = nullptr;          // shadow rays per task (sparse), 32 B per ray
+  int32_t* qperm = nullptr;        // per light: the queue in task order, as slots of the sparse segment
+  size_t jobs_n = 0;               // capacity in rays (each)
+  int32_t* qaux = nullptr;         // per light: ray counts [tasks]; then per light: block sums [tasks / 1024]
+  size_t qaux_n = 0;
   // two-level mode (fire_scene_set_two_level): bottom levels in
   // nodes4_buf[0] / tris_buf[0] (rest pose, built once), top level per frame
   // buffer
@@ -237,7 +240,7 @@ int make_lights(const fire_light* lights, int n, LightParams* out);
 
 // Stage profiler (fire_api.cu): event pairs around kernels, read lazily.
 enum Stage { kStageRefit = 0, kStagePrimary = 1, kStageShadow = 2, kStageBuild = 3, kStageShadeGbuf = 4,
-             kStageBackward = 5, kStageResolve = 6, kStages = 8 };
+             kStageBackward = 5, kStageResolve = 6, kStageQueue = 7, kStages = 8 };
 void prof_begin(fire_scene_s* s, int stage, cudaStream_t st);
 // launches: kernels launched between prof_begin and prof_end
 void prof_end(fire_scene_s* s, int stage, cudaStream_t st, int launches = 1);
@@ -272,6 +275,10 @@ struct RenderArgs {
   const uint16_t* vbody;
   fire_gbuffer_rec* g;          // per-sample records
   float* out;                   // [H*W*4]
+  // shadow-ray queue (single-frame path): light j's rays of task t sit at
+  // [j*qseg + 32t, +qcnt[j*ntasks + t]) of the primary pass's sparse queue
+  int32_t* qcnt;
+  int64_t qseg;                 // 32 x tasks of the full image
   // two-level mode (tlas != nullptr): top level, its record, each body's
   // bottom-level root; bxf holds the frame's body matrices
   const Node4* tlas;

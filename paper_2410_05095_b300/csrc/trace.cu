@@ -51,10 +51,11 @@ __device__ __forceinline__ void hit_frame_of(const RenderArgs& a, float4 B, floa
 }
 
 // Nearest hit per sample; writes the sample's record (prim, t, cast bits,
-// leaf position) and, for every light with n.l > 0 at the hit, appends a
-// shadow ray (lifted origin, unit direction, range, sample|light) to that
-// light's segment of a dense queue: one ballot per light, one atomicAdd per
-// warp, lanes ranked by the popcount of the lower lanes.
+// leaf position) and, for every light with n.l > 0 at the hit, a shadow ray
+// (lifted origin, unit direction, range, sample|light) into the task's own
+// 32 slots of that light's segment, lanes ranked by the popcount of the lower
+// lanes, and the task's count of rays per light (no atomics: the queue is
+// put in task order by k_qsum/k_qperm before the shadow pass).
 // MODE 0: traversal.  After a raster pass (raster.cu): MODE 1 traverses only
 // if that pass fell back, MODE 2 takes each sample's hit from its key
 // otherwise; exactly one of the two does the work.
@@ -111,13 +112,11 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
         want = dot3(n, l) > 0.0f;
       }
       unsigned m = __ballot_sync(kFull, want);
+      if (lane == 0) a.qcnt[(int64_t)j * ntasks + task] = __popc(m);  // every task and light
       if (m == 0) continue;
-      uint32_t base = 0;
-      if (lane == __ffs(m) - 1) base = atomicAdd(a.ctrl + kCtrlShadowLen + j, (uint32_t)__popc(m));
-      base = __shfl_sync(kFull, base, __ffs(m) - 1);
       if (want) {
         cast |= 1u << (8 + j);
-        int64_t slot = (int64_t)j * ((int64_t)a.cam.W * a.cam.H * a.cam.spp) + base + __popc(m & lower);
+        int64_t slot = (int64_t)j * a.qseg + 32 * (int64_t)task + __popc(m & lower);
         jobs[2 * slot] = make_float4(po.x, po.y, po.z, tmax);
         jobs[2 * slot + 1] = make_float4(l.x, l.y, l.z, __int_as_float((int)(sid * 8 + j)));
       }
@@ -127,8 +126,74 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
   }
 }
 
+// Task order of the shadow queue.  Per light, k_qsum adds up the tasks' ray
+// counts per block of 1024 tasks; k_qperm (one block per 1024 tasks) scans
+// its tasks' counts, starts at the sum of the earlier blocks' totals, and
+// writes its dense range in order, each position holding the sparse slot of
+// its ray (a warp writes its tasks' ranges one task at a time, one lane per
+// ray), so a warp of the shadow pass takes the rays of one or two
+// neighbouring 4x2-pixel tasks; the last block writes the light's ray count
+// to ctrl[24 + j].
+__global__ void __launch_bounds__(1024) k_qsum(const int32_t* __restrict__ cnt, int32_t* __restrict__ bsum, int ntasks,
+                                               int nblk) {
+  __shared__ int32_t wsum[32];
+  const int j = blockIdx.y, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int t = b * 1024 + tid;
+  int32_t v = t < ntasks ? cnt[(int64_t)j * ntasks + t] : 0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if (lane == 0) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int32_t y = wsum[lane];
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
+    if (lane == 0) bsum[(int64_t)j * nblk + b] = y;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_qperm(const int32_t* __restrict__ cnt, const int32_t* __restrict__ bsum,
+                                                int32_t* __restrict__ perm, uint32_t* __restrict__ len, int ntasks,
+                                                int nblk, int64_t qseg) {
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t sbase;
+  const int j = blockIdx.y, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (w == 0) {  // the earlier blocks' rays
+    int32_t y = 0;
+    for (int i = lane; i < b; i += 32) y += bsum[(int64_t)j * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
+    if (lane == 0) sbase = y;
+  }
+  const int t = b * 1024 + tid;
+  const int32_t v = t < ntasks ? cnt[(int64_t)j * ntasks + t] : 0;
+  int32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t y = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t z = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += z;
+    }
+    wsum[lane] = y;  // inclusive sums of the warps
+  }
+  __syncthreads();
+  const int32_t total = wsum[31], base = sbase;
+  const int32_t excl = x - v + (w ? wsum[w - 1] : 0);
+  int32_t* out = perm + (int64_t)j * qseg + base;
+  // the warp's tasks with rays, one after another, each written by its lanes
+  for (unsigned nz = __ballot_sync(kFull, v > 0); nz; nz &= nz - 1) {
+    const int k = __ffs(nz) - 1;
+    const int32_t c = __shfl_sync(kFull, v, k), o = __shfl_sync(kFull, excl, k);
+    if (lane < c) out[o + lane] = 32 * (b * 1024 + w * 32 + k) + lane;
+  }
+  if (b == nblk - 1 && tid == 0) len[j] = (uint32_t)(base + total);
+}
+
 // Shadow rays from the dense queue: one segment per light (light j's rays
-// from j * samples; lengths in ctrl[24 + j]), so a warp's 32 consecutive
+// from j * qseg; lengths in ctrl[24 + j]), so a warp's 32 consecutive
 // rays never mix lights (shadow 1.35 -> 1.33 ms on the 7.3M-triangle frame);
 // each warp takes 32 consecutive rays of the segments laid end to end (all
 // lanes busy until the tail); an unoccluded ray sets its light's bit in the
@@ -136,7 +201,8 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
 // every 16 node visits -- measured 7% slower: the idle lanes come from the
 // branches inside each node step, not from rays of different lengths.)
 template <int STACK, bool TWO>
-__global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs) {
+__global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __restrict__ jobs,
+                                                const int32_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31;
   TraceCtx c{a.nodes4, a.n4, TWO ? 0.0f : scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
   Trace2View c2{};
@@ -147,7 +213,7 @@ __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __re
     cnt[j] = j < a.lights.n ? a.ctrl[kCtrlShadowLen + j] : 0u;
     njobs += cnt[j];
   }
-  const int64_t seg = (int64_t)a.cam.W * a.cam.H * a.cam.spp;
+  const int64_t seg = a.qseg;
   int4* rec = reinterpret_cast<int4*>(a.g);
   while (true) {
     uint32_t base = 0;
@@ -162,7 +228,7 @@ __global__ void __launch_bounds__(128) k_shadow(RenderArgs a, const float4* __re
         off -= cnt[lj];
         ++lj;
       }
-      const int64_t js = (int64_t)lj * seg + off;
+      const int64_t js = (int64_t)lj * seg + __ldg(perm + (int64_t)lj * seg + off);
       float4 A = jobs[2 * js], B = jobs[2 * js + 1];
       int sj = __float_as_int(B.w);
       int64_t sid = sj >> 3;
@@ -449,8 +515,15 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
   }
   prof_end(s, kStagePrimary, st, raster ? (a.nt > 0 ? 6 : 3) : 1);
   if (a.lights.n > 0) {
+    prof_begin(s, kStageQueue, st);
+    const int nl = a.lights.n;
+    const int nblk = (ntasks + 1023) / 1024;
+    int32_t* bsum = a.qcnt + (int64_t)nl * ntasks;
+    k_qsum<<<dim3(nblk, nl), 1024, 0, st>>>(a.qcnt, bsum, ntasks, nblk);
+    k_qperm<<<dim3(nblk, nl), 1024, 0, st>>>(a.qcnt, bsum, s->qperm, a.ctrl + kCtrlShadowLen, ntasks, nblk, a.qseg);
+    prof_end(s, kStageQueue, st, 2);
     prof_begin(s, kStageShadow, st);
-    k_shadow<STACK, TWO><<<gs, threads, 0, st>>>(a, s->jobs);
+    k_shadow<STACK, TWO><<<gs, threads, 0, st>>>(a, s->jobs, s->qperm);
     prof_end(s, kStageShadow, st);
   }
   prof_begin(s, kStageResolve, st);

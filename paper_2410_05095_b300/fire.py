@@ -31,7 +31,7 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_scene_set_two_level", "fire_debug_trace_host", "fire_batch_last_tuning", "fire_last_error",
            "fire_version"]
 
-STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "unused7"]
+STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "queue"]
 
 
 class FireError(RuntimeError):

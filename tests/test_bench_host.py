@@ -38,16 +38,20 @@ def test_clock_summary_without_samples():
 
 
 def test_algorithmic_bytes_model():
-    nt, nv, n4, samples, pixels, rays = 1000, 600, 400, 80, 20, 30
-    b = bench.algorithmic_bytes(nt, nv, n4, samples, pixels, rays)
+    nt, nv, n4, samples, pixels, rays, counts = 1000, 600, 400, 80, 20, 30, 6
+    b = bench.algorithmic_bytes(nt, nv, n4, samples, pixels, rays, counts)
     tree = 128 * n4 + 48 * nt
-    assert b["shadow"] == tree + 40 * rays
-    assert b["primary"] == tree + 16 * samples + 32 * rays
+    assert b["shadow"] == tree + 44 * rays
+    assert b["primary"] == tree + 16 * samples + 32 * rays + 4 * counts
+    assert b["queue"] == 8 * counts + 4 * rays
     assert b["resolve"] == 48 * samples + 16 * pixels
     assert b["refit"] == 18 * nv + 96 * nt + 208 * n4
     # the headline frame: 7,299,072 triangles, 3,652,849 vertices
     full = bench.algorithmic_bytes(7_299_072, 3_652_849, 3_476_669, 8_294_400, 2_073_600, 3_842_521)
     assert 0.9e9 < full["shadow"] < 1.0e9
+    # 4 x 2-pixel tasks at 4 spp, 8 x 4 at 1 spp, ragged edges rounded up
+    assert bench.render_tasks(1920, 1080, 4) == 480 * 540
+    assert bench.render_tasks(5, 3, 4) == 2 * 2 and bench.render_tasks(9, 5, 1) == 2 * 2
 
 
 def test_committed_counters_are_per_launch_integers():
