@@ -79,6 +79,8 @@ def lib():
         L.orc_smith_g.argtypes = [C.c_double, C.c_double, C.c_double, i32]
         L.orc_shade_f64.argtypes = [P, P, P, i32, P, P, P, P, P, P]
         L.orc_grad_f64.argtypes = [P, P, P, i32, P, P, P, P, P, P, P, P]
+        L.orc_shade_f64_fresh.argtypes = [P, P, P, i32, P, P, P, P, P]
+        L.orc_shade_f64_fresh.restype = i32
         L.orc_shadow_eps.restype = C.c_float
         L.orc_shadow_eps.argtypes = [P]
         L.orc_display.argtypes = [P, i32, i32, C.c_float, i32, P, P]
@@ -272,6 +274,19 @@ class OracleScene:
         lib().orc_shade_f64(self.h, C.byref(c), C.cast(L, C.c_void_p), len(lights),
                             _p(samples["prim"]), _p(samples["t"]), _p(samples["vis"]),
                             _p(params), _p(inten), _p(img))
+        return img
+
+    def shade_f64_fresh(self, cam, lights, samples, params, inten):
+        """shade_f64 with the hit frame recomputed in FP64 from the camera ray
+        and the world triangle (flat normals, single-level scenes)."""
+        c, L = make_camera(cam), make_lights(lights)
+        params = np.ascontiguousarray(params, np.float64).reshape(-1)
+        inten = np.ascontiguousarray(inten, np.float64)
+        img = np.zeros((cam.height, cam.width, 3), np.float64)
+        r = lib().orc_shade_f64_fresh(self.h, C.byref(c), C.cast(L, C.c_void_p), len(lights),
+                                      _p(samples["prim"]), _p(samples["vis"]), _p(params), _p(inten), _p(img))
+        if r != 0:
+            raise ValueError("FP64 frame from scratch: flat normals and single-level scenes only")
         return img
 
     def grad_f64(self, cam, lights, samples, params, inten, dimg):

@@ -833,6 +833,56 @@ bool geo64(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, 
   return true;
 }
 
+// The same cosines from an FP64 hit frame recomputed from the FP32 inputs
+// alone (the camera ray and the world triangle, widened): t by
+// Moller-Trumbore in FP64, p = o + t d, n = normalize(e1 x e2) facing the
+// ray, po = p + eps n, v = normalize(-d), the light vector, h, the cosines
+// and 1/d^2 in FP64.  It owes nothing to the FP32 frame beyond those inputs,
+// so it checks the reading that holds the geometry at that frame (flat
+// normals, single-level scenes; visibility stays the forward's).
+bool geo64_fresh(const orc_scene& S, const Cam& K, const orc_light* L, int nl, int x, int y, int s,
+                 int32_t prim, uint16_t vis, Geo64& G) {
+  if (prim < 0) return false;
+  const D3 o = tod(K.o), d = tod(cam_dir(K, x, y, s));
+  V3 a32, b32, c32;
+  tri_verts(S, prim, a32, b32, c32);
+  const D3 a = tod(a32), e1 = dsub(tod(b32), a), e2 = dsub(tod(c32), a);
+  const D3 pv = dcross(d, e2);
+  const double det = ddot(e1, pv);
+  if (det == 0.0) return false;
+  const D3 q = dcross(dsub(o, a), e1);
+  const double t = ddot(e2, q) / det;
+  const D3 p = dk(o.x + t * d.x, o.y + t * d.y, o.z + t * d.z);
+  D3 n = dnorm(dcross(e1, e2));
+  if (ddot(n, d) > 0.0) n = dk(-n.x, -n.y, -n.z);
+  const double eps = scene_eps(S);
+  const D3 po = dk(p.x + eps * n.x, p.y + eps * n.y, p.z + eps * n.z);
+  const D3 v = dnorm(dk(-d.x, -d.y, -d.z));
+  G.nlights = nl;
+  for (int j = 0; j < nl; ++j) {
+    D3 l;
+    double g = 1.0;
+    if (L[j].type == 0) {
+      const D3 lv = dsub(dk(L[j].v[0], L[j].v[1], L[j].v[2]), po);
+      const double d2 = ddot(lv, lv);
+      l = dnorm(lv);
+      g = 1.0 / d2;
+    } else {
+      l = dnorm(dk(L[j].v[0], L[j].v[1], L[j].v[2]));
+    }
+    const D3 h = dnorm(dk(l.x + v.x, l.y + v.y, l.z + v.z));
+    Cos64& c = G.c[j];
+    const double ndl = ddot(n, l);
+    c.lit = ((vis >> j) & 1u) && ndl > 0.0;
+    c.nl = std::max(ndl, 0.0);
+    c.nv = std::max(ddot(n, v), 0.0);
+    c.nh = std::max(ddot(n, h), 0.0);
+    c.vh = std::max(ddot(v, h), 0.0);
+    c.g = g;
+  }
+  return true;
+}
+
 // f_c and its derivatives d/d albedo_c, d/d rough, d/d metal (kmode 0), FP64,
 // at fixed cosines.  dd is formed as (1-nh)(1+nh) + nh^2 a2 (no cancellation).
 struct Brdf64 { double f[3], dalb[3], dr[3], dm[3]; };
@@ -1068,9 +1118,9 @@ void orc_brdf_f64(const double* n, const double* v, const double* l, const doubl
 
 float orc_shadow_eps(const orc_scene* s) { return scene_eps(*s); }
 
-void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
-                   const int32_t* prim, const float* t, const uint16_t* vis,
-                   const double* params, const double* inten, double* img) {
+static void shade_f64_rows(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                           const int32_t* prim, const float* t, const uint16_t* vis,
+                           const double* params, const double* inten, bool fresh, double* img) {
   Cam K = make_cam(c);
   for (int y = 0; y < K.H; ++y)
     for (int x = 0; x < K.W; ++x) {
@@ -1078,7 +1128,9 @@ void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, 
       for (int k = 0; k < K.spp; ++k) {
         int64_t id = ((int64_t)y * K.W + x) * K.spp + k;
         Geo64 G;
-        if (!geo64(*s, K, L, nl, x, y, k, prim[id], t[id], vis[id], G)) continue;
+        if (!(fresh ? geo64_fresh(*s, K, L, nl, x, y, k, prim[id], vis[id], G)
+                    : geo64(*s, K, L, nl, x, y, k, prim[id], t[id], vis[id], G)))
+          continue;
         const double* P = params + 5 * s->tri_mat[prim[id]];
         for (int j = 0; j < nl; ++j) {
           if (!G.c[j].lit) continue;
@@ -1088,6 +1140,20 @@ void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, 
       }
       for (int ch = 0; ch < 3; ++ch) img[3 * ((int64_t)y * K.W + x) + ch] = acc[ch] / K.spp;
     }
+}
+
+void orc_shade_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                   const int32_t* prim, const float* t, const uint16_t* vis,
+                   const double* params, const double* inten, double* img) {
+  shade_f64_rows(s, c, L, nl, prim, t, vis, params, inten, false, img);
+}
+
+int32_t orc_shade_f64_fresh(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                            const int32_t* prim, const uint16_t* vis, const double* params,
+                            const double* inten, double* img) {
+  if (s->two_level || !s->vnrm.empty()) return -1;
+  shade_f64_rows(s, c, L, nl, prim, nullptr, vis, params, inten, true, img);
+  return 0;
 }
 
 void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,

@@ -106,6 +106,13 @@ void orc_grad_f64(const orc_scene* s, const orc_camera* c, const orc_light* L, i
                   const double* params, const double* inten, const double* dimg,
                   double* dparams, double* dinten);
 
+/* orc_shade_f64 with the hit frame recomputed in FP64 from the camera ray
+ * and the world triangle (t, p, n, po, v, l, h, 1/d^2 all FP64; visibility
+ * from vis).  Flat normals and single-level scenes only: -1 otherwise. */
+int32_t orc_shade_f64_fresh(const orc_scene* s, const orc_camera* c, const orc_light* L, int32_t nl,
+                            const int32_t* prim, const uint16_t* vis, const double* params,
+                            const double* inten, double* img);
+
 /* Shadow-ray offset epsilon = 1e-4 * scene-box diagonal. */
 float orc_shadow_eps(const orc_scene* s);
 

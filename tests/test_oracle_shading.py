@@ -278,3 +278,60 @@ def test_fp32_render_matches_fp64_shading():
     img32 = S.render_image(cam, lights)[..., :3]
     rel = np.abs(img32 - img64) / np.maximum(np.abs(img64), 1e-6)
     assert np.max(rel) < 1e-3 and np.median(rel[img64 > 1e-3]) < 1e-5, (rel.max(),)
+
+
+def test_fresh_fp64_frame_closed_form():
+    """shade_f64_fresh on the quad under the camera: each pixel is
+    (f_d + f_s) I cos(theta) g at the exact FP64 ray/plane point (g = 1/d^2
+    for the point light, 1 for the directional one), the shadow origin lifted
+    by eps along the plane's normal; FP64 agreement (1e-9 relative)."""
+    sc = _plane_scene(np.zeros((0, 3, 3)))
+    sc.mats[0]["albedo"] = [0.5, 0.3, 0.2]
+    sc.mats[0]["roughness"], sc.mats[0]["metallic"] = 0.35, 0.4
+    S = oracle.OracleScene(sc)
+    S.update(np.eye(3, 4, dtype=np.float32).reshape(1, 12), rebuild=True)
+    cam = sg.Camera((0.37, 10.0, 0.21), (0.37, 0.0, 0.21), (0.0, 0.0, -1.0), 60.0, 17, 13, 1)
+    lights = [sg.Light(0, (3.0, 8.0, -2.0), 100.0), sg.Light(1, (0.3, 1.0, 0.2), 2.0)]
+    samples = S.render_all_samples(cam, lights)
+    assert np.all(samples["prim"] >= 0)
+    P = oracle.params_of(sc.mats)
+    I = np.array([100.0, 2.0])
+    img = S.shade_f64_fresh(cam, lights, samples, P, I)
+    eps = float(S.shadow_eps())
+    n = np.array([0.0, 1.0, 0.0])
+    worst = 0.0
+    for y in range(cam.height):
+        for x in range(cam.width):
+            o, d = (a.astype(np.float64) for a in oracle.camera_ray(cam, x, y, 0))
+            p = o + (-o[1] / d[1]) * d
+            po = p + eps * n
+            v = -d / np.linalg.norm(d)
+            want = np.zeros(3)
+            vis = int(samples["vis"][y * cam.width + x])
+            for j, L in enumerate(lights):
+                if L.type == 0:
+                    lv = np.array(L.v, np.float32).astype(np.float64) - po
+                    g, l = 1.0 / (lv @ lv), lv / np.linalg.norm(lv)
+                else:
+                    lv = np.array(L.v, np.float32).astype(np.float64)  # the light record is FP32
+                    g, l = 1.0, lv / np.linalg.norm(lv)
+                if not (vis >> j) & 1:
+                    continue
+                fd, fs = oracle.brdf_f64(n, v, l, P[0, :3], P[0, 3], P[0, 4])  # (params_of rounds to FP32)
+                want += (fd + fs) * I[j] * l[1] * g
+            worst = max(worst, float(np.max(np.abs(img[y, x] - want) / want)))
+    assert worst < 1e-9, worst
+
+
+def test_fresh_fp64_frame_near_fp32_frame():
+    """On the tiny scene the FP64 frame from scratch and the FP32 frame give
+    the same image to FP32 frame precision (GGX peaks amplify the angle
+    rounding, hence the 1e-3 bound on the largest difference)."""
+    w, cam, lights, S, samples = _grad_setup(4, 24, 24)
+    P0 = oracle.params_of(w.scene.mats)
+    I0 = np.array([l.intensity for l in lights], np.float64)
+    a = S.shade_f64(cam, lights, samples, P0, I0)
+    b = S.shade_f64_fresh(cam, lights, samples, P0, I0)
+    rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-6)
+    assert np.max(rel) < 1e-3 and np.median(rel[b > 1e-3]) < 1e-5, (rel.max(),)
+    assert np.count_nonzero(b) > 100
