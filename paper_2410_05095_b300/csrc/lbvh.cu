@@ -1147,6 +1147,7 @@ int lbvh_count_mixed(fire_scene_s* s, cudaStream_t st, uint32_t* bad_host) {
 int lbvh_build(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) { s->built = true; s->height = 0; return FIRE_OK; }
+  s->built = false;  // until this build has completed
   // bounds live in ctrl[9..14]: lo = +inf ordered, hi = -inf ordered
   uint32_t init[6];
   for (int k = 0; k < 3; ++k) { init[k] = 0xffffffffu; init[3 + k] = 0u; }

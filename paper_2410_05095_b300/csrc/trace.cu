@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
       } else if (TWO) {
         traverse2<DeviceLoads, STACK, false>(c2, o, d, 0.0f, -1, prim, pos, t);
       } else {
-        trace_nearest_oct<STACK>(c, o, d, prim, pos, t);
+        trace_nearest<STACK>(c, o, d, prim, pos, t);
       }
       if (prim >= 0) {
         float4 B = __ldg(a.tris + 3 * (int64_t)pos + 1), C = __ldg(a.tris + 3 * (int64_t)pos + 2);

@@ -213,19 +213,6 @@ __host__ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, in
   va = tv;
 }
 
-// Near/far plane members of a node for the ray's direction octant OCT (bit
-// 0: x < 0, bit 1: y < 0, bit 2: z < 0): compile-time offsets for 0..7, the
-// ray set-up's for -1.
-template <int OCT>
-struct Planes {
-  __device__ __forceinline__ static int nx(const RaySetup& r) { return OCT < 0 ? r.nx : (OCT & 1) ? 3 : 0; }
-  __device__ __forceinline__ static int ny(const RaySetup& r) { return OCT < 0 ? r.ny : (OCT & 2) ? 4 : 1; }
-  __device__ __forceinline__ static int nz(const RaySetup& r) { return OCT < 0 ? r.nz : (OCT & 4) ? 5 : 2; }
-  __device__ __forceinline__ static int fx(const RaySetup& r) { return OCT < 0 ? r.fx : (OCT & 1) ? 0 : 3; }
-  __device__ __forceinline__ static int fy(const RaySetup& r) { return OCT < 0 ? r.fy : (OCT & 2) ? 1 : 4; }
-  __device__ __forceinline__ static int fz(const RaySetup& r) { return OCT < 0 ? r.fz : (OCT & 4) ? 2 : 5; }
-};
-
 // Stack traversal of the 4-wide tree (collapsed from the Karras binary
 // tree), nearest child first (any hit: farthest first).  One node fetch (7 x 16 B) tests all four child
 // boxes; leaf children (one triangle each) are tested at once, so the
@@ -238,15 +225,15 @@ struct Planes {
 //   else: nearest hit in (0, inf) by (t, original index) -- independent of
 //         the visiting order; prim = original index (-1 = miss), pos = sorted
 //         position, tb = t.
-//   OCT:  -1 = the near/far plane members read from the ray set-up; 0..7 =
-//         the ray's direction octant fixed at compile time, so the six plane
-//         loads take constant offsets from the node's address.
-
-template <int STACK, bool ANY, int OCT>
-__device__ __forceinline__ bool traverse_loop(const TraceCtx& c, const RaySetup& r, float3 o, float3 d, float tmax,
-                                              int skip, int& prim, int& pos, float& tb) {
-  using P = Planes<OCT>;
+template <int STACK, bool ANY>
+__device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, float tmax, int skip, int& prim,
+                                         int& pos, float& tb) {
+  prim = -1;
+  pos = -1;
+  tb = ANY ? tmax : inf_f();
+  if (c.nt == 0) return false;
   const uint32_t n4 = (uint32_t)c.n4;
+  const RaySetup r = ray_setup(o, d, c.span);
   int stack[STACK];
   stack[0] = kDone;
   int sp = 1;
@@ -262,8 +249,8 @@ __device__ __forceinline__ bool traverse_loop(const TraceCtx& c, const RaySetup&
       return false;
     }
     const float4* m = &c.nodes4[cur].lox;  // lox loy loz hix hiy hiz link
-    const float4 nx = __ldg(m + P::nx(r)), ny = __ldg(m + P::ny(r)), nz = __ldg(m + P::nz(r));
-    const float4 fx = __ldg(m + P::fx(r)), fy = __ldg(m + P::fy(r)), fz = __ldg(m + P::fz(r));
+    const float4 nx = __ldg(m + r.nx), ny = __ldg(m + r.ny), nz = __ldg(m + r.nz);
+    const float4 fx = __ldg(m + r.fx), fy = __ldg(m + r.fy), fz = __ldg(m + r.fz);
     const int4 lk = __ldg(reinterpret_cast<const int4*>(m + 6));
     float k0, k1, k2, k3;
     int v0 = lk.x, v1 = lk.y, v2 = lk.z, v3 = lk.w;
@@ -327,45 +314,6 @@ __device__ __forceinline__ bool traverse_loop(const TraceCtx& c, const RaySetup&
   return false;
 }
 
-template <int STACK, bool ANY>
-__device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, float tmax, int skip, int& prim,
-                                         int& pos, float& tb) {
-  prim = -1;
-  pos = -1;
-  tb = ANY ? tmax : inf_f();
-  if (c.nt == 0) return false;
-  const RaySetup r = ray_setup(o, d, c.span);
-  return traverse_loop<STACK, ANY, -1>(c, r, o, d, tmax, skip, prim, pos, tb);
-}
-
-// The same traversal with the direction octant fixed at compile time when
-// all active lanes of the warp share it (one of eight copies of the loop),
-// the generic loop otherwise.  (k_primary on the 7.3M-triangle frame: 1.014
-// -> 0.977 ms; k_shadow gains nothing: it needs 68 registers with the eight
-// copies, and capped at 64 it runs as before.)
-template <int STACK, bool ANY>
-__device__ __forceinline__ bool traverse_oct(const TraceCtx& c, float3 o, float3 d, float tmax, int skip, int& prim,
-                                             int& pos, float& tb) {
-  prim = -1;
-  pos = -1;
-  tb = ANY ? tmax : inf_f();
-  if (c.nt == 0) return false;
-  const RaySetup r = ray_setup(o, d, c.span);
-  const int oct = (r.inv.x < 0.0f ? 1 : 0) | (r.inv.y < 0.0f ? 2 : 0) | (r.inv.z < 0.0f ? 4 : 0);
-  const unsigned act = __activemask();
-  if (__match_any_sync(act, oct) != act) return traverse_loop<STACK, ANY, -1>(c, r, o, d, tmax, skip, prim, pos, tb);
-  switch (oct) {
-    case 0: return traverse_loop<STACK, ANY, 0>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 1: return traverse_loop<STACK, ANY, 1>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 2: return traverse_loop<STACK, ANY, 2>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 3: return traverse_loop<STACK, ANY, 3>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 4: return traverse_loop<STACK, ANY, 4>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 5: return traverse_loop<STACK, ANY, 5>(c, r, o, d, tmax, skip, prim, pos, tb);
-    case 6: return traverse_loop<STACK, ANY, 6>(c, r, o, d, tmax, skip, prim, pos, tb);
-    default: return traverse_loop<STACK, ANY, 7>(c, r, o, d, tmax, skip, prim, pos, tb);
-  }
-}
-
 template <int STACK>
 __device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float3 d, int& prim, int& pos,
                                               float& tb) {
@@ -377,19 +325,6 @@ __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d,
   int prim, pos;
   float tb;
   return traverse<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
-}
-
-template <int STACK>
-__device__ __forceinline__ void trace_nearest_oct(const TraceCtx& c, float3 o, float3 d, int& prim, int& pos,
-                                                  float& tb) {
-  traverse_oct<STACK, false>(c, o, d, 0.0f, -1, prim, pos, tb);
-}
-
-template <int STACK>
-__device__ __forceinline__ bool trace_any_oct(const TraceCtx& c, float3 o, float3 d, float tmax, int skip) {
-  int prim, pos;
-  float tb;
-  return traverse_oct<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
 }
 
 // ---------------------------------------------------------------------------
