@@ -481,8 +481,8 @@ def main():
                     help="oracle samples per host thread per reference step")
     ap.add_argument("--no-side", action="store_true", help="skip the batched and backward side runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    ap.add_argument("--render-bps", type=int, default=7,
-                    help="blocks per SM of the primary pass in the pipelined frames (0 = occupancy limit; 7 leaves room for the next frame's refit blocks beside it)")
+    ap.add_argument("--render-bps", type=int, default=6,
+                    help="blocks per SM of the primary pass in the pipelined frames (0 = occupancy limit; 6 leaves room for the next frame's refit blocks beside it)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = env_rank()
