@@ -107,7 +107,7 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------- roofline
-KERNEL_NAMES = {"refit": "k_refit4_leaves+k_refit4_level+k_refit4_small", "primary": "k_primary",
+KERNEL_NAMES = {"refit": "k_refit_leaves+k_refit_tl+k_refit_top", "primary": "k_primary",
                 "queue": "k_qsum+k_qperm", "shadow": "k_shadow", "resolve": "k_shade<resolve>"}
 
 
@@ -122,10 +122,10 @@ def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shad
     """Minimum bytes each kernel family must move per frame
     (queue_counts = lights x tasks):
     refit   -- read rest vertices (16 B) + body ids (2 B) per vertex, the
-               sorted index record (16 B), material (4 B) and 4-wide lane
-               (4 B) per triangle; write the 48-B triangle record and the
-               24-B leaf box; per 4-wide node read its 112-B boxes+links once
-               (by its parent) and write its 96 B of boxes once
+               sorted index record (16 B) and material (4 B) per triangle;
+               write its 48-B record and its 24-B box, read the box back
+               (its treelet); per 4-wide node read its 8-B list entry and
+               16-B child slots and write its 96 B of boxes once
     primary -- read the traversal tree once (128 B per 4-wide node + 48 B
                per triangle) + write a 16-B record per sample, a 32-B
                queued shadow ray and a 4-B ray count per task and light
@@ -136,7 +136,7 @@ def algorithmic_bytes(nt: int, nv: int, n4: int, samples: int, pixels: int, shad
     resolve -- read the 16-B record per sample + 32 B of its triangle for the
                hit frame + write a 16-B pixel."""
     tree = 128 * n4 + 48 * nt
-    return {"refit": nv * 18 + nt * (16 + 4 + 4 + 48 + 24) + n4 * (112 + 96),
+    return {"refit": nv * 18 + nt * (16 + 4 + 48 + 24 + 24) + n4 * (8 + 16 + 96),
             "primary": tree + 16 * samples + 32 * shadow_rays + 4 * queue_counts,
             "queue": 8 * queue_counts + 4 * shadow_rays,
             "shadow": tree + 44 * shadow_rays,
@@ -481,8 +481,8 @@ def main():
                     help="oracle samples per host thread per reference step")
     ap.add_argument("--no-side", action="store_true", help="skip the batched and backward side runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    ap.add_argument("--render-bps", type=int, default=6,
-                    help="blocks per SM of the primary pass in the pipelined frames (0 = occupancy limit; 6 leaves room for the next frame's refit blocks beside it)")
+    ap.add_argument("--render-bps", type=int, default=7,
+                    help="blocks per SM of the primary pass in the pipelined frames (0 = occupancy limit; 7 leaves room for the next frame's refit blocks beside it)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, local_rank, world = env_rank()

@@ -211,9 +211,10 @@ void free_scene(fire_scene_s* s) {
                   s->sidx, s->smat, s->nodes, s->leaf_slot, s->node_slot, s->counters, s->tris_buf[0],
                   s->tris_buf[1], s->nodes4_buf[0], s->nodes4_buf[1], s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
-                  s->leaf_slot4, s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
+                  s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
                   s->blas_root, s->body_box, s->body_range, s->xf_ident, s->tlas_buf[0], s->tlas_buf[1],
-                  s->tinfo_buf[0], s->tinfo_buf[1], s->stage, s->qperm, s->qaux};
+                  s->tinfo_buf[0], s->tinfo_buf[1], s->stage, s->qperm, s->qaux, s->tl_node, s->tl_refs,
+                  s->tl_info, s->tl_top, s->tl_grp, s->nunion, s->tl_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int b = 0; b < 2; ++b) {
@@ -261,8 +262,13 @@ int alloc_lbvh(fire_scene_s* s) {
       {(void**)&s->tris_buf[1], 48 * (size_t)T},
       {(void**)&s->cen, 16 * (size_t)T},          {(void**)&s->keys_alt, 8 * (size_t)T},
       {(void**)&s->vals_alt, 4 * (size_t)T},      {(void**)&s->hist, 4 * (size_t)(kSortBins * (ntiles + 1))},
-      {(void**)&s->leaf_slot4, 4 * (size_t)T},     {(void**)&s->rank, 4 * (size_t)T},
+      {(void**)&s->rank, 4 * (size_t)T},
       {(void**)&s->stage, 24 * (size_t)T},
+      {(void**)&s->tl_node, 8 * (size_t)T},       {(void**)&s->tl_refs, 16 * (size_t)T},
+      {(void**)&s->tl_info, 16 * (size_t)T},
+      {(void**)&s->tl_top, 4 * (size_t)T},        {(void**)&s->tl_grp, 8 * (size_t)(kMaxDepth4 + 1)},
+      {(void**)&s->nunion, 24 * (size_t)T},
+      {(void**)&s->tl_scratch, 4 * (12 * (size_t)T + (size_t)T / 1024 + 64 + kMaxDepth4)},
       {(void**)&s->lvl_aux, 12 * (size_t)kMaxDepth4 + 16},
       {(void**)&s->nodes4_buf[0], 128 * (size_t)std::max<int64_t>(T, 1)},
       {(void**)&s->nodes4_buf[1], 128 * (size_t)std::max<int64_t>(T, 1)},

@@ -49,9 +49,6 @@ struct __align__(16) Node4 {
 };
 static_assert(sizeof(Node4) == 128, "4-wide node must be 128 bytes");
 constexpr int kEmptyLink = (int)0x80000000;
-// leaf_slot4 flag: the leaf's 4-wide node also has internal members (the
-// refit stages the leaf's box; 4 x node + lane stays below 2^30)
-constexpr int32_t kSlotMixed = 1 << 30;
 
 // Triangle record in leaf (sorted) order, 48 B:
 //   v0.xyz, w = original triangle index (bits)
@@ -154,8 +151,18 @@ struct fire_scene_s {
   uint8_t* lvl_aux = nullptr;   // device: 4-wide depth starts (i64 [kMaxDepth4]), collapse queue
                                 //   lengths (u32 [kMaxDepth4]) and the node counter (u32)
   std::vector<int64_t> lvl4;    // host: 4-wide nodes of depth L are [lvl4[L], lvl4[L+1])
-  int32_t* leaf_slot4 = nullptr;// [nt] 4 * (4-wide node) + lane of each leaf (| kSlotMixed)
-  float* stage = nullptr;       // [nt*6] refit: boxes of the leaves in mixed nodes (sorted order)
+  float* stage = nullptr;       // [nt*6] refit: every leaf's box (sorted order)
+  // treelet refit (single-level; lbvh.cu)
+  int2* tl_node = nullptr;      // [nt] per list slot: 4-wide node, depth below its treelet root
+  int4* tl_refs = nullptr;      // [nt] per list slot: children (list slot, ~leaf offset, kEmptyLink)
+  int4* tl_info = nullptr;      // [nt] per treelet: list offset, nodes | max depth << 16, first, last leaf
+  int32_t* tl_top = nullptr;    // [nt] top nodes (above the treelets), deepest depth first
+  int64_t* tl_grp = nullptr;    // [kMaxDepth4 + 1] top-list start of each depth
+  float* nunion = nullptr;      // [nt*6] union box of each treelet root and top node, by 4-wide node
+  int32_t* tl_scratch = nullptr;// build scratch [12*nt + nt/1024 + 64 + kMaxDepth4]
+  int ntl = 0;                  // treelets
+  int64_t norphan = 0;          // leaves whose parent is a top node
+  std::vector<int64_t> tl_grp_host;  // host copy of tl_grp
   fire::Node4* nodes4 = nullptr;// [max(nt, 1)] 4-wide traversal tree (current buffer)
   int64_t n4 = 0;               // 4-wide nodes in use
   int height4 = 0;              // 4-wide levels
@@ -248,6 +255,7 @@ void prof_end(fire_scene_s* s, int stage, cudaStream_t st, int launches = 1);
 // lbvh.cu
 int lbvh_build(fire_scene_s* s, cudaStream_t st);
 int lbvh_refit(fire_scene_s* s, cudaStream_t st);
+int treelet_build(fire_scene_s* s, cudaStream_t st);
 // two-level mode: top level of the current frame buffer from s->xf (one
 // block; also copies the matrices into the buffer's xf_buf)
 int tlas_build(fire_scene_s* s, cudaStream_t st);

@@ -465,8 +465,7 @@ __device__ __forceinline__ float box_area(float4 a, float4 b) {  // sector: lo x
 
 __device__ __forceinline__ void collapse_one(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs,
                                              uint32_t i, int32_t* __restrict__ out_pairs, uint32_t* nout,
-                                             uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4,
-                                             int32_t* __restrict__ leaf_slot4, int64_t nt) {
+                                             uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4) {
   const int b = in_pairs[2 * i], q = in_pairs[2 * i + 1];
   int link[4] = {kEmptyLink, kEmptyLink, kEmptyLink, kEmptyLink}, src[4] = {-1, -1, -1, -1};
   float area[4] = {0, 0, 0, 0};
@@ -497,8 +496,6 @@ __device__ __forceinline__ void collapse_one(const Node* __restrict__ nodes, con
   int out[4];
   for (int k = 0; k < 4; ++k) {
     out[k] = link[k];
-    if (k < m && link[k] < 0 && link[k] != kEmptyLink && (int64_t)~link[k] < nt)
-      leaf_slot4[~link[k]] = 4 * q + k;  // where the per-frame refit puts this leaf's box
     if (k < m && link[k] >= 0) {
       const uint32_t q2 = atomicAdd(alloc, 1u);  // 4-wide node index
       if (q2 >= cap4) {                          // never: a 4-wide node consumes >= 1 binary node
@@ -522,14 +519,13 @@ __device__ __forceinline__ void collapse_one(const Node* __restrict__ nodes, con
 // host launches one fixed grid per depth without reading the length back.
 __global__ void k_collapse(const Node* __restrict__ nodes, const int32_t* __restrict__ in_pairs,
                            const uint32_t* __restrict__ nin_p, int32_t* __restrict__ out_pairs, uint32_t* nout,
-                           uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4,
-                           int32_t* __restrict__ leaf_slot4, int64_t nt) {
+                           uint32_t* alloc, Node4* __restrict__ nodes4, int64_t cap4) {
   const uint32_t nin = *nin_p;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nin; i += gridDim.x * blockDim.x)
-    collapse_one(nodes, in_pairs, i, out_pairs, nout, alloc, nodes4, cap4, leaf_slot4, nt);
+    collapse_one(nodes, in_pairs, i, out_pairs, nout, alloc, nodes4, cap4);
 }
 
-// Per frame: copy each member's box from its binary slot (whole 32-B sector
+// At build: copy each member's box from its binary slot (whole 32-B sector
 // reads, 112-B node writes).
 __global__ void __launch_bounds__(256) k_fill4(const Node* __restrict__ nodes, Node4* __restrict__ nodes4, int64_t n4) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -592,8 +588,7 @@ __global__ void __launch_bounds__(1024) k_body_roots(const uint64_t* __restrict_
                                                      const int32_t* __restrict__ range, int nbody,
                                                      const int32_t* __restrict__ leaf_slot,
                                                      int32_t* __restrict__ blas_root, int32_t* __restrict__ pairs,
-                                                     uint32_t* __restrict__ qlen, Node4* __restrict__ nodes4,
-                                                     int32_t* __restrict__ leaf_slot4) {
+                                                     uint32_t* __restrict__ qlen, Node4* __restrict__ nodes4) {
   __shared__ int32_t scan_a[1024], scan_m[1024];
   const int b = threadIdx.x;
   int32_t f = -1, l = -1;
@@ -637,7 +632,6 @@ __global__ void __launch_bounds__(1024) k_body_roots(const uint64_t* __restrict_
     n->hiz = n->hix;
     n->link = make_int4(~f, kEmptyLink, kEmptyLink, kEmptyLink);
     n->src = make_int4(slot, -1, -1, -1);
-    leaf_slot4[f] = 4 * q;
     return;
   }
   int32_t root;
@@ -969,137 +963,407 @@ __global__ void __launch_bounds__(1024) k_tlas(const float* __restrict__ xf, int
 }
 
 // ----------------------------------------------------------------------------
-// Per-frame refit of the 4-wide tree.  The collapse numbers the 4-wide nodes
-// depth by depth, so each depth is a contiguous index range whose children
-// all lie in the next one.
-//   k_refit4_leaves  one thread per leaf: transform, 48-B record, leaf box
-//                    into its 4-wide slot
-//   k_refit4_level   nodes of one depth, deepest first: each internal
-//                    child's box = union of that child's four boxes (unused
-//                    slots hold the inverted infinite box, neutral for
-//                    min/max); the node is rewritten whole
-//   k_refit4_small   one block runs a run of small depths in order,
-//                    __syncthreads() between them
-// Min/max are exact, so every box equals the min/max over its triangles'
-// vertices bit for bit.
+// Per-frame refit of the 4-wide tree, by treelets.  At build the tree is cut
+// into treelets -- the largest subtrees of at most kTlNodes 4-wide nodes (a
+// treelet root has at most kTlNodes nodes in its subtree, its parent more)
+// -- and the top nodes above them.  A treelet's leaves are one contiguous
+// range of sorted triangles (a subtree of the radix tree covers a key
+// range), so each frame
+//   1. k_refit_leaves writes every triangle's 48-B record and its box
+//      (`stage`, 24 B per leaf, coalesced);
+//   2. k_refit_tl, one warp per treelet, reads its leaves' boxes (one
+//      range) and writes its nodes deepest first, each node's six child-box
+//      vectors whole (96 B), from the leaf boxes and the unions of its
+//      internal children in shared memory; the treelet root's union goes to
+//      nunion;
+//   3. the top nodes, deepest depth first, from nunion and `stage`.
+// Each node is written once, whole, and no node's boxes are read back.  Min/max are
+// exact, so every box equals the min/max over its triangles' vertices bit
+// for bit.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_refit4_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
-                                                       const float* __restrict__ xf, const uint4* __restrict__ sidx,
-                                                       const uint32_t* __restrict__ smat, int64_t nt,
-                                                       float4* __restrict__ tris, Node4* __restrict__ nodes4,
-                                                       const int32_t* __restrict__ leaf_slot4, int64_t n4,
-                                                       float* __restrict__ xfb, int nxf, float* __restrict__ stage) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < nxf) xfb[i] = xf[i];  // the frame buffer's copy of the body matrices
-  if (i >= nt) return;
-  uint4 id = sidx[i];
-  float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
-  float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
-  float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
-  float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
-  tris[3 * i] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
-  tris[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[i]));
-  tris[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
-  float3 lo = fmin3(w0, fmin3(w1, w2)), hi = fmax3(w0, fmax3(w1, w2));
-  const int32_t ls = leaf_slot4[i];
-  if (ls < 0) return;  // never for a complete collapse
-  if (ls & kSlotMixed) {
-    // a node with internal members too: its level pass writes it whole,
-    // taking this box from the staging array (6 consecutive floats per
-    // leaf, coalesced) -- no partial sector of the node is written here
-    float* b = stage + 6 * i;
-    b[0] = lo.x;
-    b[1] = lo.y;
-    b[2] = lo.z;
-    b[3] = hi.x;
-    b[4] = hi.y;
-    b[5] = hi.z;
-    return;
-  }
-  if ((ls >> 2) >= n4) return;  // never for a complete collapse
-  float* n = reinterpret_cast<float*>(nodes4 + (ls >> 2));
-  const int lanes = nt == 1 ? 2 : 1;  // a single triangle sits in two slots of the root
-  for (int k = 0; k < lanes; ++k) {
-    const int c = (ls & 3) + k;
-    n[0 + c] = lo.x;
-    n[4 + c] = lo.y;
-    n[8 + c] = lo.z;
-    n[12 + c] = hi.x;
-    n[16 + c] = hi.y;
-    n[20 + c] = hi.z;
+constexpr int kTlNodes = 32;                 // nodes per treelet, at most (= one warp)
+constexpr int kTlLeaves = 3 * kTlNodes + 1;  // leaves of a 4-wide subtree of kTlNodes nodes, at most
+constexpr int kTlWarps = 4;                  // treelets per block
+// a treelet's boxes in shared memory, 6 floats per slot: its leaves
+// [0, kTlLeaves), its nodes' unions [kTlLeaves, kTlLeaves + kTlNodes), and
+// one slot holding the inverted infinite box (an unused child)
+constexpr int kTlSlotEmpty = kTlLeaves + kTlNodes;
+constexpr int kTlSlots = kTlSlotEmpty + 1;
+// build counters: [0] treelets, [1] orphan leaves, [2] top nodes, [3] error
+// bits, [4] leaves covered by treelets
+constexpr int kTlCounters = 8;
+
+// Triangle at sorted position p (index record id): world vertices -> its
+// 48-B record; box.
+__device__ __forceinline__ void leaf_record_id(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                                               const float* __restrict__ xf, uint4 id,
+                                               const uint32_t* __restrict__ smat, float4* __restrict__ tris,
+                                               int64_t p, float3& lo, float3& hi) {
+  const float3 w0 = xform(xf + 12 * vb[id.x], rest[id.x]);
+  const float3 w1 = xform(xf + 12 * vb[id.y], rest[id.y]);
+  const float3 w2 = xform(xf + 12 * vb[id.z], rest[id.z]);
+  const float3 e1 = sub3(w1, w0), e2 = sub3(w2, w0);
+  tris[3 * p] = make_float4(w0.x, w0.y, w0.z, __uint_as_float(id.w));
+  tris[3 * p + 1] = make_float4(e1.x, e1.y, e1.z, __uint_as_float(smat[p]));
+  tris[3 * p + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+  lo = fmin3(w0, fmin3(w1, w2));
+  hi = fmax3(w0, fmax3(w1, w2));
+}
+
+__device__ __forceinline__ void leaf_record(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                                            const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                                            const uint32_t* __restrict__ smat, float4* __restrict__ tris, int64_t p,
+                                            float3& lo, float3& hi) {
+  leaf_record_id(rest, vb, xf, sidx[p], smat, tris, p, lo, hi);
+}
+
+// Writes node q's child boxes (b[6][4]: lox, loy, loz, hix, hiy, hiz per
+// child slot) whole and returns their union in u[6].
+__device__ __forceinline__ void write_node(Node4* __restrict__ nodes4, int64_t q, const float b[6][4], float u[6]) {
+  float4* n = &nodes4[q].lox;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) n[k] = make_float4(b[k][0], b[k][1], b[k][2], b[k][3]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    u[k] = fminf(fminf(b[k][0], b[k][1]), fminf(b[k][2], b[k][3]));
+    u[k + 3] = fmaxf(fmaxf(b[k + 3][0], b[k + 3][1]), fmaxf(b[k + 3][2], b[k + 3][3]));
   }
 }
 
-// A node with at least one internal member, written whole: an internal
-// member's box is the union of its child's four boxes (unused slots hold
-// the inverted infinite box, neutral for min/max), a leaf member's box
-// comes from the staging array (its leaf was marked kSlotMixed at build),
-// an unused slot keeps the inverted infinite box.
-__device__ __forceinline__ void refit4_node(Node4* nodes4, int64_t q, int64_t n4, const float* __restrict__ stage,
-                                            int64_t nt) {
-  Node4* n = nodes4 + q;
-  const int4 lk = n->link;
-  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
-  if (l[0] < 0 && l[1] < 0 && l[2] < 0 && l[3] < 0) return;  // leaves only: written by the leaf kernel
+// Leaves: one thread per triangle writes its 48-B record and its box (6
+// floats at lbox + 6p).  Short 128-thread blocks: they find room beside a
+// render's blocks when the refit overlaps the previous frame's render.
+__global__ void __launch_bounds__(128) k_refit_leaves(const float4* __restrict__ rest, const uint16_t* __restrict__ vb,
+                                                      const float* __restrict__ xf, const uint4* __restrict__ sidx,
+                                                      const uint32_t* __restrict__ smat, int64_t nt,
+                                                      float4* __restrict__ tris, float* __restrict__ lbox,
+                                                      float* __restrict__ xfb, int nxf) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < nxf) xfb[p] = xf[p];  // the frame buffer's copy of the body matrices
+  if (p >= nt) return;
+  float3 lo, hi;
+  leaf_record(rest, vb, xf, sidx, smat, tris, p, lo, hi);
+  float2* o = reinterpret_cast<float2*>(lbox + 6 * p);
+  o[0] = make_float2(lo.x, lo.y);
+  o[1] = make_float2(lo.z, hi.x);
+  o[2] = make_float2(hi.y, hi.z);
+}
+
+// Treelet nodes: one warp per treelet loads its leaves' boxes (one
+// contiguous range of lbox) into shared memory, then writes its nodes
+// deepest first, one lane per node: the node's six child-box vectors whole
+// (96 B) from the leaf boxes and the unions of its internal children, and
+// its own union in shared memory for its parent (a warp barrier between
+// depths); the treelet root's union also goes to nunion.  Four treelets per
+// 128-thread block, no block barrier: the blocks are as short-lived as
+// those of the leaf pass, so they fit beside a render's blocks.
+__global__ void __launch_bounds__(32 * kTlWarps) k_refit_tl(Node4* __restrict__ nodes4,
+                                                            const int4* __restrict__ info,
+                                                            const int2* __restrict__ tl_node,
+                                                            const int4* __restrict__ refs,
+                                                            const float* __restrict__ lbox,
+                                                            float* __restrict__ nunion, int ntl) {
+  __shared__ float2 boxes[kTlWarps][kTlSlots][3];  // each warp's treelet: lo.xy, lo.z hi.x, hi.yz per slot
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kTlWarps + w;
+  if (t >= ntl) return;  // the whole warp
+  float2(*bx)[3] = boxes[w];
+  const int4 in = info[t];
+  const int off = in.x, nn = in.y & 0xffff, maxrd = in.y >> 16, l0 = in.z, l1 = in.w;
   const float inf = __int_as_float(0x7f800000);
-  float4 m[6];
+  if (lane == 0) {
+    bx[kTlSlotEmpty][0] = make_float2(inf, inf);
+    bx[kTlSlotEmpty][1] = make_float2(inf, -inf);
+    bx[kTlSlotEmpty][2] = make_float2(-inf, -inf);
+  }
+  const float2* src = reinterpret_cast<const float2*>(lbox + 6 * (int64_t)l0);
+  for (int j = lane; j <= l1 - l0; j += 32) {  // a lane per leaf: 3 x 8 B
+    bx[j][0] = src[3 * j];
+    bx[j][1] = src[3 * j + 1];
+    bx[j][2] = src[3 * j + 2];
+  }
+  int64_t q = -1;
+  int rd = -1;
+  int4 rf = make_int4(kTlSlotEmpty, kTlSlotEmpty, kTlSlotEmpty, kTlSlotEmpty);
+  if (lane < nn) {
+    const int2 e = tl_node[off + lane];
+    q = e.x;
+    rd = e.y;
+    rf = refs[off + lane];
+  }
+  __syncwarp();
+  for (int r = maxrd; r >= 0; --r) {
+    if (rd == r) {
+      const int c4[4] = {rf.x, rf.y, rf.z, rf.w};
+      float b[6][4];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) m[j] = j < 3 ? make_float4(inf, inf, inf, inf) : make_float4(-inf, -inf, -inf, -inf);
-  float* f = reinterpret_cast<float*>(m);
+      for (int c = 0; c < 4; ++c) {
+        const float2 x0 = bx[c4[c]][0], x1 = bx[c4[c]][1], x2 = bx[c4[c]][2];
+        b[0][c] = x0.x; b[1][c] = x0.y; b[2][c] = x1.x;
+        b[3][c] = x1.y; b[4][c] = x2.x; b[5][c] = x2.y;
+      }
+      float u[6];
+      write_node(nodes4, q, b, u);
+      bx[kTlLeaves + lane][0] = make_float2(u[0], u[1]);
+      bx[kTlLeaves + lane][1] = make_float2(u[2], u[3]);
+      bx[kTlLeaves + lane][2] = make_float2(u[4], u[5]);
+      if (r == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nunion[6 * q + k] = u[k];
+    }
+    __syncwarp();
+  }
+}
+
+// A top node: its internal children's unions from nunion (treelet roots and
+// deeper top nodes), its leaves' boxes from lbox.
+__device__ __forceinline__ void refit_top_node(Node4* __restrict__ nodes4, int64_t q, int64_t n4, int64_t nt,
+                                               float* __restrict__ nunion, const float* __restrict__ stage) {
+  const int4 lk = nodes4[q].link;
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  const float inf = __int_as_float(0x7f800000);
+  float b[6][4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    if (l[c] == kEmptyLink) continue;
-    if (l[c] < 0) {
-      const int64_t p = ~(int64_t)l[c];
-      if (p >= nt) continue;  // never for a complete collapse
-      const float* b = stage + 6 * p;
+    const float* src = nullptr;
+    if (l[c] >= 0 && l[c] < n4) src = nunion + 6 * (int64_t)l[c];
+    else if (l[c] < 0 && l[c] != kEmptyLink && ~(int64_t)l[c] < nt) src = stage + 6 * ~(int64_t)l[c];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) f[j * 4 + c] = __ldcg(b + j);
-      continue;
-    }
-    if (l[c] >= n4) continue;  // never for a complete collapse
-    const Node4* ch = nodes4 + l[c];
-    float4 a[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) a[j] = __ldcg(&ch->lox + j);
-    f[0 * 4 + c] = fminf(fminf(a[0].x, a[0].y), fminf(a[0].z, a[0].w));
-    f[1 * 4 + c] = fminf(fminf(a[1].x, a[1].y), fminf(a[1].z, a[1].w));
-    f[2 * 4 + c] = fminf(fminf(a[2].x, a[2].y), fminf(a[2].z, a[2].w));
-    f[3 * 4 + c] = fmaxf(fmaxf(a[3].x, a[3].y), fmaxf(a[3].z, a[3].w));
-    f[4 * 4 + c] = fmaxf(fmaxf(a[4].x, a[4].y), fmaxf(a[4].z, a[4].w));
-    f[5 * 4 + c] = fmaxf(fmaxf(a[5].x, a[5].y), fmaxf(a[5].z, a[5].w));
+    for (int k = 0; k < 6; ++k) b[k][c] = src ? __ldcg(src + k) : (k < 3 ? inf : -inf);
   }
+  float u[6];
+  write_node(nodes4, q, b, u);
 #pragma unroll
-  for (int j = 0; j < 6; ++j) (&n->lox)[j] = m[j];
+  for (int k = 0; k < 6; ++k) nunion[6 * q + k] = u[k];
 }
 
-__global__ void __launch_bounds__(128) k_refit4_level(Node4* nodes4, int64_t begin, int64_t end, int64_t n4,
-                                                      const float* __restrict__ stage, int64_t nt) {
-  const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q < end) refit4_node(nodes4, q, n4, stage, nt);
+__global__ void __launch_bounds__(128) k_refit_top_level(Node4* nodes4, const int32_t* __restrict__ top, int64_t b,
+                                                         int64_t e, int64_t n4, int64_t nt, float* nunion,
+                                                         const float* __restrict__ stage) {
+  const int64_t i = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < e) refit_top_node(nodes4, top[i], n4, nt, nunion, stage);
 }
 
-// depths lvl[d0] .. lvl[d1], deepest (d1) first
-__global__ void __launch_bounds__(1024) k_refit4_small(Node4* nodes4, const int64_t* __restrict__ lvl, int d0, int d1,
-                                                       int64_t n4, const float* __restrict__ stage, int64_t nt) {
-  for (int dth = d1; dth >= d0; --dth) {
-    for (int64_t q = lvl[dth] + threadIdx.x; q < lvl[dth + 1]; q += blockDim.x) refit4_node(nodes4, q, n4, stage, nt);
+// groups g0 .. g1 of the top list (each one depth, deepest first) in order
+__global__ void __launch_bounds__(1024) k_refit_top_small(Node4* nodes4, const int32_t* __restrict__ top,
+                                                          const int64_t* __restrict__ grp, int g0, int g1, int64_t n4,
+                                                          int64_t nt, float* nunion, const float* __restrict__ stage) {
+  for (int g = g0; g <= g1; ++g) {
+    for (int64_t i = grp[g] + threadIdx.x; i < grp[g + 1]; i += blockDim.x)
+      refit_top_node(nodes4, top[i], n4, nt, nunion, stage);
     __syncthreads();
   }
 }
 
-// Build: mark the leaves of nodes that also have internal members
-// (kSlotMixed in their leaf_slot4): the per-frame refit stages their boxes.
-__global__ void k_mark_mixed(const Node4* __restrict__ nodes4, int64_t n4, int32_t* __restrict__ leaf_slot4,
-                             int64_t nt) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n4) return;
+// ---- treelet build (once per build, single-level trees) ----------------------
+// subtree node and leaf counts, one depth (deepest first)
+__global__ void k_tl_size(const Node4* __restrict__ nodes4, int64_t begin, int64_t end, int64_t n4,
+                          int32_t* __restrict__ size, int32_t* __restrict__ nleaf) {
+  const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= end) return;
   const int4 lk = nodes4[q].link;
   const int l[4] = {lk.x, lk.y, lk.z, lk.w};
-  const bool internal = l[0] >= 0 || l[1] >= 0 || l[2] >= 0 || l[3] >= 0;
-  if (!internal) return;
-  for (int c = 0; c < 4; ++c)
-    if (l[c] < 0 && l[c] != kEmptyLink && ~(int64_t)l[c] < nt) leaf_slot4[~l[c]] |= kSlotMixed;
+  int32_t sz = 1, nl = 0;
+  for (int c = 0; c < 4; ++c) {
+    if (l[c] >= 0 && l[c] < n4) {
+      sz += size[l[c]];
+      nl += nleaf[l[c]];
+    } else if (l[c] < 0 && l[c] != kEmptyLink) {
+      nl += 1;
+    }
+  }
+  size[q] = sz;
+  nleaf[q] = nl;
+}
+
+__global__ void k_tl_root(const int32_t* __restrict__ size, int32_t* tid, int32_t* depth, int32_t* top, int32_t* ctr) {
+  if (size[0] <= kTlNodes) {
+    tid[0] = 0;
+    depth[0] = 0;
+    ctr[0] = 1;
+  } else {
+    tid[0] = -1;
+    top[0] = 0;
+    ctr[2] = 1;
+  }
+}
+
+// treelet membership, one depth (shallowest first): a child of a top node
+// starts a treelet if its subtree is small enough, else it is a top node;
+// a child of a treelet node joins that treelet; leaves extend their
+// treelet's leaf range or are orphans (children of top nodes, counted)
+__global__ void k_tl_assign(const Node4* __restrict__ nodes4, int64_t begin, int64_t end, int d, int64_t n4,
+                            int64_t nt, const int32_t* __restrict__ size, int32_t* tid, int32_t* depth, int32_t* lo,
+                            int32_t* hi, int32_t* cnt, int32_t* nl, int32_t* top, int32_t* ctr) {
+  const int64_t q = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= end) return;
+  const int t = tid[q];
+  if (t >= 0) atomicAdd(&cnt[t], 1);
+  const int4 lk = nodes4[q].link;
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  for (int c = 0; c < 4; ++c) {
+    if (l[c] >= 0 && l[c] < n4) {
+      int tc = t;
+      if (t < 0) {
+        if (size[l[c]] <= kTlNodes) {
+          tc = atomicAdd(&ctr[0], 1);
+          depth[tc] = d + 1;
+        } else {
+          top[atomicAdd(&ctr[2], 1)] = l[c];
+        }
+      }
+      tid[l[c]] = tc;
+    } else if (l[c] != kEmptyLink) {  // a leaf (an internal link >= n4 never occurs)
+      const int64_t p = ~(int64_t)l[c];
+      if (l[c] >= 0 || p >= nt) {  // never for a complete collapse
+        atomicOr(&ctr[3], 1);
+        continue;
+      }
+      if (t >= 0) {
+        atomicMin(&lo[t], (int32_t)p);
+        atomicMax(&hi[t], (int32_t)p);
+        atomicAdd(&nl[t], 1);
+      } else {
+        atomicAdd(&ctr[1], 1);  // an orphan: its box is read by the top pass
+      }
+    }
+  }
+}
+
+// exclusive scan of n int32 values: block sums, then each block's scan from
+// the sum of the earlier blocks
+__global__ void __launch_bounds__(1024) k_scan_sums(const int32_t* __restrict__ in, int64_t n,
+                                                    int32_t* __restrict__ bsum) {
+  __shared__ int32_t ws[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t i = blockIdx.x * 1024ll + tid;
+  int32_t v = i < n ? in[i] : 0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int32_t y = ws[lane];
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) bsum[blockIdx.x] = y;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const int32_t* __restrict__ in, int64_t n,
+                                                     const int32_t* __restrict__ bsum, int32_t* __restrict__ out) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t base;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (w == 0) {
+    int32_t y = 0;
+    for (int k = lane; k < (int)blockIdx.x; k += 32) y += bsum[k];
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) base = y;
+  }
+  const int64_t i = blockIdx.x * 1024ll + tid;
+  const int32_t v = i < n ? in[i] : 0;
+  int32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t y = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    ws[lane] = y;
+  }
+  __syncthreads();
+  if (i < n) out[i] = base + (w ? ws[w - 1] : 0) + x - v;
+}
+
+// list slot of every treelet node (its treelet's nodes contiguous, in any order)
+__global__ void k_tl_scatter(int64_t n4, const int32_t* __restrict__ tid, const int32_t* __restrict__ off,
+                             int32_t* cur, int2* __restrict__ tl_node, int32_t* __restrict__ local) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const int t = tid[q];
+  if (t < 0) return;
+  const int32_t k = atomicAdd(&cur[t], 1);
+  tl_node[off[t] + k] = make_int2((int)q, 0);
+  local[q] = k;
+}
+
+// per list slot: depth below the treelet root, and its children as
+// shared-memory slots of the treelet kernel (leaf - first leaf, kTlLeaves +
+// list slot of an internal child, kTlSlotEmpty)
+__global__ void k_tl_refs(const Node4* __restrict__ nodes4, int64_t nlist, int64_t n4, int64_t nt,
+                          int2* __restrict__ tl_node, const int32_t* __restrict__ tid, const int32_t* __restrict__ local,
+                          const int32_t* __restrict__ lo, const int32_t* __restrict__ depth,
+                          const int64_t* __restrict__ lvl4, int D, int4* __restrict__ refs, int32_t* maxrd,
+                          int32_t* ctr) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nlist) return;
+  const int q = tl_node[i].x;
+  if (q < 0 || q >= n4) {  // never: every slot is written once by k_tl_scatter
+    atomicOr(&ctr[3], 32);
+    return;
+  }
+  const int t = tid[q];
+  int dq = 0;
+  for (int k = 1; k < D; ++k) dq += lvl4[k] <= q;
+  const int r = dq - depth[t];
+  tl_node[i].y = r;
+  atomicMax(&maxrd[t], r);
+  const int4 lk = nodes4[q].link;
+  const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+  int o[4];
+  for (int c = 0; c < 4; ++c) {
+    o[c] = kTlSlotEmpty;
+    if (l[c] >= 0 && l[c] < n4) {
+      if (tid[l[c]] != t || local[l[c]] >= kTlNodes) atomicOr(&ctr[3], 4);
+      else o[c] = kTlLeaves + local[l[c]];
+    } else if (l[c] < 0 && l[c] != kEmptyLink) {
+      const int64_t j = ~(int64_t)l[c] - lo[t];
+      if (j < 0 || j >= kTlLeaves || ~(int64_t)l[c] >= nt) atomicOr(&ctr[3], 8);
+      else o[c] = (int)j;
+    }
+  }
+  refs[i] = make_int4(o[0], o[1], o[2], o[3]);
+}
+
+// top nodes: a flag per node, then (after an exclusive scan of the flags)
+// the list in descending node order = deepest depth first
+__global__ void k_tl_topflag(int64_t n4, const int32_t* __restrict__ tid, int32_t* __restrict__ flag) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < n4) flag[q] = tid[q] < 0 ? 1 : 0;
+}
+
+__global__ void k_tl_topscatter(int64_t n4, int64_t ntop, const int32_t* __restrict__ flag,
+                                const int32_t* __restrict__ pos, int32_t* __restrict__ top) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < n4 && flag[q] && pos[q] < ntop) top[ntop - 1 - pos[q]] = (int32_t)q;  // (pos < ntop: always)
+}
+
+// pos at the first node of each depth (the top nodes above that depth)
+__global__ void k_tl_topbounds(const int32_t* __restrict__ pos, const int64_t* __restrict__ lvl4, int D,
+                               int32_t* __restrict__ out) {
+  const int d = threadIdx.x;
+  if (d < D) out[d] = pos[lvl4[d]];
+}
+
+// per treelet: (list offset, nodes | max depth << 16, first leaf, last
+// leaf); checks that the leaves form one range of at most kTlLeaves
+__global__ void k_tl_info(int ntl, int64_t nt, const int32_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                          const int32_t* __restrict__ maxrd, const int32_t* __restrict__ lo,
+                          const int32_t* __restrict__ hi, const int32_t* __restrict__ nl, int4* __restrict__ info,
+                          int32_t* ctr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntl) return;
+  const int n = hi[t] - lo[t] + 1;
+  const bool ok = cnt[t] >= 1 && cnt[t] <= kTlNodes && maxrd[t] >= 0 && maxrd[t] < 0x7fff && n >= 1 &&
+                  n <= kTlLeaves && (n == nl[t] || nt == 1);
+  if (!ok) atomicOr(&ctr[3], 16);
+  info[t] = make_int4(off[t], cnt[t] | (maxrd[t] << 16), lo[t], hi[t]);
+  atomicAdd(&ctr[4], n);
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -1229,7 +1493,6 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
     }
     if (int e = cuda_check(cudaMemcpyAsync(qlen, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, st), "copy"))
       return e;
-    if (int e = cuda_check(cudaMemsetAsync(s->leaf_slot4, 0xff, 4 * T, st), "memset")) return e;
     if (s->two_level) {
       // every body's subtree root starts a bottom level (key prefix above bit 3m)
       int prefix_bits = 0;
@@ -1240,12 +1503,11 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
       k_body_ranges<<<grid_for(T, 256), 256, 0, st>>>(s->keys, T, prefix_bits > 0 ? shift : 63, s->nbody,
                                                        s->body_range, s->ctrl + 8);
       k_body_roots<<<1, 1024, 0, st>>>(s->keys, T, s->body_range, s->nbody, s->leaf_slot, s->blas_root, qa, qlen,
-                                       s->nodes4, s->leaf_slot4);
+                                       s->nodes4);
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(capq, 256), (int64_t)sm_count() * 8));
     for (int d = 0; d < L; ++d) {
-      k_collapse<<<grid, 256, 0, st>>>(s->nodes, qa, qlen + d, qb, qlen + d + 1, alloc, s->nodes4, cap4,
-                                       s->leaf_slot4, T);
+      k_collapse<<<grid, 256, 0, st>>>(s->nodes, qa, qlen + d, qb, qlen + d + 1, alloc, s->nodes4, cap4);
       std::swap(qa, qb);
     }
     if (int e = cuda_check(cudaGetLastError(), "collapse")) return e;
@@ -1262,13 +1524,12 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
                            "copy"))
       return e;
     k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
-    if (!s->two_level && s->n4 > 0)
-      k_mark_mixed<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes4, s->n4, s->leaf_slot4, T);
     if (s->two_level)
       k_body_boxes<<<grid_for(s->nbody, 256), 256, 0, st>>>(s->nodes4, s->n4, s->blas_root, s->nbody, s->body_box);
     if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
     if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // lvl4 host vector copied
   }
+  if (int e = treelet_build(s, st)) return e;
   s->built = true;
   return FIRE_OK;
 }
@@ -1290,33 +1551,110 @@ int lbvh_refit(fire_scene_s* s, cudaStream_t st) {
   const int64_t T = s->nt;
   if (T == 0) return FIRE_OK;
   prof_begin(s, kStageRefit, st);
-  // 128-thread blocks: small enough to be scheduled beside the render
-  // kernels' blocks when a refit overlaps the previous frame's render
   const int nxf = 12 * s->nbody;
-  k_refit4_leaves<<<grid_for(std::max<int64_t>(T, nxf), 128), 128, 0, st>>>(
-      s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->nodes4, s->leaf_slot4, s->n4, s->xf_buf[s->cur], nxf,
-      s->stage);
-  // depths, deepest first: runs of depths of at most 1024 nodes go to one
-  // block, larger ones get their own launch (a one-block depth of 8192
-  // nodes took 8 dependent rounds: refit 0.63 -> 0.57 ms with this split)
-  const int D = (int)s->lvl4.size() - 1;  // depths 0 .. D-1
-  const int64_t* lvl_dev = reinterpret_cast<const int64_t*>(s->lvl_aux);
-  int d = D - 1, launches = 1;
-  while (d >= 0) {
-    const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
+  k_refit_leaves<<<grid_for(std::max<int64_t>(T, nxf), 128), 128, 0, st>>>(s->rest, s->vbody, s->xf, s->sidx, s->smat, T, s->tris, s->stage,
+                                              s->xf_buf[s->cur], nxf);
+  if (s->ntl > 0)
+    k_refit_tl<<<(unsigned)((s->ntl + kTlWarps - 1) / kTlWarps), 32 * kTlWarps, 0, st>>>(
+        s->nodes4, s->tl_info, s->tl_node, s->tl_refs, s->stage, s->nunion, s->ntl);
+  // top nodes, deepest depth first: a depth of more than 1024 top nodes gets
+  // its own launch, runs of smaller ones go to one block
+  const std::vector<int64_t>& grp = s->tl_grp_host;
+  const int G = (int)grp.size() - 1;
+  int launches = s->ntl > 0 ? 2 : 1;
+  for (int g = 0; g < G;) {
+    const int64_t n = grp[g + 1] - grp[g];
     ++launches;
     if (n > 1024) {
-      k_refit4_level<<<grid_for(n, 128), 128, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], s->n4, s->stage, T);
-      --d;
+      k_refit_top_level<<<grid_for(n, 128), 128, 0, st>>>(s->nodes4, s->tl_top, grp[g], grp[g + 1], s->n4, T,
+                                                           s->nunion, s->stage);
+      ++g;
       continue;
     }
-    int d0 = d;
-    while (d0 > 0 && s->lvl4[d0] - s->lvl4[d0 - 1] <= 1024) --d0;
-    k_refit4_small<<<1, 1024, 0, st>>>(s->nodes4, lvl_dev, d0, d, s->n4, s->stage, T);
-    d = d0 - 1;
+    int g1 = g;
+    while (g1 + 1 < G && grp[g1 + 2] - grp[g1 + 1] <= 1024) ++g1;
+    k_refit_top_small<<<1, 1024, 0, st>>>(s->nodes4, s->tl_top, s->tl_grp, g, g1, s->n4, T, s->nunion, s->stage);
+    g = g1 + 1;
   }
   prof_end(s, kStageRefit, st, launches);
   return cuda_check(cudaGetLastError(), "refit kernels");
+}
+
+// Treelets of a single-level tree (after the collapse; see the refit above).
+int treelet_build(fire_scene_s* s, cudaStream_t st) {
+  s->ntl = 0;
+  s->norphan = 0;
+  s->tl_grp_host.assign(1, 0);
+  if (s->two_level || s->n4 == 0) return FIRE_OK;
+  const int64_t T = s->nt, n4 = s->n4;
+  int32_t* w = s->tl_scratch;
+  int32_t *size = w, *nleaf = w + T, *tid = w + 2 * T, *local = w + 3 * T, *lo = w + 4 * T, *hi = w + 5 * T;
+  int32_t *cnt = w + 6 * T, *cur = w + 7 * T, *depth = w + 8 * T, *maxrd = w + 9 * T, *nl = w + 10 * T;
+  int32_t* off = w + 11 * T;
+  int32_t* bsum = w + 12 * T;
+  int32_t* ctr = bsum + (T + 1023) / 1024 + 1;
+  if (int e = cuda_check(cudaMemsetAsync(lo, 0x7f, 4 * T, st), "memset")) return e;  // 0x7f7f7f7f > any leaf
+  if (int e = cuda_check(cudaMemsetAsync(hi, 0xff, 4 * T, st), "memset")) return e;  // -1
+  if (int e = cuda_check(cudaMemsetAsync(cnt, 0, 8 * T, st), "memset")) return e;    // cnt, cur
+  if (int e = cuda_check(cudaMemsetAsync(maxrd, 0, 8 * T, st), "memset")) return e;  // maxrd, nl
+  if (int e = cuda_check(cudaMemsetAsync(ctr, 0, 4 * kTlCounters, st), "memset")) return e;
+  const int D = (int)s->lvl4.size() - 1;
+  for (int d = D - 1; d >= 0; --d) {
+    const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
+    k_tl_size<<<grid_for(n, 256), 256, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], n4, size, nleaf);
+  }
+  k_tl_root<<<1, 1, 0, st>>>(size, tid, depth, s->tl_top, ctr);
+  for (int d = 0; d < D; ++d) {
+    const int64_t n = s->lvl4[d + 1] - s->lvl4[d];
+    k_tl_assign<<<grid_for(n, 256), 256, 0, st>>>(s->nodes4, s->lvl4[d], s->lvl4[d + 1], d, n4, T, size, tid, depth,
+                                                  lo, hi, cnt, nl, s->tl_top, ctr);
+  }
+  int32_t h[kTlCounters];
+  if (int e = cuda_check(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st), "copy")) return e;
+  if (int e = cuda_check(cudaStreamSynchronize(st), "treelets")) return e;
+  if (h[3] != 0 || h[0] < 1) return set_error(FIRE_ERR_CUDA, "treelet partition of the 4-wide tree failed");
+  const int ntl = h[0];
+  const int64_t norph = h[1], ntop = h[2], nlist = n4 - ntop;
+  const int64_t nb = (ntl + 1023) / 1024;
+  k_scan_sums<<<(unsigned)nb, 1024, 0, st>>>(cnt, ntl, bsum);
+  k_scan_apply<<<(unsigned)nb, 1024, 0, st>>>(cnt, ntl, bsum, off);
+  k_tl_scatter<<<grid_for(n4, 256), 256, 0, st>>>(n4, tid, off, cur, s->tl_node, local);
+  if (nlist > 0)
+    k_tl_refs<<<grid_for(nlist, 256), 256, 0, st>>>(s->nodes4, nlist, n4, T, s->tl_node, tid, local, lo, depth,
+                                                    reinterpret_cast<const int64_t*>(s->lvl_aux), D, s->tl_refs,
+                                                    maxrd, ctr);
+  k_tl_info<<<grid_for(ntl, 256), 256, 0, st>>>(ntl, T, off, cnt, maxrd, lo, hi, nl, s->tl_info, ctr);
+  // top list, deepest depth first (descending node order), and where each
+  // depth starts in it
+  int32_t* flag = nleaf;  // free after the sizes
+  int32_t* pos = size;    // free after the assignment
+  int32_t* bounds = ctr + kTlCounters;  // [D]
+  const int64_t nb4 = (n4 + 1023) / 1024;
+  k_tl_topflag<<<grid_for(n4, 256), 256, 0, st>>>(n4, tid, flag);
+  k_scan_sums<<<(unsigned)nb4, 1024, 0, st>>>(flag, n4, bsum);
+  k_scan_apply<<<(unsigned)nb4, 1024, 0, st>>>(flag, n4, bsum, pos);
+  k_tl_topscatter<<<grid_for(n4, 256), 256, 0, st>>>(n4, ntop, flag, pos, s->tl_top);
+  k_tl_topbounds<<<1, kMaxDepth4, 0, st>>>(pos, reinterpret_cast<const int64_t*>(s->lvl_aux), D, bounds);
+  std::vector<int32_t> P((size_t)D + 1);
+  if (int e = cuda_check(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st), "copy")) return e;
+  if (int e = cuda_check(cudaMemcpyAsync(P.data(), bounds, 4 * (size_t)D, cudaMemcpyDeviceToHost, st), "copy"))
+    return e;
+  if (int e = cuda_check(cudaGetLastError(), "treelet kernels")) return e;
+  if (int e = cuda_check(cudaStreamSynchronize(st), "treelets")) return e;
+  if (h[3] != 0 || h[4] + norph != T)
+    return set_error(FIRE_ERR_CUDA, "treelet partition of the 4-wide tree failed");
+  P[D] = (int32_t)ntop;
+  // depth d's top nodes sit at [ntop - P[d+1], ntop - P[d]) of the list
+  std::vector<int64_t> grp(1, 0);
+  for (int d = D - 1; d >= 0; --d)
+    if (P[d + 1] > P[d]) grp.push_back(ntop - P[d]);
+  if (grp.back() != ntop) return set_error(FIRE_ERR_CUDA, "treelet top list inconsistent");
+  if (int e = cuda_check(cudaMemcpyAsync(s->tl_grp, grp.data(), 8 * grp.size(), cudaMemcpyHostToDevice, st), "copy"))
+    return e;
+  s->ntl = ntl;
+  s->norphan = norph;
+  s->tl_grp_host = grp;
+  return FIRE_OK;
 }
 
 }  // namespace fire

@@ -45,7 +45,7 @@ def test_algorithmic_bytes_model():
     assert b["primary"] == tree + 16 * samples + 32 * rays + 4 * counts
     assert b["queue"] == 8 * counts + 4 * rays
     assert b["resolve"] == 48 * samples + 16 * pixels
-    assert b["refit"] == 18 * nv + 96 * nt + 208 * n4
+    assert b["refit"] == 18 * nv + 116 * nt + 120 * n4
     # the headline frame: 7,299,072 triangles, 3,652,849 vertices
     full = bench.algorithmic_bytes(7_299_072, 3_652_849, 3_476_669, 8_294_400, 2_073_600, 3_842_521)
     assert 0.9e9 < full["shadow"] < 1.0e9

@@ -3,7 +3,7 @@
 sampled outputs of a refit frame that the oracle computes one by one, and
 the launch configuration the benchmark times (refit of frame i on a
 high-priority second stream overlapping the render of frame i-1, primary
-pass at 6 blocks per SM) giving the serial frames bit for bit."""
+pass at 7 blocks per SM) giving the serial frames bit for bit."""
 import numpy as np
 import pytest
 
@@ -81,7 +81,7 @@ def test_fullsize_pipelined_bench_configuration():
     Gb.build(xf0)
     dev = [torch.from_numpy(p).cuda() for p in poses]
     side = torch.cuda.Stream(priority=-1)
-    opts = fb.fire.make_opts(blocks_per_sm=6)
+    opts = fb.fire.make_opts(blocks_per_sm=7)
     outs = [torch.empty_like(serial[0]) for _ in poses]
     torch.cuda.synchronize()
     for i in range(len(poses)):
