@@ -280,18 +280,24 @@ __device__ __forceinline__ void resolve_write(const RenderArgs& a, int lane, boo
 __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int ntasks, const float* inten) {
   const int lane = threadIdx.x & 31;
   const float eps = frame_eps(a);
-  while (true) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(a.ctrl + 1, 1);
-    task = __shfl_sync(kFull, task, 0);
-    if (task >= ntasks) return;
-    int x, y, k;
-    bool valid = task_sample(g, task, lane, x, y, k);
+  // tasks by a static warp stride (the work per task is even: no counter
+  // round trip), the next task's record loaded before this task is shaded
+  const int stride = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  int task = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int x = 0, y = 0, k = 0;
+  bool valid = task < ntasks && task_sample(g, task, lane, x, y, k);
+  int4 next = valid ? reinterpret_cast<const int4*>(a.g)[((int64_t)y * a.cam.W + x) * a.cam.spp + k]
+                    : make_int4(-1, 0, 0, 0);
+  for (; task < ntasks; task += stride) {
+    const int4 rr = next;
+    const int cx = x, cy = y, ck = k;
+    const bool cvalid = valid;
+    valid = task + stride < ntasks && task_sample(g, task + stride, lane, x, y, k);
+    if (valid) next = reinterpret_cast<const int4*>(a.g)[((int64_t)y * a.cam.W + x) * a.cam.spp + k];
     float3 rad = f3(0.0f, 0.0f, 0.0f);
     int hit = 0;
-    if (valid) {
-      int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
-      int4 rr = reinterpret_cast<const int4*>(a.g)[sid];
+    if (cvalid) {
+      const int x = cx, y = cy, k = ck;
       int prim = rr.x, pos = rr.w;
       const uint32_t vis = (uint32_t)rr.z;
       if (prim >= 0) {
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
         }
       }
     }
-    resolve_write(a, lane, valid, x, y, rad, hit);
+    resolve_write(a, lane, cvalid, cx, cy, rad, hit);
   }
 }
 
