@@ -342,37 +342,42 @@ __global__ void __launch_bounds__(128) k_shade(RenderArgs a, TaskGrid g, int nta
 //   df/dalb = (1-F)(1-m)/pi + (D vis - (1-m) alb/pi)(1 - w5) m
 //   df/dm   = (D vis - (1-m) alb/pi)(1 - w5)(alb - 0.04) - (1-F) alb/pi
 //   df/dr   = F (dD/dr vis + D dvis/dr)
-// Per-sample terms and per-warp sums (shuffles; material terms per group of
-// lanes sharing a material) are FP32; everything above is FP64: shared-memory
-// atomics per block, global atomics into `acc` (nmat*5 + nlights doubles,
-// zero on entry), and the last block to finish adds `acc` into the FP32
-// outputs and zeroes it.
-__global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
+// Per-sample terms, per-warp sums (shuffles; material terms per group of
+// lanes sharing a material) and the block's sums of a few warp sums (shared
+// atomics) are FP32; the sums over blocks are FP64: global atomics into
+// `acc` (nmat*5 + nlights doubles, zero on entry), and the last block to
+// finish adds `acc` into the FP32 outputs and zeroes it.
+__global__ void __launch_bounds__(128, 8) k_shade_bwd(RenderArgs a, TaskGrid g, int ntasks, const float* inten,
                                                    const float* dL, float* dparams, float* dinten,
                                                    double* acc) {
-  extern __shared__ double sacc[];  // [nmat*5 + nlights]
+  extern __shared__ float sacc[];  // [nmat*5 + nlights]
   __shared__ bool last_block;
   const int nm5 = a.mats.n * 5;
   const int nacc = nm5 + a.lights.n;
-  for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) sacc[i] = 0.0f;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const float eps = frame_eps(a);
-  while (true) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(a.ctrl + 2, 1);
-    task = __shfl_sync(kFull, task, 0);
-    if (task >= ntasks) break;
-    int x, y, k;
-    bool valid = task_sample(g, task, lane, x, y, k);
+  // tasks by a static warp stride, the next task's record loaded first (as
+  // in k_shade)
+  const int stride = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  int task = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int nx = 0, ny = 0, nk = 0;
+  bool nvalid = task < ntasks && task_sample(g, task, lane, nx, ny, nk);
+  int4 next = nvalid ? reinterpret_cast<const int4*>(a.g)[((int64_t)ny * a.cam.W + nx) * a.cam.spp + nk]
+                     : make_int4(-1, 0, 0, 0);
+  for (; task < ntasks; task += stride) {
+    const int x = nx, y = ny, k = nk;
+    const bool valid = nvalid;
+    const int4 rr = next;
+    nvalid = task + stride < ntasks && task_sample(g, task + stride, lane, nx, ny, nk);
+    if (nvalid) next = reinterpret_cast<const int4*>(a.g)[((int64_t)ny * a.cam.W + nx) * a.cam.spp + nk];
     float gm[5] = {0, 0, 0, 0, 0};
     float gl[kMaxLights];
 #pragma unroll
     for (int j = 0; j < kMaxLights; ++j) gl[j] = 0.0f;
     int mat = -1;
     if (valid) {
-      int64_t sid = ((int64_t)y * a.cam.W + x) * a.cam.spp + k;
-      int4 rr = reinterpret_cast<const int4*>(a.g)[sid];
       if (rr.x >= 0) {
         float4 up4 = reinterpret_cast<const float4*>(dL)[(int64_t)y * a.cam.W + x];
         float inv_spp = 1.0f / (float)a.cam.spp;
@@ -432,14 +437,13 @@ __global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, 
     }
     // FP32 warp sums: the light terms over the whole warp, the material
     // terms over each group of lanes sharing a material (one pass per
-    // distinct material); one FP64 shared atomic per sum, by one lane (FP64
-    // instructions run at a small fraction of the FP32 rate)
+    // distinct material); one shared atomic per sum, by one lane
     unsigned todo = __ballot_sync(kFull, mat >= 0);
     if (todo == 0) continue;
     for (int j = 0; j < a.lights.n; ++j) {
       float v = gl[j];
       for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-      if (lane == 0) atomicAdd(&sacc[nm5 + j], (double)v);
+      if (lane == 0) atomicAdd(&sacc[nm5 + j], v);
     }
     while (todo) {
       const int leader = __ffs(todo) - 1;
@@ -454,13 +458,13 @@ __global__ void __launch_bounds__(128, 6) k_shade_bwd(RenderArgs a, TaskGrid g, 
       }
       if (lane == leader) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * m + q], (double)v[q]);
+        for (int q = 0; q < 5; ++q) atomicAdd(&sacc[5 * m + q], v[q]);
       }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nacc; i += blockDim.x)
-    if (sacc[i] != 0.0) atomicAdd(acc + i, sacc[i]);
+    if (sacc[i] != 0.0f) atomicAdd(acc + i, (double)sacc[i]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last_block = atomicAdd(a.ctrl + 3, 1u) == gridDim.x - 1;
@@ -600,7 +604,7 @@ int shade_backward(fire_scene_s* s, const RenderArgs& a, const float* inten, con
   int ntasks = g.tiles_x * g.tiles_y;
   if (ntasks == 0) return FIRE_OK;
   const int nacc = a.mats.n * 5 + a.lights.n;
-  size_t smem = sizeof(double) * nacc;
+  size_t smem = sizeof(float) * nacc;
   if (smem > 48 * 1024) {
     if (int e = cuda_check(cudaFuncSetAttribute(k_shade_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                            "smem attr"))
@@ -635,9 +639,9 @@ int shade_backward_on(const RenderArgs& a, const float* inten, const float* dL, 
   if (ntasks == 0) return FIRE_OK;
   const int nacc = a.mats.n * 5 + a.lights.n;
   if (nacc > 6144) return set_error(FIRE_ERR_INVALID_ARG, "too many parameters for the scratch backward");
-  int grid = std::max(1, std::min(sm_count() * occupancy_blocks(k_shade_bwd, 128, sizeof(double) * nacc),
+  int grid = std::max(1, std::min(sm_count() * occupancy_blocks(k_shade_bwd, 128, sizeof(float) * nacc),
                                   (ntasks + 3) / 4));
-  k_shade_bwd<<<grid, 128, sizeof(double) * nacc, st>>>(a, g, ntasks, inten, dL, dparams, dinten, acc);
+  k_shade_bwd<<<grid, 128, sizeof(float) * nacc, st>>>(a, g, ntasks, inten, dL, dparams, dinten, acc);
   return cuda_check(cudaGetLastError(), "k_shade_bwd");
 }
 
