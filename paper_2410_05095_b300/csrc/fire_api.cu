@@ -651,7 +651,7 @@ int fire_render(fire_scene s, const fire_camera* cam, const fire_light* lights, 
     if (cudaError_t e = dev_alloc((void**)&s->qperm, njobs * 4, &s->bytes)) return cuda_check(e, "shadow queue order");
     s->jobs_n = njobs;
   }
-  const size_t nq = (size_t)std::max(1, nlights) * (ntask_full + (ntask_full + 1023) / 1024);
+  const size_t nq = (size_t)std::max(1, nlights) * (ntask_full + (ntask_full + 255) / 256 + 1);  // counts, block sums
   if (s->qaux_n < nq) {
     if (s->qaux) {
       cudaFree(s->qaux);

@@ -127,33 +127,38 @@ __global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, in
 }
 
 // Task order of the shadow queue.  Per light, k_qsum adds up the tasks' ray
-// counts per block of 1024 tasks; k_qperm (one block per 1024 tasks) scans
+// counts per block of kQTasks tasks; k_qperm (one block per kQTasks tasks) scans
 // its tasks' counts, starts at the sum of the earlier blocks' totals, and
 // writes its dense range in order, each position holding the sparse slot of
 // its ray (a warp writes its tasks' ranges one task at a time, one lane per
 // ray), so a warp of the shadow pass takes the rays of one or two
 // neighbouring 4x2-pixel tasks; the last block writes the light's ray count
-// to ctrl[24 + j].
-__global__ void __launch_bounds__(1024) k_qsum(const int32_t* __restrict__ cnt, int32_t* __restrict__ bsum, int ntasks,
+// to ctrl[24 + j].  Blocks of 256 threads: when the next frame's refit
+// overlaps the render, they find room beside its blocks (1024-thread
+// blocks waited 0.17 ms for whole SMs).
+constexpr int kQTasks = 256;
+constexpr int kQWarps = kQTasks / 32;
+
+__global__ void __launch_bounds__(kQTasks) k_qsum(const int32_t* __restrict__ cnt, int32_t* __restrict__ bsum, int ntasks,
                                                int nblk) {
-  __shared__ int32_t wsum[32];
+  __shared__ int32_t wsum[kQWarps];
   const int j = blockIdx.y, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int t = b * 1024 + tid;
+  const int t = b * kQTasks + tid;
   int32_t v = t < ntasks ? cnt[(int64_t)j * ntasks + t] : 0;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   if (lane == 0) wsum[w] = v;
   __syncthreads();
   if (w == 0) {
-    int32_t y = wsum[lane];
+    int32_t y = lane < kQWarps ? wsum[lane] : 0;
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
     if (lane == 0) bsum[(int64_t)j * nblk + b] = y;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_qperm(const int32_t* __restrict__ cnt, const int32_t* __restrict__ bsum,
+__global__ void __launch_bounds__(kQTasks) k_qperm(const int32_t* __restrict__ cnt, const int32_t* __restrict__ bsum,
                                                 int32_t* __restrict__ perm, uint32_t* __restrict__ len, int ntasks,
                                                 int nblk, int64_t qseg) {
-  __shared__ int32_t wsum[32];
+  __shared__ int32_t wsum[kQWarps];
   __shared__ int32_t sbase;
   const int j = blockIdx.y, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (w == 0) {  // the earlier blocks' rays
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(1024) k_qperm(const int32_t* __restrict__ cnt,
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
     if (lane == 0) sbase = y;
   }
-  const int t = b * 1024 + tid;
+  const int t = b * kQTasks + tid;
   const int32_t v = t < ntasks ? cnt[(int64_t)j * ntasks + t] : 0;
   int32_t x = v;
   for (int o = 1; o < 32; o <<= 1) {
@@ -172,22 +177,22 @@ __global__ void __launch_bounds__(1024) k_qperm(const int32_t* __restrict__ cnt,
   if (lane == 31) wsum[w] = x;
   __syncthreads();
   if (w == 0) {
-    int32_t y = wsum[lane];
+    int32_t y = lane < kQWarps ? wsum[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t z = __shfl_up_sync(kFull, y, o);
       if (lane >= o) y += z;
     }
-    wsum[lane] = y;  // inclusive sums of the warps
+    if (lane < kQWarps) wsum[lane] = y;  // inclusive sums of the warps
   }
   __syncthreads();
-  const int32_t total = wsum[31], base = sbase;
+  const int32_t total = wsum[kQWarps - 1], base = sbase;
   const int32_t excl = x - v + (w ? wsum[w - 1] : 0);
   int32_t* out = perm + (int64_t)j * qseg + base;
   // the warp's tasks with rays, one after another, each written by its lanes
   for (unsigned nz = __ballot_sync(kFull, v > 0); nz; nz &= nz - 1) {
     const int k = __ffs(nz) - 1;
     const int32_t c = __shfl_sync(kFull, v, k), o = __shfl_sync(kFull, excl, k);
-    if (lane < c) out[o + lane] = 32 * (b * 1024 + w * 32 + k) + lane;
+    if (lane < c) out[o + lane] = 32 * (b * kQTasks + w * 32 + k) + lane;
   }
   if (b == nblk - 1 && tid == 0) len[j] = (uint32_t)(base + total);
 }
@@ -530,10 +535,11 @@ int launch_render(fire_scene_s* s, const RenderArgs& a, const TaskGrid& g, int n
   if (a.lights.n > 0) {
     prof_begin(s, kStageQueue, st);
     const int nl = a.lights.n;
-    const int nblk = (ntasks + 1023) / 1024;
+    const int nblk = (ntasks + kQTasks - 1) / kQTasks;
     int32_t* bsum = a.qcnt + (int64_t)nl * ntasks;
-    k_qsum<<<dim3(nblk, nl), 1024, 0, st>>>(a.qcnt, bsum, ntasks, nblk);
-    k_qperm<<<dim3(nblk, nl), 1024, 0, st>>>(a.qcnt, bsum, s->qperm, a.ctrl + kCtrlShadowLen, ntasks, nblk, a.qseg);
+    k_qsum<<<dim3(nblk, nl), kQTasks, 0, st>>>(a.qcnt, bsum, ntasks, nblk);
+    k_qperm<<<dim3(nblk, nl), kQTasks, 0, st>>>(a.qcnt, bsum, s->qperm, a.ctrl + kCtrlShadowLen, ntasks, nblk,
+                                                a.qseg);
     prof_end(s, kStageQueue, st, 2);
     prof_begin(s, kStageShadow, st);
     k_shadow<STACK, TWO><<<gs, threads, 0, st>>>(a, s->jobs, s->qperm);
