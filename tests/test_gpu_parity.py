@@ -57,6 +57,50 @@ def test_lbvh_duplicate_keys_and_tiny_counts(fb):
         assert_lbvh_equal(G, S, sc)
 
 
+def _xf_rot(rng, nbody):
+    """Rigid 3x4 matrices: a rotation about a random unit axis and a shift."""
+    out = np.zeros((nbody, 12), np.float32)
+    for b in range(nbody):
+        ax = rng.unit_vector()
+        ang = rng.uniform(-0.6, 0.6)
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+        shift = np.array([[rng.uniform(-0.5, 0.5)] for _ in range(3)])
+        out[b] = np.concatenate([R, shift], 1).reshape(12)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 33, 34, 100, 5000])
+def test_refit_tiny_and_treelet_edges(fb, n):
+    """The per-frame refit (by treelets of at most 32 4-wide nodes and the top
+    nodes above them) at triangle counts around one treelet and below it:
+    after two frames of motion of two bodies the boxes and triangle records
+    equal the oracle's refit bit for bit, and a render agrees with it."""
+    rng = sg.Rng(91 + n)
+    meshes, mesh_body = [], []
+    for i in range(n):
+        c = np.array([rng.uniform(-3, 3), rng.uniform(-3, 3), rng.uniform(-3, 3)])
+        size = 3.0 if n < 100 else 0.4  # few triangles: big ones, so that the image shows them
+        e = [np.array([rng.uniform(-size, size) for _ in range(3)]) for _ in range(2)]
+        meshes.append((np.stack([c, c + e[0], c + e[1]]), np.array([[0, 1, 2]])))
+        mesh_body.append(i % 2)
+    sc = sg.assemble(meshes, 2, sg.random_materials(rng, 2), mesh_body=mesh_body, nbody=2)
+    G, S = build_pair(sc)
+    for _ in range(2):
+        xf = _xf_rot(rng, 2)
+        G.refit(xf)
+        S.update(xf, rebuild=False)
+        assert np.array_equal(G.dump("boxes"), S.get("boxes"))
+        assert_tris_equal(G, S, sc)
+    assert G.sync_status() == 0
+    cam = sg.Camera((0.3, 0.7, 9.0), (0, 0, 0), (0, 1, 0), 50.0, 24, 16, 4)
+    lights = [sg.Light(0, (2.0, 6.0, 3.0), 40.0)]
+    img, g = _render(G, cam, lights)
+    ref = S.render_all_samples(cam, lights)
+    _, bad = compare_samples(g, ref)
+    assert bad.mean() < 0.01
+
+
 @pytest.mark.parametrize("nbody", [1000, 65536])
 def test_lbvh_many_bodies_bitexact(fb, nbody):
     """Keys with a wide body field (B = 10 and 16 bits, m = 17 and 15 bits per
