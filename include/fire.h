@@ -213,7 +213,10 @@ int fire_render_info(fire_scene s, int64_t* out4);
 int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream);
 
 /* Refit with the topology of the last build (§IV-B-3 step 4: new transforms
- * each frame): re-transform the vertices and recompute every box bottom-up.
+ * each frame): re-transform the vertices and recompute every box bottom-up
+ * (by treelets: subtrees of at most 32 4-wide nodes cut at build, each
+ * refit by one warp from shared memory, then the nodes above them; every
+ * box is the exact min/max over its triangles' vertices).
  * Before any build -> FIRE_ERR_NOT_BUILT.
  *
  * Frame buffers: the per-frame data (48-B triangle records and the 4-wide
@@ -224,7 +227,9 @@ int fire_bvh_build(fire_scene s, const float* body_xforms, int32_t xforms_on_dev
  * overwrites; a render waits for the refit that wrote its buffer), so a
  * refit issued on its own stream overlaps the previous frame's render, like
  * the paper's asynchronous compute queue.  Supported overlap: one refit
- * stream and one stream of render/shade calls per scene. */
+ * stream and one stream of render/shade calls per scene.  (Measured best:
+ * render calls on a high-priority stream, the refit on a normal one, and
+ * fire_render_opts.blocks_per_sm = 7.) */
 int fire_bvh_refit(fire_scene s, const float* body_xforms, int32_t xforms_on_device, void* stream);
 
 /* ---------------------------------------------------------------- render */
