@@ -207,9 +207,11 @@ __global__ void __launch_bounds__(kQTasks) k_qperm(const int32_t* __restrict__ c
 // branches inside each node step, not from rays of different lengths.)
 // The single-level kernel is held to 56 registers (9 blocks of 128 per SM,
 // no spills; 1.081 -> 1.062 ms against 62 registers and 8 blocks; 48
-// registers spill and cost 1.19 ms); the two-level one keeps its registers.
+// registers spill and cost 1.19 ms).  The two-level kernel is held to 70
+// registers (7 blocks per SM, no spills): its shadow pass went 1.91 -> 1.63
+// ms against the uncapped 93 registers; 64 registers spill and give 1.71.
 template <int STACK, bool TWO>
-__global__ void __launch_bounds__(128, TWO ? 1 : 9) k_shadow(RenderArgs a, const float4* __restrict__ jobs,
+__global__ void __launch_bounds__(128, TWO ? 7 : 9) k_shadow(RenderArgs a, const float4* __restrict__ jobs,
                                                 const int32_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31;
   TraceCtx c{a.nodes4, a.n4, TWO ? 0.0f : scene_span(a.nodes4, a.nt), a.tris, a.nt, a.iter_cap, a.ctrl + 8};
