@@ -107,7 +107,11 @@ extern "C" int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec*
   // fire_sync_status) see this one, as after fire_shade_backward
   s->last_stream = st;
   frame_acquire(s, st);
+  // timed as the backward stage, as in fire_shade_backward (the profiler's
+  // events are host objects: no device memory)
+  prof_begin(s, kStageBackward, st);
   const int e = shade_backward_on(a, inten, dL_drgba, dparams, dinten, acc, st);
+  prof_end(s, kStageBackward, st);
   frame_release(s, st);
   return e;
 }

@@ -59,8 +59,11 @@ __device__ __forceinline__ void hit_frame_of(const RenderArgs& a, float4 B, floa
 // MODE 0: traversal.  After a raster pass (raster.cu): MODE 1 traverses only
 // if that pass fell back, MODE 2 takes each sample's hit from its key
 // otherwise; exactly one of the two does the work.
+// Single level: 64 registers, 8 blocks of 128 per SM.  Two level: 72
+// registers, 7 blocks (primary 1.81 -> 1.64 ms against 64 registers, which
+// spill 206 B; 80 registers at 6 blocks give 1.72).
 template <int STACK, int MODE, bool TWO>
-__global__ void __launch_bounds__(128, 8) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
+__global__ void __launch_bounds__(128, TWO ? 7 : 8) k_primary(RenderArgs a, TaskGrid g, int ntasks, float4* __restrict__ jobs) {
   if (MODE != 0 && (MODE == 1) != (a.ctrl[kCtrlRasterFlag] != 0u)) return;
   const int lane = threadIdx.x & 31;
   const unsigned lower = (1u << lane) - 1u;

@@ -98,3 +98,29 @@ def test_noalloc_backward_rejects_more_parameters_than_its_scratch():
     with pytest.raises(fb.FireError) as e:
         G.shade_backward_noalloc(gb, cam, lights, params, inten, dimg, dP, dI)
     assert e.value.code == -1 and "4096" in str(e.value)
+
+
+def test_noalloc_backward_is_timed_as_the_backward_stage():
+    import torch
+
+    import paper_2410_05095_b300 as fb
+    w = sg.workload_tiny41k(32, 32)
+    cam = sg.Camera(**{**w.camera.__dict__, "spp": 1})
+    lights = [sg.LIGHTS_MAIN[0]]
+    G = fb.Scene.from_numpy(w.scene)
+    G.build(w.scene.identity_xforms())
+    gb = torch.zeros((cam.width * cam.height, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, lights, gbuf=gb)
+    params = torch.ones((len(w.scene.mats), 5), device="cuda") * 0.5
+    inten = torch.tensor([lights[0].intensity], dtype=torch.float32, device="cuda")
+    dimg = torch.ones((cam.height, cam.width, 4), device="cuda")
+    dP, dI = torch.zeros_like(params), torch.zeros_like(inten)
+    G.profile(True)
+    G.profile_read()  # drop what the build and render recorded
+    for _ in range(3):
+        G.shade_backward_noalloc(gb, cam, lights, params, inten, dimg, dP, dI)
+    prof = G.profile_read()
+    G.profile(False)
+    ms, launches = prof["backward"]
+    assert launches == 3 and ms > 0
+    assert G.sync_status() == 0
