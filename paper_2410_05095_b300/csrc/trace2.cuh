@@ -91,10 +91,10 @@ __host__ __device__ __forceinline__ bool leaf_test2(const Trace2View& c, int cod
 
 // Stack traversal of the top level and the bottom levels it reaches (the
 // single-level traversal's node step: sign-selected planes, FMA slabs,
-// leaves tested at once, entered children ordered by entry distance --
-// nearest first, any hit farthest first).  In the top level every entered
-// member, node or instance, is ordered and pushed; an instance is entered
-// when it is popped.
+// leaves tested at once, entered children ordered by slab4's key -- the
+// middle of the span nearest first, any hit the farthest exit first).  In
+// the top level every entered member, node or instance, is ordered and
+// pushed; an instance is entered when it is popped.
 //   ANY:  any hit in (0, tmax) other than triangle `skip`; true on a hit.
 //   else: nearest hit by (t, original index): prim (-1 = miss), pos =
 //         sorted position, tb = t.
@@ -169,10 +169,10 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
     const int4 lk = M::i4(reinterpret_cast<const int4*>(m + 6));
     float k0, k1, k2, k3;
     int v0 = lk.x, v1 = lk.y, v2 = lk.z, v3 = lk.w;
-    bool h0 = slab4(r, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tb, k0);
-    bool h1 = slab4(r, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tb, k1);
-    bool h2 = slab4(r, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tb, k2);
-    bool h3 = slab4(r, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tb, k3);
+    bool h0 = slab4<ANY>(r, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tb, k0);
+    bool h1 = slab4<ANY>(r, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tb, k1);
+    bool h2 = slab4<ANY>(r, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tb, k2);
+    bool h3 = slab4<ANY>(r, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tb, k3);
     if (in_body) {
       // triangle leaves: tested at once
       unsigned lm = (unsigned)(h0 && v0 < 0) | ((unsigned)(h1 && v1 < 0) << 1) | ((unsigned)(h2 && v2 < 0) << 2) |
@@ -204,12 +204,6 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
     if (cnt == 1) {
       cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
       continue;
-    }
-    if (ANY) {
-      k0 = -k0;
-      k1 = -k1;
-      k2 = -k2;
-      k3 = -k3;
     }
     k0 = h0 ? k0 : inf_f();
     k1 = h1 ? k1 : inf_f();
