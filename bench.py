@@ -182,6 +182,73 @@ def l2_read_probe(fb, torch, sizes_mb=(24, 48, 80), reps=40):
                    "L2-resident buffer, best of 5 launches per size, CUDA events"}
 
 
+def camera_rays(cam, x, y, k):
+    """Pinhole rays of samples (x, y, k) in float32, the render's camera
+    formula (4 spp: the rotated grid); for traversal statistics only."""
+    pos, tgt, up = (np.array(v, np.float64) for v in (cam.pos, cam.target, cam.up))
+    f = tgt - pos
+    f /= np.linalg.norm(f)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    f, r, u = (v.astype(np.float32) for v in (f, r, u))
+    sy = np.float32(np.tan(np.float64(cam.vfov_deg) * np.pi / 360.0))
+    sx = sy * np.float32(np.float32(cam.width) / np.float32(cam.height))
+    if cam.spp == 4:
+        ox = np.array([-0.125, 0.375, -0.375, 0.125], np.float32)[k]
+        oy = np.array([-0.375, -0.125, 0.125, 0.375], np.float32)[k]
+    else:
+        ox = oy = np.zeros(len(k), np.float32)
+    ndx = (np.float32(2) * (x.astype(np.float32) + (np.float32(0.5) + ox))) / np.float32(cam.width) - np.float32(1)
+    ndy = np.float32(1) - (np.float32(2) * (y.astype(np.float32) + (np.float32(0.5) + oy))) / np.float32(cam.height)
+    d = (ndx * sx)[:, None] * r + (ndy * sy)[:, None] * u + f
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    o = np.tile(np.array(cam.pos, np.float32), (len(d), 1))
+    return o, d
+
+
+def traversal_demand(G, cam, gb_host, nwarps=2048):
+    """Node steps, triangle tests and warp demand per ray of the frame's
+    primary and shadow passes, from the render kernels' traversal code run on
+    the host (fire_debug_trace_stats) over `nwarps` warps of each pass spread
+    evenly over it: a primary warp's task (4x2 pixels x 4 samples, or 8x4 x
+    1), and 32 consecutive shadow rays of the dense queue of the last render
+    (fire_debug_dump 12).  Demand bytes of a warp: distinct 4-wide nodes x
+    128 B + distinct triangle records x 48 B."""
+    spp = cam.spp
+    tw, rows = (4, 2) if spp == 4 else (8, 4)
+    tiles_x, tiles_y = -(-cam.width // tw), -(-cam.height // rows)
+    tasks = np.unique(np.linspace(0, tiles_x * tiles_y - 1, nwarps).astype(np.int64))
+    lane = np.arange(32)
+    q = lane >> 2 if spp == 4 else lane
+    k = lane & 3 if spp == 4 else np.zeros(32, np.int64)
+    x = ((tasks % tiles_x)[:, None] * tw + (q % tw)[None, :]).ravel()
+    y = ((tasks // tiles_x)[:, None] * rows + (q // tw)[None, :]).ravel()
+    kk = np.tile(k, len(tasks))
+    full = ((x < cam.width) & (y < cam.height)).reshape(-1, 32).all(1)  # tasks without idle lanes
+    keep = np.repeat(full, 32)
+    o, d = camera_rays(cam, x[keep], y[keep], kk[keep])
+    out = {}
+    prim = G.trace_stats(o, d, group=32)
+    q_rays = G.dump("shadow_rays")
+    sid = q_rays[:, 7].view(np.int32) >> 3
+    nq = len(q_rays) // 32
+    starts = np.unique(np.linspace(0, max(nq - 1, 0), min(nwarps, max(nq, 1))).astype(np.int64)) * 32
+    idx = (starts[:, None] + np.arange(32)[None, :]).ravel()
+    idx = idx[idx < len(q_rays)]
+    qs = q_rays[idx]
+    shad = G.trace_stats(qs[:, 0:3], qs[:, 4:7], tmax=qs[:, 3], skip=gb_host[sid[idx], 0], any_hit=True, group=32)
+    for name, st in (("primary", prim), ("shadow", shad)):
+        n = max(st["rays"], 1)
+        out[name] = {"rays_sampled": st["rays"], "warps_sampled": st["groups"],
+                     "node_steps_per_ray": st["node_steps"] / n, "tri_tests_per_ray": st["tri_tests"] / n,
+                     "warp_distinct_nodes_per_ray": st["group_nodes"] / n,
+                     "warp_distinct_tris_per_ray": st["group_tris"] / n,
+                     "demand_bytes_per_ray": (128 * st["group_nodes"] + 48 * st["group_tris"]) / n,
+                     "check": {"bad_loads": st["bad_loads"], "err": st["err"]}}
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -702,6 +769,8 @@ def main():
     shadow_rays = int(sum(((vis >> (8 + j)) & 1).sum().item() for j in range(len(lights))))
     primary_rays = cam.width * cam.height * cam.spp
     hits = int((gb[:, 0] >= 0).sum().item())
+    # traversal work and warp demand of this frame (host run of the kernels' traversal code)
+    demand = traversal_demand(G, cam, gb.cpu().numpy()) if rank == 0 else None
     del gb
 
     avg = {k: stages[k][0] / K for k in ("refit", "primary", "queue", "shadow", "resolve")}  # one of each per frame
@@ -730,6 +799,23 @@ def main():
         roofline["l2"] = {"bytes_per_launch": l2b, "achieved": got, "peak": probe["gbs"], "unit": "GB/s",
                           "frac": got / probe["gbs"], "peak_source": probe["how"],
                           "peak_buffer_mb": probe["buffer_mb"]}
+    # demand traffic of the traversal kernels: per warp, each distinct node and
+    # triangle record fetched once (what the warp asks of L2 if L1 kept
+    # nothing between warps), scaled to the frame's rays, over the live time
+    if demand is not None:
+        probe_gbs = roofline.get("l2", {}).get("peak") or l2_read_probe(fb, torch)["gbs"]
+        for name, rays in (("primary", primary_rays), ("shadow", shadow_rays)):
+            dm = demand[name]
+            dm["demand_bytes_per_launch"] = dm["demand_bytes_per_ray"] * rays
+            dm["achieved_gbs"] = dm["demand_bytes_per_launch"] / (avg[name] * 1e-3) / 1e9
+            dm["l2_frac"] = dm["achieved_gbs"] / probe_gbs
+            dm["hbm_frac"] = dm["achieved_gbs"] / peak
+        roofline["demand"] = {**demand, "l2_peak_gbs": probe_gbs,
+                              "bytes": "per warp: distinct 4-wide nodes x 128 B + distinct triangle records x 48 B",
+                              "sample": "2048 warps of each pass spread evenly over the frame (a primary task of "
+                                        "32 samples; 32 consecutive rays of the shadow queue in the shadow pass's "
+                                        "order); the render kernels' traversal code run on the host over copies "
+                                        "of the frame's tree (fire_debug_trace_stats)"}
     # the traversal kernels are issue-bound: warp instructions per launch (ncu)
     # over the live launch time, against 4 schedulers x 1 warp-inst/clock per SM
     clocks = clk.summary()

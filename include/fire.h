@@ -361,6 +361,11 @@ int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec* gbuf, cons
  * 10 its record                         16 B: float eps, float span, int32 nodes
  *                                       in use, int32 error (nonzero: not built)
  * 11 body matrices of the current buffer float[nbody*12]
+ * any scene:
+ * 12 the last fire_render's shadow rays in the order its shadow pass takes
+ *    them (light by light, each light's rays in task order)  float[n*8]:
+ *    origin xyz, t_max, unit direction xyz, sample * 8 + light (int bits);
+ *    n = fire_render_info out[3] (0 before any render)
  * bytes must equal the exact size; otherwise FIRE_ERR_INVALID_ARG. */
 int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes);
 
@@ -384,19 +389,34 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes);
  * (FIRE_ERR_NOT_BUILT until the next fire_bvh_build). */
 int fire_scene_set_two_level(fire_scene s, int32_t enable);
 
-/* Check of the two-level traversal on the host (test hook; synchronises the
- * device): the scene's current structures are copied to host memory and
- * the traversal code of the render kernels, compiled for the host, runs the
- * n rays o3/d3 (host float[n*3]; the direction need not be unit).  any = 0:
- * nearest hit over (0, inf) -> prim (original index or -1) and t; any = 1:
- * any hit in (0, tmax[i]) other than triangle skip[i] (skip may be NULL) ->
- * hit[i].  Every load is checked to lie inside the copied arrays and be
- * aligned for its width.  err_out: the traversal's error bits (1 stack,
- * 2 iteration cap, 4 a link outside the structure) | 0x100 if any load
- * failed the check.  Outputs may be NULL.  Single-level scene ->
- * FIRE_ERR_INVALID_ARG. */
+/* Check of the traversal on the host (test hook; synchronises the device):
+ * the scene's current structures (the 4-wide tree and its triangle records,
+ * or the two-level structure) are copied to host memory and the traversal
+ * code of the render kernels, compiled for the host, runs the n rays o3/d3
+ * (host float[n*3]; the direction need not be unit).  any = 0: nearest hit
+ * over (0, inf) -> prim (original index or -1) and t; any = 1: any hit in
+ * (0, tmax[i]) other than triangle skip[i] (skip may be NULL) -> hit[i].
+ * Every load is checked to lie inside the copied arrays and be aligned for
+ * its width.  err_out: the traversal's error bits (1 stack, 2 iteration cap,
+ * 4 a link outside the structure) | 0x100 if any load failed the check.
+ * Outputs may be NULL. */
 int fire_debug_trace_host(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip,
                           int64_t n, int32_t any, int32_t* prim, float* t, uint8_t* hit, uint32_t* err_out);
+
+/* Traversal work and memory demand (measurement aid; synchronises the
+ * device): the rays of fire_debug_trace_host, run the same way, in groups
+ * of `group` consecutive rays (32: the rays a warp of the primary or shadow
+ * pass takes together; the last group may be shorter).  A node step is one
+ * fetch of a 4-wide node (7 x 16 B of its 128 B), a triangle test one fetch
+ * of a 48-B record.  out8 (host int64[8]): [0] rays, [1] node steps, [2]
+ * triangle tests, [3] the sum over groups of the distinct nodes the group
+ * fetched, [4] of the distinct triangle records, [5] groups, [6] loads that
+ * failed the check (0), [7] the traversal's error bits.  Demand bytes of a
+ * group = distinct nodes x 128 + distinct records x 48: what its warp asks
+ * of L2, once per node and record, when L1 keeps nothing between warps.
+ * group < 1 -> FIRE_ERR_INVALID_ARG. */
+int fire_debug_trace_stats(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip,
+                           int64_t n, int32_t any, int32_t group, int64_t* out8);
 
 /* Synchronise `stream`, then return and clear the scene's sticky device error
  * (FIRE_OK, FIRE_ERR_STACK_OVERFLOW or FIRE_ERR_TIMEOUT). */

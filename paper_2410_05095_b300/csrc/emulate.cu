@@ -1,13 +1,22 @@
-// Host emulation of the two-level traversal (a check, not a render path):
-// the device structures of a built two-level scene are copied to host
-// memory and the traversal code the render kernels run (traverse2, compiled
-// here for the host) walks them for the caller's rays.  Every load goes
-// through HostCheckedLoads, which verifies that the address lies inside one
-// of the copied arrays and is aligned for its width (16 B for the vector
-// loads, 4 B for scalars -- the device arrays themselves are 256-B aligned by
+// Host emulation of the traversal (a check and a measurement aid, not a
+// render path): the device structures of a built scene are copied to host
+// memory and the traversal code the render kernels run (traverse for the
+// single-level tree, traverse2 for the two-level structure, compiled here
+// for the host) walks them for the caller's rays.  Every load goes through
+// HostCheckedLoads, which verifies that the address lies inside one of the
+// copied arrays and is aligned for its width (16 B for the vector loads, 4 B
+// for scalars -- the device arrays themselves are 256-B aligned by
 // cudaMalloc, which fire_scene checks); a violation is counted, the load
 // returns zeros, and the call reports it.  The kernels' own index checks run
 // here unchanged.
+//
+// The same loads give the traversal's work and demand: a node step is one
+// fetch of a 4-wide node's link vector (the last of its seven 16-B loads),
+// a triangle test one fetch of a record's first vector; for groups of rays
+// taken together (32: a warp of the primary or shadow pass) the distinct
+// nodes and triangles the group fetched are what its warp asks of the
+// memory system, once each.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -16,18 +25,44 @@
 namespace fire {
 namespace {
 
+enum RegionKind { kNodes = 0, kTris = 1, kOther = 2 };
+
 struct Region {
   const char* base;
   size_t bytes;
+  int kind;
 };
 thread_local std::vector<Region> g_regions;
 thread_local uint64_t g_bad_loads = 0;
 
+// visit records of the current group (node key = region << 40 | node index)
+struct Visits {
+  bool on = false;
+  int64_t steps = 0, tests = 0;
+  std::vector<int64_t> nodes, tris;
+};
+thread_local Visits g_visits;
+
 template <class T>
 bool load_ok(const T* p) {
   const char* c = reinterpret_cast<const char*>(p);
-  for (const Region& r : g_regions)
-    if (c >= r.base && c + sizeof(T) <= r.base + r.bytes) return ((size_t)(c - r.base) % sizeof(T)) == 0;
+  for (size_t k = 0; k < g_regions.size(); ++k) {
+    const Region& r = g_regions[k];
+    if (c >= r.base && c + sizeof(T) <= r.base + r.bytes) {
+      const size_t off = (size_t)(c - r.base);
+      if (off % sizeof(T) != 0) return false;
+      if (g_visits.on) {
+        if (r.kind == kNodes && sizeof(T) == 16 && off % sizeof(Node4) == 96) {  // a node's link vector
+          ++g_visits.steps;
+          g_visits.nodes.push_back(((int64_t)k << 40) | (int64_t)(off / sizeof(Node4)));
+        } else if (r.kind == kTris && off % 48 == 0) {  // a record's first vector
+          ++g_visits.tests;
+          g_visits.tris.push_back((int64_t)(off / 48));
+        }
+      }
+      return true;
+    }
+  }
   return false;
 }
 
@@ -42,7 +77,7 @@ T checked_load(const T* p) {
   return *p;
 }
 
-// (host and device members only because traverse2 is a host-and-device
+// (host and device members only because the traversal is a host-and-device
 // template; the device side is never called)
 struct HostCheckedLoads {
 #ifdef __CUDA_ARCH__
@@ -60,26 +95,58 @@ struct HostCheckedLoads {
 #endif
 };
 
+// Totals over groups: [0] rays, [1] node steps, [2] triangle tests, [3] sum
+// of the distinct nodes per group, [4] of the distinct triangles, [5] groups.
+struct GroupTotals {
+  int64_t v[6] = {0, 0, 0, 0, 0, 0};
+  void close_group() {
+    auto distinct = [](std::vector<int64_t>& x) {
+      std::sort(x.begin(), x.end());
+      const int64_t n = std::unique(x.begin(), x.end()) - x.begin();
+      x.clear();
+      return n;
+    };
+    v[1] += g_visits.steps;
+    v[2] += g_visits.tests;
+    v[3] += distinct(g_visits.nodes);
+    v[4] += distinct(g_visits.tris);
+    v[5] += 1;
+    g_visits.steps = g_visits.tests = 0;
+  }
+};
+
+// One ray through the structure the view describes.
 template <int STACK>
-void run(const Trace2View& v, const float* o3, const float* d3, const float* tmax, const int32_t* skip, int64_t n,
-         bool any, int32_t* prim, float* t, uint8_t* hit) {
+bool trace_one(const Trace2View* v2, const TraceCtx* v1, float3 o, float3 d, bool any, float tmax, int skip, int& p,
+               float& tb) {
+  int pos = -1;
+  if (v2) {
+    if (any) return traverse2<HostCheckedLoads, STACK, true>(*v2, o, d, tmax, skip, p, pos, tb);
+    traverse2<HostCheckedLoads, STACK, false>(*v2, o, d, 0.0f, -1, p, pos, tb);
+  } else {
+    if (any) return traverse<HostCheckedLoads, STACK, true>(*v1, o, d, tmax, skip, p, pos, tb);
+    traverse<HostCheckedLoads, STACK, false>(*v1, o, d, 0.0f, -1, p, pos, tb);
+  }
+  return p >= 0;
+}
+
+template <int STACK>
+void run(const Trace2View* v2, const TraceCtx* v1, const float* o3, const float* d3, const float* tmax,
+         const int32_t* skip, int64_t n, bool any, int32_t* prim, float* t, uint8_t* hit, int group,
+         GroupTotals* tot) {
   for (int64_t i = 0; i < n; ++i) {
+    if (tot && i > 0 && i % group == 0) tot->close_group();
     const float3 o = f3(o3[3 * i], o3[3 * i + 1], o3[3 * i + 2]);
     const float3 d = f3(d3[3 * i], d3[3 * i + 1], d3[3 * i + 2]);
-    int p = -1, pos = -1;
+    int p = -1;
     float tb = 0.0f;
-    bool h;
-    if (any) {
-      h = traverse2<HostCheckedLoads, STACK, true>(v, o, d, tmax ? tmax[i] : inf_f(), skip ? skip[i] : -1, p, pos,
-                                                   tb);
-    } else {
-      traverse2<HostCheckedLoads, STACK, false>(v, o, d, 0.0f, -1, p, pos, tb);
-      h = p >= 0;
-    }
+    const bool h = trace_one<STACK>(v2, v1, o, d, any, tmax ? tmax[i] : inf_f(), skip ? skip[i] : -1, p, tb);
     if (prim) prim[i] = any ? -1 : p;
     if (t) t[i] = any ? 0.0f : tb;
     if (hit) hit[i] = h ? 1 : 0;
   }
+  if (tot && n > 0) tot->close_group();
+  if (tot) tot->v[0] += n;
 }
 
 template <class T>
@@ -87,6 +154,65 @@ int fetch(std::vector<T>& h, const void* dev, size_t count) {
   h.resize(count > 0 ? count : 1);
   if (count == 0) return FIRE_OK;
   return cuda_check(cudaMemcpy(h.data(), dev, count * sizeof(T), cudaMemcpyDeviceToHost), "emulation copy");
+}
+
+// Copies the scene's current structures and runs the rays (group > 0:
+// visit totals into tot).
+int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip, int64_t n,
+            bool any, int32_t* prim, float* t, uint8_t* hit, uint32_t* err_out, int group, GroupTotals* tot) {
+  if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "emulation before build");
+  *err_out = 0;
+  if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
+  std::vector<Node4> tlas, nodes;
+  std::vector<float4> tris;
+  std::vector<int32_t> roots;
+  std::vector<float> xf;
+  std::vector<TlasInfo> info;
+  const size_t nb = (size_t)s->nbody;
+  const int64_t cap = s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64;
+  if (int e = fetch(nodes, s->nodes4, (size_t)s->n4)) return e;
+  if (int e = fetch(tris, s->tris, 3 * (size_t)s->nt)) return e;
+  g_regions.clear();
+  if (s->two_level) {
+    if (int e = fetch(info, s->tinfo, 1)) return e;
+    if (int e = fetch(tlas, s->tlas, nb + 2)) return e;
+    if (int e = fetch(roots, s->blas_root, nb)) return e;
+    if (int e = fetch(xf, s->xf_buf[s->cur], 12 * nb)) return e;
+    if (info[0].err) *err_out |= kErrStack;
+    g_regions.push_back({reinterpret_cast<const char*>(tlas.data()), sizeof(Node4) * (nb + 2), kNodes});
+  }
+  g_regions.push_back({reinterpret_cast<const char*>(nodes.data()), sizeof(Node4) * (size_t)s->n4, kNodes});
+  g_regions.push_back({reinterpret_cast<const char*>(tris.data()), sizeof(float4) * 3 * (size_t)s->nt, kTris});
+  if (s->two_level) {
+    g_regions.push_back({reinterpret_cast<const char*>(roots.data()), 4 * nb, kOther});
+    g_regions.push_back({reinterpret_cast<const char*>(xf.data()), 48 * nb, kOther});
+  }
+  g_bad_loads = 0;
+  g_visits = Visits{};
+  uint32_t err = 0;
+  Trace2View v2{};
+  TraceCtx v1{};
+  if (s->two_level) {
+    const TlasInfo ti = info[0];
+    v2 = Trace2View{tlas.data(), std::min<int64_t>(ti.n, (int64_t)nb + 2), nodes.data(), s->n4, tris.data(), s->nt,
+                    roots.data(), xf.data(), s->nbody, ti.span, cap, &err};
+  } else {
+    v1 = TraceCtx{nodes.data(), s->n4, scene_span<HostCheckedLoads>(nodes.data(), s->nt), tris.data(), s->nt, cap,
+                  &err};
+  }
+  g_visits.on = tot != nullptr;  // (after the span's root-box loads)
+  const Trace2View* p2 = s->two_level ? &v2 : nullptr;
+  const TraceCtx* p1 = s->two_level ? nullptr : &v1;
+  switch (stack_for_height(stack_need(s), 0)) {
+    case 32: run<32>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
+    case 64: run<64>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
+    default: run<128>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
+  }
+  g_visits = Visits{};
+  g_regions.clear();
+  *err_out |= err;
+  if (g_bad_loads) *err_out |= 0x100u;
+  return FIRE_OK;
 }
 
 }  // namespace
@@ -100,41 +226,19 @@ extern "C" int fire_debug_trace_host(fire_scene s, const float* o3, const float*
   set_error(FIRE_OK, "");
   if (!s || !err_out || (n > 0 && (!o3 || !d3)) || n < 0)
     return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
-  if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "emulation before build");
-  if (!s->two_level) return set_error(FIRE_ERR_INVALID_ARG, "the emulation covers the two-level structure");
-  *err_out = 0;
-  if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
-  std::vector<Node4> tlas, blas;
-  std::vector<float4> tris;
-  std::vector<int32_t> roots;
-  std::vector<float> xf;
-  std::vector<TlasInfo> info;
-  const size_t nb = (size_t)s->nbody;
-  if (int e = fetch(info, s->tinfo, 1)) return e;
-  if (int e = fetch(tlas, s->tlas, nb + 2)) return e;
-  if (int e = fetch(blas, s->nodes4, (size_t)s->n4)) return e;
-  if (int e = fetch(tris, s->tris, 3 * (size_t)s->nt)) return e;
-  if (int e = fetch(roots, s->blas_root, nb)) return e;
-  if (int e = fetch(xf, s->xf_buf[s->cur], 12 * nb)) return e;
-  const TlasInfo ti = info[0];
-  if (ti.err) *err_out |= kErrStack;
-  g_regions.clear();
-  g_regions.push_back({reinterpret_cast<const char*>(tlas.data()), sizeof(Node4) * (nb + 2)});
-  g_regions.push_back({reinterpret_cast<const char*>(blas.data()), sizeof(Node4) * (size_t)s->n4});
-  g_regions.push_back({reinterpret_cast<const char*>(tris.data()), sizeof(float4) * 3 * (size_t)s->nt});
-  g_regions.push_back({reinterpret_cast<const char*>(roots.data()), 4 * nb});
-  g_regions.push_back({reinterpret_cast<const char*>(xf.data()), 48 * nb});
-  g_bad_loads = 0;
+  return emulate(s, o3, d3, tmax, skip, n, any != 0, prim, t, hit, err_out, 0, nullptr);
+}
+
+extern "C" int fire_debug_trace_stats(fire_scene s, const float* o3, const float* d3, const float* tmax,
+                                      const int32_t* skip, int64_t n, int32_t any, int32_t group, int64_t* out8) {
+  set_error(FIRE_OK, "");
+  if (!s || !out8 || (n > 0 && (!o3 || !d3)) || n < 0) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
+  if (group < 1) return set_error(FIRE_ERR_INVALID_ARG, "group must be >= 1");
+  GroupTotals tot;
   uint32_t err = 0;
-  Trace2View v{tlas.data(), std::min<int64_t>(ti.n, (int64_t)nb + 2), blas.data(), s->n4, tris.data(), s->nt,
-               roots.data(), xf.data(), s->nbody, ti.span, s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64, &err};
-  switch (stack_for_height(stack_need(s), 0)) {
-    case 32: run<32>(v, o3, d3, tmax, skip, n, any != 0, prim, t, hit); break;
-    case 64: run<64>(v, o3, d3, tmax, skip, n, any != 0, prim, t, hit); break;
-    default: run<128>(v, o3, d3, tmax, skip, n, any != 0, prim, t, hit); break;
-  }
-  g_regions.clear();
-  *err_out |= err;
-  if (g_bad_loads) *err_out |= 0x100u;
+  if (int e = emulate(s, o3, d3, tmax, skip, n, any != 0, nullptr, nullptr, nullptr, &err, group, &tot)) return e;
+  for (int k = 0; k < 6; ++k) out8[k] = tot.v[k];
+  out8[6] = g_bad_loads;
+  out8[7] = err;
   return FIRE_OK;
 }

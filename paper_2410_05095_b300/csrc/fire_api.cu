@@ -883,6 +883,33 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
       if (what == 10) return need(sizeof(TlasInfo)) ? get(host_dst, s->tinfo, sizeof(TlasInfo)) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
       return need(48 * nb) ? get(host_dst, s->xf_buf[s->cur], 48 * nb) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
     }
+    case 12: {  // the last fire_render's shadow rays, in the order the shadow pass takes them
+      int64_t cnt[kMaxLights] = {0}, nr = 0;
+      if (s->rendered && s->jobs && s->qperm && s->last_nlights > 0) {
+        uint32_t w[32];
+        if (int e = get(w, s->ctrl, sizeof(w))) return e;
+        for (int j = 0; j < s->last_nlights; ++j) nr += cnt[j] = w[kCtrlShadowLen + j];
+      }
+      if (!need(32 * (size_t)nr)) break;
+      const int64_t seg = s->last_qseg;
+      std::vector<int32_t> perm;
+      std::vector<float4> jobs;
+      float4* o = reinterpret_cast<float4*>(host_dst);
+      for (int j = 0; j < s->last_nlights; ++j) {
+        if (cnt[j] == 0) continue;
+        if (cnt[j] > seg) return set_error(FIRE_ERR_CUDA, "shadow queue longer than its segment");
+        perm.resize((size_t)cnt[j]);
+        jobs.resize(2 * (size_t)seg);
+        if (int e = get(perm.data(), s->qperm + j * seg, 4 * (size_t)cnt[j])) return e;
+        if (int e = get(jobs.data(), s->jobs + 2 * j * seg, 32 * (size_t)seg)) return e;
+        for (int64_t k = 0; k < cnt[j]; ++k) {
+          if (perm[k] < 0 || perm[k] >= seg) return set_error(FIRE_ERR_CUDA, "shadow queue order out of range");
+          *o++ = jobs[2 * (size_t)perm[k]];
+          *o++ = jobs[2 * (size_t)perm[k] + 1];
+        }
+      }
+      return FIRE_OK;
+    }
     default:
       return set_error(FIRE_ERR_INVALID_ARG, "unknown dump selector");
   }

@@ -225,6 +225,8 @@ struct fire_scene_s {
   cudaStream_t last_stream = nullptr;
   bool rendered = false;        // a fire_render ran (fire_render_info)
   bool last_raster = false;     // its primary pass rasterised
+  int64_t last_qseg = 0;        // its shadow queue: slots per light segment
+  int last_nlights = 0;         // and lights
   void* prof = nullptr;         // fire::Profiler when enabled
 };
 

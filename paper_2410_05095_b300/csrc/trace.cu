@@ -581,6 +581,8 @@ int render_frame(fire_scene_s* s, const RenderArgs& a, const fire_render_opts& o
   raster = raster && s->rkeys && s->pieces && s->graze && a.cam.W < 65536 && a.cam.H < 65536;
   s->rendered = true;
   s->last_raster = raster;
+  s->last_qseg = a.qseg;
+  s->last_nlights = a.lights.n;
   if (a.tlas) {  // two-level (no raster pass: fire_render refuses the flag)
     switch (stack_for_height(stack_need(s), o.stack_depth)) {
       case 8: return launch_render<8, true>(s, a, g, ntasks, o, false, st);

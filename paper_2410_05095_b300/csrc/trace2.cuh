@@ -38,25 +38,6 @@ struct Trace2View {
   uint32_t* err;          // sticky error word
 };
 
-// Device loads (read-only path) and a sticky error word.  (The host side of
-// these members exists only because traverse2 is a host-and-device
-// template; host code uses its own policy.)
-struct DeviceLoads {
-#ifdef __CUDA_ARCH__
-  __host__ __device__ static float4 f4(const float4* p) { return __ldg(p); }
-  __host__ __device__ static int4 i4(const int4* p) { return __ldg(p); }
-  __host__ __device__ static float f1(const float* p) { return __ldg(p); }
-  __host__ __device__ static int i1(const int32_t* p) { return __ldg(p); }
-  __host__ __device__ static void fail(uint32_t* e, uint32_t bits) { atomicOr(e, bits); }
-#else
-  __host__ __device__ static float4 f4(const float4* p) { return *p; }
-  __host__ __device__ static int4 i4(const int4* p) { return *p; }
-  __host__ __device__ static float f1(const float* p) { return *p; }
-  __host__ __device__ static int i1(const int32_t* p) { return *p; }
-  __host__ __device__ static void fail(uint32_t* e, uint32_t bits) { *e |= bits; }
-#endif
-};
-
 // o' = R^T (o - t), d' = R^T d for the row-major 3x4 matrix m.
 __host__ __device__ __forceinline__ void object_ray(const float m[12], float3 o, float3 d, float3& oo, float3& dd) {
   const float3 q = sub3(o, f3(m[3], m[7], m[11]));

@@ -97,6 +97,36 @@ __host__ __device__ __forceinline__ bool mt_t(float3 o, float3 d, float4 A, floa
   return true;
 }
 
+// Memory policy of the traversal code, which is written once for the device
+// and the host: DeviceLoads (read-only-path __ldg loads, atomicOr on the
+// sticky error word) in the kernels; the host emulation passes a policy that
+// checks every load.  (The host side of these members exists only because
+// the traversal is a host-and-device template; host code uses its own.)
+struct DeviceLoads {
+#ifdef __CUDA_ARCH__
+  __host__ __device__ static float4 f4(const float4* p) { return __ldg(p); }
+  __host__ __device__ static int4 i4(const int4* p) { return __ldg(p); }
+  __host__ __device__ static float f1(const float* p) { return __ldg(p); }
+  __host__ __device__ static int i1(const int32_t* p) { return __ldg(p); }
+  __host__ __device__ static void fail(uint32_t* e, uint32_t bits) { atomicOr(e, bits); }
+#else
+  __host__ __device__ static float4 f4(const float4* p) { return *p; }
+  __host__ __device__ static int4 i4(const int4* p) { return *p; }
+  __host__ __device__ static float f1(const float* p) { return *p; }
+  __host__ __device__ static int i1(const int32_t* p) { return *p; }
+  __host__ __device__ static void fail(uint32_t* e, uint32_t bits) { *e |= bits; }
+#endif
+};
+
+// Index of the lowest set bit of a non-zero mask.
+__host__ __device__ __forceinline__ int lowest_slot(unsigned m) {
+#ifdef __CUDA_ARCH__
+  return __ffs(m) - 1;
+#else
+  return __builtin_ctz(m);
+#endif
+}
+
 struct TraceCtx {
   const Node4* __restrict__ nodes4;  // 4-wide traversal tree
   int64_t n4;
@@ -112,14 +142,14 @@ constexpr int kDone = 0x7fffffff;  // stack sentinel: nothing left to visit
 // Leaf = one triangle at sorted position ~code.  Nearest mode updates the
 // (t, original index) minimum; any mode returns true on a hit in (0, tmax)
 // that is not triangle `skip`.
-template <bool ANY>
-__device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o, float3 d, float tmax, int skip,
-                                          int& prim, int& pos, float& tb) {
+template <class M, bool ANY>
+__host__ __device__ __forceinline__ bool leaf_test(const TraceCtx& c, int code, float3 o, float3 d, float tmax,
+                                                   int skip, int& prim, int& pos, float& tb) {
   int p = ~code;
   if ((uint64_t)p >= (uint64_t)c.nt) p = 0;  // never for a built tree (keeps loads in bounds)
   const float4* tr = c.tris + 3 * (int64_t)p;
-  float4 A = __ldg(tr), B = __ldg(tr + 1), C = __ldg(tr + 2);
-  int orig = __float_as_int(A.w);
+  float4 A = M::f4(tr), B = M::f4(tr + 1), C = M::f4(tr + 2);
+  int orig = float_as_bits(A.w);
   float t;
   if (ANY) return orig != skip && mt_t(o, d, A, B, C, t) && t > 0.0f && t < tmax;
   if (mt_t(o, d, A, B, C, t) && t > 0.0f && t < inf_f() && (t < tb || (t == tb && orig < prim))) {
@@ -238,9 +268,9 @@ __host__ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, in
 //   else: nearest hit in (0, inf) by (t, original index) -- independent of
 //         the visiting order; prim = original index (-1 = miss), pos = sorted
 //         position, tb = t.
-template <int STACK, bool ANY>
-__device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, float tmax, int skip, int& prim,
-                                         int& pos, float& tb) {
+template <class M, int STACK, bool ANY>
+__host__ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, float tmax, int skip,
+                                                  int& prim, int& pos, float& tb) {
   prim = -1;
   pos = -1;
   tb = ANY ? tmax : inf_f();
@@ -251,20 +281,20 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
   stack[0] = kDone;
   int sp = 1;
   int cur = 0;  // 4-wide node, or kDone
-  int budget = (int)min(c.cap, (int64_t)0x7fffffff);
+  int budget = (int)(c.cap < (int64_t)0x7fffffff ? c.cap : (int64_t)0x7fffffff);
   while (cur != kDone) {
     if (--budget < 0) {
-      atomicOr(c.err, kErrTimeout);
+      M::fail(c.err, kErrTimeout);
       return false;
     }
     if ((uint32_t)cur >= n4) {  // never for a built tree
-      atomicOr(c.err, kErrCorrupt);
+      M::fail(c.err, kErrCorrupt);
       return false;
     }
     const float4* m = &c.nodes4[cur].lox;  // lox loy loz hix hiy hiz link
-    const float4 nx = __ldg(m + r.nx), ny = __ldg(m + r.ny), nz = __ldg(m + r.nz);
-    const float4 fx = __ldg(m + r.fx), fy = __ldg(m + r.fy), fz = __ldg(m + r.fz);
-    const int4 lk = __ldg(reinterpret_cast<const int4*>(m + 6));
+    const float4 nx = M::f4(m + r.nx), ny = M::f4(m + r.ny), nz = M::f4(m + r.nz);
+    const float4 fx = M::f4(m + r.fx), fy = M::f4(m + r.fy), fz = M::f4(m + r.fz);
+    const int4 lk = M::i4(reinterpret_cast<const int4*>(m + 6));
     float k0, k1, k2, k3;
     int v0 = lk.x, v1 = lk.y, v2 = lk.z, v3 = lk.w;
     bool h0 = slab4<ANY>(r, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tb, k0);
@@ -280,10 +310,10 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
     h2 = h2 && !(lm & 4u);
     h3 = h3 && !(lm & 8u);
     while (lm) {
-      const int slot = __ffs(lm) - 1;
+      const int slot = lowest_slot(lm);
       lm &= lm - 1;
       const int code = slot == 0 ? v0 : slot == 1 ? v1 : slot == 2 ? v2 : v3;
-      if (leaf_test<ANY>(c, code, o, d, tmax, skip, prim, pos, tb)) return true;
+      if (leaf_test<M, ANY>(c, code, o, d, tmax, skip, prim, pos, tb)) return true;
     }
     const int cnt = (int)h0 + (int)h1 + (int)h2 + (int)h3;
     if (cnt == 0) {
@@ -314,7 +344,7 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
       if (cnt >= 3) stack[sp++] = v2;
       stack[sp++] = v1;
     } else {
-      atomicOr(c.err, kErrStack);
+      M::fail(c.err, kErrStack);
     }
     cur = v0;
   }
@@ -324,14 +354,14 @@ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, float3 d, 
 template <int STACK>
 __device__ __forceinline__ void trace_nearest(const TraceCtx& c, float3 o, float3 d, int& prim, int& pos,
                                               float& tb) {
-  traverse<STACK, false>(c, o, d, 0.0f, -1, prim, pos, tb);
+  traverse<DeviceLoads, STACK, false>(c, o, d, 0.0f, -1, prim, pos, tb);
 }
 
 template <int STACK>
 __device__ __forceinline__ bool trace_any(const TraceCtx& c, float3 o, float3 d, float tmax, int skip) {
   int prim, pos;
   float tb;
-  return traverse<STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
+  return traverse<DeviceLoads, STACK, true>(c, o, d, tmax, skip, prim, pos, tb);
 }
 
 // ---------------------------------------------------------------------------
@@ -379,11 +409,12 @@ __device__ __forceinline__ float3 shading_normal(const SmoothCtx& c, int pos, fl
 
 // Scene box = union of the 4-wide root's child boxes (the same exact min/max
 // as the binary root's box).
-__device__ __forceinline__ void root_box(const Node4* nodes4, float3& lo, float3& hi) {
+template <class M = DeviceLoads>
+__host__ __device__ __forceinline__ void root_box(const Node4* nodes4, float3& lo, float3& hi) {
   const Node4* r = nodes4;
-  const int4 lk = __ldg(&r->link);
-  const float4 lx = __ldg(&r->lox), ly = __ldg(&r->loy), lz = __ldg(&r->loz);
-  const float4 hx = __ldg(&r->hix), hy = __ldg(&r->hiy), hz = __ldg(&r->hiz);
+  const int4 lk = M::i4(&r->link);
+  const float4 lx = M::f4(&r->lox), ly = M::f4(&r->loy), lz = M::f4(&r->loz);
+  const float4 hx = M::f4(&r->hix), hy = M::f4(&r->hiy), hz = M::f4(&r->hiz);
   const int l[4] = {lk.x, lk.y, lk.z, lk.w};
   const float LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w}, LZ[4] = {lz.x, lz.y, lz.z, lz.w};
   const float HX[4] = {hx.x, hx.y, hx.z, hx.w}, HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
@@ -407,10 +438,11 @@ __device__ __forceinline__ float scene_eps(const Node4* nodes4, int64_t nt) {
 }
 
 // Largest |coordinate| of the scene box (scale of the box-test slack).
-__device__ __forceinline__ float scene_span(const Node4* nodes4, int64_t nt) {
+template <class M = DeviceLoads>
+__host__ __device__ __forceinline__ float scene_span(const Node4* nodes4, int64_t nt) {
   if (nt == 0) return 0.0f;
   float3 lo, hi;
-  root_box(nodes4, lo, hi);
+  root_box<M>(nodes4, lo, hi);
   return fmax3f(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y)), fmaxf(fabsf(lo.z), fabsf(hi.z)));
 }
 

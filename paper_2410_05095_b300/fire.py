@@ -20,7 +20,8 @@ ERRORS = {-1: "FIRE_ERR_INVALID_ARG", -2: "FIRE_ERR_OOM", -3: "FIRE_ERR_CUDA",
           -4: "FIRE_ERR_STACK_OVERFLOW", -5: "FIRE_ERR_TIMEOUT", -6: "FIRE_ERR_NOT_BUILT"}
 
 DUMP = {"morton": 0, "order": 1, "children": 2, "parent": 3, "boxes": 4, "tris": 5,
-        "centroid_bounds": 6, "nodes4": 7, "blas_root": 8, "tlas": 9, "tlas_info": 10, "body_xforms": 11}
+        "centroid_bounds": 6, "nodes4": 7, "blas_root": 8, "tlas": 9, "tlas_info": 10, "body_xforms": 11,
+        "shadow_rays": 12}
 
 EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials", "fire_scene_info",
            "fire_bvh_build", "fire_bvh_refit", "fire_render", "fire_render_batch", "fire_shade",
@@ -29,7 +30,7 @@ EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials"
            "fire_profile_enable", "fire_profile_read", "fire_shade_backward_noalloc", "fire_render_info",
            "fire_display", "fire_scene_set_materials_ex", "fire_scene_set_normals", "fire_probe_read",
            "fire_scene_set_two_level", "fire_debug_trace_host", "fire_batch_last_tuning", "fire_last_error",
-           "fire_version"]
+           "fire_version", "fire_debug_trace_stats"]
 
 STAGES = ["refit", "primary", "shadow", "build", "shade_gbuf", "backward", "resolve", "queue"]
 
@@ -97,6 +98,7 @@ def lib():
             "fire_probe_read": [P, i64, i32, P, i32, P],
             "fire_scene_set_two_level": [P, i32],
             "fire_debug_trace_host": [P, P, P, P, P, i64, i32, P, P, P, P],
+            "fire_debug_trace_stats": [P, P, P, P, P, i64, i32, i32, P],
             "fire_batch_last_tuning": [P, P],
         }
         for name, args in sig.items():
@@ -285,8 +287,8 @@ class Scene:
         _check(lib().fire_scene_set_two_level(self.h, int(bool(enable))))
 
     def trace_host(self, o, d, tmax=None, skip=None, any_hit=False):
-        """Host emulation of the two-level traversal (fire_debug_trace_host):
-        returns (prim, t, hit, error bits) for rays o, d [n, 3]."""
+        """Host emulation of the traversal (fire_debug_trace_host): returns
+        (prim, t, hit, error bits) for rays o, d [n, 3]."""
         o = np.ascontiguousarray(o, np.float32)
         d = np.ascontiguousarray(d, np.float32)
         n = len(o)
@@ -299,6 +301,19 @@ class Scene:
                                            _ptr(prim), _ptr(t), _ptr(hit), C.byref(err)))
         return prim, t, hit.astype(bool), int(err.value)
 
+    def trace_stats(self, o, d, tmax=None, skip=None, any_hit=False, group=32) -> dict:
+        """Traversal work and demand of rays o, d [n, 3] in groups of `group`
+        (fire_debug_trace_stats)."""
+        o = np.ascontiguousarray(o, np.float32)
+        d = np.ascontiguousarray(d, np.float32)
+        tm = None if tmax is None else np.ascontiguousarray(tmax, np.float32)
+        sk = None if skip is None else np.ascontiguousarray(skip, np.int32)
+        out = np.zeros(8, np.int64)
+        _check(lib().fire_debug_trace_stats(self.h, _ptr(o), _ptr(d), _ptr(tm), _ptr(sk), len(o),
+                                            int(bool(any_hit)), int(group), _ptr(out)))
+        keys = ("rays", "node_steps", "tri_tests", "group_nodes", "group_tris", "groups", "bad_loads", "err")
+        return dict(zip(keys, (int(x) for x in out)))
+
     def dump(self, what: str) -> np.ndarray:
         T = self.nt
         nb = self.nbody
@@ -308,6 +323,8 @@ class Scene:
                   "centroid_bounds": (np.float32, (6,)), "nodes4": (np.float32, (self.info()["n4"], 32)),
                   "blas_root": (np.int32, (nb,)), "tlas": (np.float32, (nb + 2, 32)),
                   "tlas_info": (np.float32, (4,)), "body_xforms": (np.float32, (nb, 12))}
+        if what == "shadow_rays":
+            shapes[what] = (np.float32, (self.render_info()["shadow_rays"], 8))
         dt, shp = shapes[what]
         out = np.zeros(shp, dt)
         _check(lib().fire_debug_dump(self.h, DUMP[what], _ptr(out), out.nbytes))
