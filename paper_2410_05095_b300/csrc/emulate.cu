@@ -166,7 +166,7 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   std::vector<Node4> tlas, nodes;
   std::vector<float4> tris;
   std::vector<int32_t> roots;
-  std::vector<float> xf;
+  std::vector<float4> xf;  // 3 rows per body (16-B aligned, as the device buffer)
   std::vector<TlasInfo> info;
   const size_t nb = (size_t)s->nbody;
   const int64_t cap = s->iter_cap > 0 ? s->iter_cap : 2 * s->nt + 64;
@@ -177,7 +177,7 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
     if (int e = fetch(info, s->tinfo, 1)) return e;
     if (int e = fetch(tlas, s->tlas, nb + 2)) return e;
     if (int e = fetch(roots, s->blas_root, nb)) return e;
-    if (int e = fetch(xf, s->xf_buf[s->cur], 12 * nb)) return e;
+    if (int e = fetch(xf, s->xf_buf[s->cur], 3 * nb)) return e;
     if (info[0].err) *err_out |= kErrStack;
     g_regions.push_back({reinterpret_cast<const char*>(tlas.data()), sizeof(Node4) * (nb + 2), kNodes});
   }
@@ -195,7 +195,7 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   if (s->two_level) {
     const TlasInfo ti = info[0];
     v2 = Trace2View{tlas.data(), std::min<int64_t>(ti.n, (int64_t)nb + 2), nodes.data(), s->n4, tris.data(), s->nt,
-                    roots.data(), xf.data(), s->nbody, ti.span, cap, &err};
+                    roots.data(), reinterpret_cast<const float*>(xf.data()), s->nbody, ti.span, cap, &err};
   } else {
     v1 = TraceCtx{nodes.data(), s->n4, scene_span<HostCheckedLoads>(nodes.data(), s->nt), tris.data(), s->nt, cap,
                   &err};

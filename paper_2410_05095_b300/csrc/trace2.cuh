@@ -31,7 +31,7 @@ struct Trace2View {
   const float4* tris;     // rest-pose triangle records
   int64_t nt;
   const int32_t* blas_root;  // [nbody]
-  const float* xf;        // [nbody*12] the frame's body matrices
+  const float* xf;        // [nbody*12] the frame's body matrices (16-B aligned)
   int nbody;
   float span;             // box-test slack scale (TlasInfo::span)
   int64_t cap;            // node-visit cap per ray
@@ -52,12 +52,12 @@ __host__ __device__ __forceinline__ void object_ray(const float m[12], float3 o,
 template <class M, bool ANY>
 __host__ __device__ __forceinline__ bool leaf_test2(const Trace2View& c, int code, float3 o, float3 d, float tmax,
                                                     int skip, int& prim, int& pos, float& tb) {
-  const int64_t p = ~(int64_t)code;
-  if (p < 0 || p >= c.nt) {
+  const uint32_t p = ~(uint32_t)code;  // (a triangle link is negative: p < 2^31)
+  if ((int64_t)p >= c.nt) {
     M::fail(c.err, kErrCorrupt);
     return false;
   }
-  const float4* tr = c.tris + 3 * p;
+  const float4* tr = c.tris + 3 * (size_t)p;
   const float4 A = M::f4(tr), B = M::f4(tr + 1), C = M::f4(tr + 2);
   const int orig = float_as_bits(A.w);
   float t;
@@ -94,7 +94,7 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
   stack[0] = kDone;
   int sp = 1;
   int cur = 0;  // top-level root
-  int64_t budget = c.cap;
+  int budget = (int)(c.cap < (int64_t)0x7fffffff ? c.cap : (int64_t)0x7fffffff);
   while (cur != kDone) {
     if (--budget < 0) {
       M::fail(c.err, kErrTimeout);
@@ -128,9 +128,10 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
         cur = stack[--sp];
         continue;
       }
-      float m[12];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) m[k] = M::f1(c.xf + 12 * (int64_t)b + k);
+      // the body's matrix: three 16-B rows (48 B per body from a 16-B aligned base)
+      const float4* mx = reinterpret_cast<const float4*>(c.xf) + 3 * (int64_t)b;
+      const float4 m0 = M::f4(mx), m1 = M::f4(mx + 1), m2 = M::f4(mx + 2);
+      const float m[12] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w};
       object_ray(m, o, d, ro, rd);
       r = ray_setup(ro, rd, c.span);
       stack[sp++] = kExitInstance;
@@ -139,8 +140,8 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
       continue;
     }
     const Node4* base = in_body ? c.blas : c.tlas;
-    const int64_t nn = in_body ? c.nblas : c.ntlas;
-    if (cur < 0 || cur >= nn) {
+    const uint32_t nn = (uint32_t)(in_body ? c.nblas : c.ntlas);  // (node counts < 2^31)
+    if ((uint32_t)cur >= nn) {
       M::fail(c.err, kErrCorrupt);
       return false;
     }
@@ -163,7 +164,7 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
       h2 = h2 && !(lm & 4u);
       h3 = h3 && !(lm & 8u);
       while (lm) {
-        const int slot = (lm & 1u) ? 0 : (lm & 2u) ? 1 : (lm & 4u) ? 2 : 3;
+        const int slot = lowest_slot(lm);
         lm &= lm - 1;
         const int code = slot == 0 ? v0 : slot == 1 ? v1 : slot == 2 ? v2 : v3;
         if (leaf_test2<M, ANY>(c, code, ro, rd, tmax, skip, prim, pos, tb)) return true;
