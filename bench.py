@@ -770,7 +770,12 @@ def main():
     primary_rays = cam.width * cam.height * cam.spp
     hits = int((gb[:, 0] >= 0).sum().item())
     # traversal work and warp demand of this frame (host run of the kernels' traversal code)
-    demand = traversal_demand(G, cam, gb.cpu().numpy()) if rank == 0 else None
+    demand = None
+    if rank == 0:
+        try:
+            demand = traversal_demand(G, cam, gb.cpu().numpy())
+        except Exception as e:  # a measurement aid: never costs the bench line
+            demand = {"error": f"{type(e).__name__}: {e}"}
     del gb
 
     avg = {k: stages[k][0] / K for k in ("refit", "primary", "queue", "shadow", "resolve")}  # one of each per frame
@@ -802,7 +807,9 @@ def main():
     # demand traffic of the traversal kernels: per warp, each distinct node and
     # triangle record fetched once (what the warp asks of L2 if L1 kept
     # nothing between warps), scaled to the frame's rays, over the live time
-    if demand is not None:
+    if demand is not None and "error" in demand:
+        roofline["demand"] = demand
+    elif demand is not None:
         probe_gbs = roofline.get("l2", {}).get("peak") or l2_read_probe(fb, torch)["gbs"]
         for name, rays in (("primary", primary_rays), ("shadow", shadow_rays)):
             dm = demand[name]
