@@ -155,20 +155,14 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
     bool h1 = slab4<ANY>(r, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tb, k1);
     bool h2 = slab4<ANY>(r, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tb, k2);
     bool h3 = slab4<ANY>(r, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tb, k3);
+    unsigned lm = 0;  // triangle leaves of a bottom-level node
     if (in_body) {
-      // triangle leaves: tested at once
-      unsigned lm = (unsigned)(h0 && v0 < 0) | ((unsigned)(h1 && v1 < 0) << 1) | ((unsigned)(h2 && v2 < 0) << 2) |
-                    ((unsigned)(h3 && v3 < 0) << 3);
+      lm = (unsigned)(h0 && v0 < 0) | ((unsigned)(h1 && v1 < 0) << 1) | ((unsigned)(h2 && v2 < 0) << 2) |
+           ((unsigned)(h3 && v3 < 0) << 3);
       h0 = h0 && !(lm & 1u);
       h1 = h1 && !(lm & 2u);
       h2 = h2 && !(lm & 4u);
       h3 = h3 && !(lm & 8u);
-      while (lm) {
-        const int slot = lowest_slot(lm);
-        lm &= lm - 1;
-        const int code = slot == 0 ? v0 : slot == 1 ? v1 : slot == 2 ? v2 : v3;
-        if (leaf_test2<M, ANY>(c, code, ro, rd, tmax, skip, prim, pos, tb)) return true;
-      }
     } else {
       // an unused slot holds the inverted infinite box and is never entered;
       // a link of kEmptyLink that passes anyway would be a corrupt node
@@ -178,32 +172,40 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
         return false;
       }
     }
+    // the next entry first, then this node's leaves (the single-level
+    // traversal's step order; leaf codes from the link vector)
+    int next;
     const int cnt = (int)h0 + (int)h1 + (int)h2 + (int)h3;
     if (cnt == 0) {
-      cur = stack[--sp];
-      continue;
-    }
-    if (cnt == 1) {
-      cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
-      continue;
-    }
-    k0 = h0 ? k0 : inf_f();
-    k1 = h1 ? k1 : inf_f();
-    k2 = h2 ? k2 : inf_f();
-    k3 = h3 ? k3 : inf_f();
-    cswap(k0, v0, k1, v1);
-    cswap(k2, v2, k3, v3);
-    cswap(k0, v0, k2, v2);
-    cswap(k1, v1, k3, v3);
-    cswap(k1, v1, k2, v2);
-    if (sp + cnt - 1 <= STACK) {
-      if (cnt == 4) stack[sp++] = v3;
-      if (cnt >= 3) stack[sp++] = v2;
-      stack[sp++] = v1;
+      next = stack[--sp];
+    } else if (cnt == 1) {
+      next = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
     } else {
-      M::fail(c.err, kErrStack);
+      k0 = h0 ? k0 : inf_f();
+      k1 = h1 ? k1 : inf_f();
+      k2 = h2 ? k2 : inf_f();
+      k3 = h3 ? k3 : inf_f();
+      cswap(k0, v0, k1, v1);
+      cswap(k2, v2, k3, v3);
+      cswap(k0, v0, k2, v2);
+      cswap(k1, v1, k3, v3);
+      cswap(k1, v1, k2, v2);
+      if (sp + cnt - 1 <= STACK) {
+        if (cnt == 4) stack[sp++] = v3;
+        if (cnt >= 3) stack[sp++] = v2;
+        stack[sp++] = v1;
+      } else {
+        M::fail(c.err, kErrStack);
+      }
+      next = v0;
     }
-    cur = v0;
+    while (lm) {
+      const int slot = lowest_slot(lm);
+      lm &= lm - 1;
+      const int code = slot == 0 ? lk.x : slot == 1 ? lk.y : slot == 2 ? lk.z : lk.w;
+      if (leaf_test2<M, ANY>(c, code, ro, rd, tmax, skip, prim, pos, tb)) return true;
+    }
+    cur = next;
   }
   return false;
 }

@@ -309,44 +309,50 @@ __host__ __device__ __forceinline__ bool traverse(const TraceCtx& c, float3 o, f
     h1 = h1 && !(lm & 2u);
     h2 = h2 && !(lm & 4u);
     h3 = h3 && !(lm & 8u);
+    // the next node first (pop, the one entered child, or the first of the
+    // ordered children with the rest pushed), then this node's leaves: the
+    // lanes' different branches end before the leaf loop, and the leaf codes
+    // come from the link vector (the ordering permutes v0..v3).  The visiting
+    // order is the same either way; measured against leaves first: primary
+    // 0.995 -> 0.946 ms, shadow 0.96 -> 0.93 ms (7.3M-triangle frame).
+    int next;
+    const int cnt = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+    if (cnt == 0) {
+      next = stack[--sp];
+    } else if (cnt == 1) {
+      next = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
+    } else {
+      // ordered by slab4's key: on the 7.3M-triangle frame 57-61 % of the
+      // shadow rays are occluded, mostly by bodies between the surface and
+      // the light rather than by the surface's own neighbourhood, and an
+      // order toward the light reaches them sooner (farthest entry first
+      // measured 1.41 -> 1.37 ms against nearest entry first, which was 9 %
+      // faster than the unsorted order)
+      k0 = h0 ? k0 : inf_f();
+      k1 = h1 ? k1 : inf_f();
+      k2 = h2 ? k2 : inf_f();
+      k3 = h3 ? k3 : inf_f();
+      cswap(k0, v0, k1, v1);
+      cswap(k2, v2, k3, v3);
+      cswap(k0, v0, k2, v2);
+      cswap(k1, v1, k3, v3);
+      cswap(k1, v1, k2, v2);
+      if (sp + cnt - 1 <= STACK) {
+        if (cnt == 4) stack[sp++] = v3;
+        if (cnt >= 3) stack[sp++] = v2;
+        stack[sp++] = v1;
+      } else {
+        M::fail(c.err, kErrStack);
+      }
+      next = v0;
+    }
     while (lm) {
       const int slot = lowest_slot(lm);
       lm &= lm - 1;
-      const int code = slot == 0 ? v0 : slot == 1 ? v1 : slot == 2 ? v2 : v3;
+      const int code = slot == 0 ? lk.x : slot == 1 ? lk.y : slot == 2 ? lk.z : lk.w;
       if (leaf_test<M, ANY>(c, code, o, d, tmax, skip, prim, pos, tb)) return true;
     }
-    const int cnt = (int)h0 + (int)h1 + (int)h2 + (int)h3;
-    if (cnt == 0) {
-      cur = stack[--sp];
-      continue;
-    }
-    if (cnt == 1) {
-      cur = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
-      continue;
-    }
-    // ordered by slab4's key: on the 7.3M-triangle frame 57-61 % of the
-    // shadow rays are occluded, mostly by bodies between the surface and the
-    // light rather than by the surface's own neighbourhood, and an order
-    // toward the light reaches them sooner (farthest entry first measured
-    // 1.41 -> 1.37 ms against nearest entry first, which was 9 % faster
-    // than the unsorted order)
-    k0 = h0 ? k0 : inf_f();
-    k1 = h1 ? k1 : inf_f();
-    k2 = h2 ? k2 : inf_f();
-    k3 = h3 ? k3 : inf_f();
-    cswap(k0, v0, k1, v1);
-    cswap(k2, v2, k3, v3);
-    cswap(k0, v0, k2, v2);
-    cswap(k1, v1, k3, v3);
-    cswap(k1, v1, k2, v2);
-    if (sp + cnt - 1 <= STACK) {
-      if (cnt == 4) stack[sp++] = v3;
-      if (cnt >= 3) stack[sp++] = v2;
-      stack[sp++] = v1;
-    } else {
-      M::fail(c.err, kErrStack);
-    }
-    cur = v0;
+    cur = next;
   }
   return false;
 }
