@@ -76,25 +76,25 @@ __device__ __forceinline__ bool slab(float3 o, float3 inv, float lox, float loy,
 
 // ---------------------------------------------------------------------------
 // Ray/triangle test (Moller-Trumbore) in the fixed FP32 order:
-//   p = d x e2, det = e1.p (reject 0), inv = 1/det, s = o - v0, u = (s.p) inv,
-//   q = s x e1, v = (d.q) inv, t = (e2.q) inv; inside iff u >= 0, v >= 0,
-//   fl(u + v) <= 1.  (u > 1 is rejected early: with v >= 0 it implies
-//   fl(u + v) > 1, so the decision is the same.)
+//   p = d x e2, det = e1.p, inv = 1/det, s = o - v0, u = (s.p) inv,
+//   q = s x e1, v = (d.q) inv, t = (e2.q) inv; inside iff det != 0, u >= 0,
+//   u <= 1, v >= 0, fl(u + v) <= 1.  Every term is computed and the decision
+//   taken once at the end (a det of 0 gives an infinite inv and u, v that
+//   fail the tests): in the traversal's leaf loop, which runs with few lanes,
+//   early exits only split those lanes further (shadow pass 0.929 -> 0.920
+//   ms against returning at det == 0 and at u outside [0, 1]).
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ bool mt_t(float3 o, float3 d, float4 A, float4 B, float4 C, float& t) {
   float3 v0 = xyz(A), e1 = xyz(B), e2 = xyz(C);
   float3 p = cross3(d, e2);
   float det = dot3(e1, p);
-  if (det == 0.0f) return false;
   float inv = rcp_rn(det);
   float3 s = sub3(o, v0);
   float u = dot3(s, p) * inv;
-  if (!(u >= 0.0f && u <= 1.0f)) return false;
   float3 q = cross3(s, e1);
   float v = dot3(d, q) * inv;
-  if (!(v >= 0.0f && (u + v) <= 1.0f)) return false;
   t = dot3(e2, q) * inv;
-  return true;
+  return det != 0.0f && u >= 0.0f && u <= 1.0f && v >= 0.0f && (u + v) <= 1.0f;
 }
 
 // Memory policy of the traversal code, which is written once for the device
