@@ -4,7 +4,10 @@ roofline, and the committed ncu counters it reads."""
 import json
 import os
 
+import numpy as np
+
 import bench
+import scenegen as sg
 
 
 def _clocks_from(lines):
@@ -92,3 +95,21 @@ def test_host_threads_and_split_sample():
     seen.clear()
     bench.oracle_samples(FakeScene(), None, [], ids, 1)
     assert seen == [list(ids)]
+
+
+def test_demand_sample_rays_are_the_render_camera():
+    """The rays bench.py replays for the warp-demand count (its float32
+    pinhole camera with the 4-spp rotated grid) are the oracle's camera rays
+    to a few ulp, so the sampled warps trace the render's rays."""
+    import oracle
+    w = sg.workload_frame7m(nspheres=4, cells=8)
+    for spp in (1, 4):
+        cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 37, 23, spp)
+        rng = np.random.default_rng(spp)
+        x, y = rng.integers(0, cam.width, 200), rng.integers(0, cam.height, 200)
+        k = rng.integers(0, spp, 200)
+        o, d = bench.camera_rays(cam, x, y, k)
+        for i in range(len(x)):
+            ro, rd = oracle.camera_ray(cam, int(x[i]), int(y[i]), int(k[i]))
+            assert np.allclose(o[i], ro, rtol=0, atol=0)
+            assert np.allclose(d[i], rd, rtol=0, atol=4e-7)

@@ -158,3 +158,22 @@ def test_trace_stats_invariants_on_camera_rays(fb):
     assert ss["rays"] == len(q) and ss["err"] == 0 and ss["bad_loads"] == 0
     assert len(q) <= ss["node_steps"] and ss["group_nodes"] < ss["node_steps"]
     assert ss["group_tris"] <= ss["tri_tests"]
+
+
+def test_trace_stats_edges(fb):
+    """No rays: all counts zero; a group longer than the input: one group;
+    a group size below 1 is refused."""
+    tri = np.array([[[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]])
+    from test_oracle_lbvh import _scene_from_tris
+    sc = _scene_from_tris(tri)
+    G = fb.Scene.from_numpy(sc)
+    G.build(sc.identity_xforms())
+    e = np.zeros((0, 3), np.float32)
+    st = G.trace_stats(e, e, group=32)
+    assert all(v == 0 for v in st.values()), st
+    o = np.array([[0.25, 0.25, 1.0]] * 5, np.float32)
+    d = np.array([[0.0, 0.0, -1.0]] * 5, np.float32)
+    st = G.trace_stats(o, d, group=64)
+    assert st["groups"] == 1 and st["rays"] == 5 and st["tri_tests"] == 5 and st["group_tris"] == 1
+    with pytest.raises(fb.FireError):
+        G.trace_stats(o, d, group=0)
