@@ -229,7 +229,7 @@ def traversal_demand(G, cam, gb_host, nwarps=2048):
     keep = np.repeat(full, 32)
     o, d = camera_rays(cam, x[keep], y[keep], kk[keep])
     out = {}
-    prim = G.trace_stats(o, d, group=32)
+    prim = G.trace_stats(o, d, group=32, per_ray=True)
     q_rays = G.dump("shadow_rays")
     sid = q_rays[:, 7].view(np.int32) >> 3
     nq = len(q_rays) // 32
@@ -237,14 +237,19 @@ def traversal_demand(G, cam, gb_host, nwarps=2048):
     idx = (starts[:, None] + np.arange(32)[None, :]).ravel()
     idx = idx[idx < len(q_rays)]
     qs = q_rays[idx]
-    shad = G.trace_stats(qs[:, 0:3], qs[:, 4:7], tmax=qs[:, 3], skip=gb_host[sid[idx], 0], any_hit=True, group=32)
+    shad = G.trace_stats(qs[:, 0:3], qs[:, 4:7], tmax=qs[:, 3], skip=gb_host[sid[idx], 0], any_hit=True, group=32,
+                         per_ray=True)
     for name, st in (("primary", prim), ("shadow", shad)):
         n = max(st["rays"], 1)
+        # node steps a warp runs (its longest ray) against its lanes' steps
+        w = st["steps"][: len(st["steps"]) // 32 * 32].reshape(-1, 32)
+        busy = float(w.sum() / max(32 * w.max(1).sum(), 1))
         out[name] = {"rays_sampled": st["rays"], "warps_sampled": st["groups"],
                      "node_steps_per_ray": st["node_steps"] / n, "tri_tests_per_ray": st["tri_tests"] / n,
                      "warp_distinct_nodes_per_ray": st["group_nodes"] / n,
                      "warp_distinct_tris_per_ray": st["group_tris"] / n,
                      "demand_bytes_per_ray": (128 * st["group_nodes"] + 48 * st["group_tris"]) / n,
+                     "lanes_busy_by_length": busy,
                      "check": {"bad_loads": st["bad_loads"], "err": st["err"]}}
     return out
 

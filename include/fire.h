@@ -414,9 +414,10 @@ int fire_debug_trace_host(fire_scene s, const float* o3, const float* d3, const 
  * failed the check (0), [7] the traversal's error bits.  Demand bytes of a
  * group = distinct nodes x 128 + distinct records x 48: what its warp asks
  * of L2, once per node and record, when L1 keeps nothing between warps.
+ * steps (host int32[n], may be NULL): each ray's node steps.
  * group < 1 -> FIRE_ERR_INVALID_ARG. */
 int fire_debug_trace_stats(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip,
-                           int64_t n, int32_t any, int32_t group, int64_t* out8);
+                           int64_t n, int32_t any, int32_t group, int64_t* out8, int32_t* steps);
 
 /* Synchronise `stream`, then return and clear the scene's sticky device error
  * (FIRE_OK, FIRE_ERR_STACK_OVERFLOW or FIRE_ERR_TIMEOUT). */

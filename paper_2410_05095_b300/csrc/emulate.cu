@@ -133,14 +133,16 @@ bool trace_one(const Trace2View* v2, const TraceCtx* v1, float3 o, float3 d, boo
 template <int STACK>
 void run(const Trace2View* v2, const TraceCtx* v1, const float* o3, const float* d3, const float* tmax,
          const int32_t* skip, int64_t n, bool any, int32_t* prim, float* t, uint8_t* hit, int group,
-         GroupTotals* tot) {
+         GroupTotals* tot, int32_t* steps) {
   for (int64_t i = 0; i < n; ++i) {
     if (tot && i > 0 && i % group == 0) tot->close_group();
     const float3 o = f3(o3[3 * i], o3[3 * i + 1], o3[3 * i + 2]);
     const float3 d = f3(d3[3 * i], d3[3 * i + 1], d3[3 * i + 2]);
     int p = -1;
     float tb = 0.0f;
+    const int64_t s0 = g_visits.steps;
     const bool h = trace_one<STACK>(v2, v1, o, d, any, tmax ? tmax[i] : inf_f(), skip ? skip[i] : -1, p, tb);
+    if (steps) steps[i] = (int32_t)(g_visits.steps - s0);
     if (prim) prim[i] = any ? -1 : p;
     if (t) t[i] = any ? 0.0f : tb;
     if (hit) hit[i] = h ? 1 : 0;
@@ -159,7 +161,8 @@ int fetch(std::vector<T>& h, const void* dev, size_t count) {
 // Copies the scene's current structures and runs the rays (group > 0:
 // visit totals into tot).
 int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, const int32_t* skip, int64_t n,
-            bool any, int32_t* prim, float* t, uint8_t* hit, uint32_t* err_out, int group, GroupTotals* tot) {
+            bool any, int32_t* prim, float* t, uint8_t* hit, uint32_t* err_out, int group, GroupTotals* tot,
+            int32_t* steps) {
   if (!s->built) return set_error(FIRE_ERR_NOT_BUILT, "emulation before build");
   *err_out = 0;
   if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
@@ -204,9 +207,9 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   const Trace2View* p2 = s->two_level ? &v2 : nullptr;
   const TraceCtx* p1 = s->two_level ? nullptr : &v1;
   switch (stack_for_height(stack_need(s), 0)) {
-    case 32: run<32>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
-    case 64: run<64>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
-    default: run<128>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot); break;
+    case 32: run<32>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot, steps); break;
+    case 64: run<64>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot, steps); break;
+    default: run<128>(p2, p1, o3, d3, tmax, skip, n, any, prim, t, hit, group, tot, steps); break;
   }
   g_visits = Visits{};
   g_regions.clear();
@@ -226,17 +229,19 @@ extern "C" int fire_debug_trace_host(fire_scene s, const float* o3, const float*
   set_error(FIRE_OK, "");
   if (!s || !err_out || (n > 0 && (!o3 || !d3)) || n < 0)
     return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
-  return emulate(s, o3, d3, tmax, skip, n, any != 0, prim, t, hit, err_out, 0, nullptr);
+  return emulate(s, o3, d3, tmax, skip, n, any != 0, prim, t, hit, err_out, 0, nullptr, nullptr);
 }
 
 extern "C" int fire_debug_trace_stats(fire_scene s, const float* o3, const float* d3, const float* tmax,
-                                      const int32_t* skip, int64_t n, int32_t any, int32_t group, int64_t* out8) {
+                                      const int32_t* skip, int64_t n, int32_t any, int32_t group, int64_t* out8,
+                                      int32_t* steps) {
   set_error(FIRE_OK, "");
   if (!s || !out8 || (n > 0 && (!o3 || !d3)) || n < 0) return set_error(FIRE_ERR_INVALID_ARG, "NULL argument");
   if (group < 1) return set_error(FIRE_ERR_INVALID_ARG, "group must be >= 1");
   GroupTotals tot;
   uint32_t err = 0;
-  if (int e = emulate(s, o3, d3, tmax, skip, n, any != 0, nullptr, nullptr, nullptr, &err, group, &tot)) return e;
+  if (int e = emulate(s, o3, d3, tmax, skip, n, any != 0, nullptr, nullptr, nullptr, &err, group, &tot, steps))
+    return e;
   for (int k = 0; k < 6; ++k) out8[k] = tot.v[k];
   out8[6] = g_bad_loads;
   out8[7] = err;

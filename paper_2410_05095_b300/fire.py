@@ -98,7 +98,7 @@ def lib():
             "fire_probe_read": [P, i64, i32, P, i32, P],
             "fire_scene_set_two_level": [P, i32],
             "fire_debug_trace_host": [P, P, P, P, P, i64, i32, P, P, P, P],
-            "fire_debug_trace_stats": [P, P, P, P, P, i64, i32, i32, P],
+            "fire_debug_trace_stats": [P, P, P, P, P, i64, i32, i32, P, P],
             "fire_batch_last_tuning": [P, P],
         }
         for name, args in sig.items():
@@ -301,18 +301,22 @@ class Scene:
                                            _ptr(prim), _ptr(t), _ptr(hit), C.byref(err)))
         return prim, t, hit.astype(bool), int(err.value)
 
-    def trace_stats(self, o, d, tmax=None, skip=None, any_hit=False, group=32) -> dict:
+    def trace_stats(self, o, d, tmax=None, skip=None, any_hit=False, group=32, per_ray=False) -> dict:
         """Traversal work and demand of rays o, d [n, 3] in groups of `group`
-        (fire_debug_trace_stats)."""
+        (fire_debug_trace_stats); per_ray: also each ray's node steps."""
         o = np.ascontiguousarray(o, np.float32)
         d = np.ascontiguousarray(d, np.float32)
         tm = None if tmax is None else np.ascontiguousarray(tmax, np.float32)
         sk = None if skip is None else np.ascontiguousarray(skip, np.int32)
         out = np.zeros(8, np.int64)
+        steps = np.zeros(len(o), np.int32) if per_ray else None
         _check(lib().fire_debug_trace_stats(self.h, _ptr(o), _ptr(d), _ptr(tm), _ptr(sk), len(o),
-                                            int(bool(any_hit)), int(group), _ptr(out)))
+                                            int(bool(any_hit)), int(group), _ptr(out), _ptr(steps)))
         keys = ("rays", "node_steps", "tri_tests", "group_nodes", "group_tris", "groups", "bad_loads", "err")
-        return dict(zip(keys, (int(x) for x in out)))
+        res = dict(zip(keys, (int(x) for x in out)))
+        if per_ray:
+            res["steps"] = steps
+        return res
 
     def dump(self, what: str) -> np.ndarray:
         T = self.nt

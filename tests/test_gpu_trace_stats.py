@@ -126,8 +126,9 @@ def test_trace_stats_on_separated_boxes(fb):
     assert st["tri_tests"] == 12
     assert st["group_nodes"] == 4
     assert st["group_tris"] == 3
-    st1 = G.trace_stats(o, d, group=1)
+    st1 = G.trace_stats(o, d, group=1, per_ray=True)
     assert st1["groups"] == 16 and st1["group_nodes"] == 16 and st1["group_tris"] == 12
+    assert (st1["steps"] == 1).all()
     prim, _, _, _ = G.trace_host(o, d)
     assert (prim[:12] >= 0).all() and (prim[12:] == -1).all()
 
@@ -146,8 +147,9 @@ def test_trace_stats_invariants_on_camera_rays(fb):
     assert st["rays"] == n and st["groups"] == -(-n // 32) and st["bad_loads"] == 0 and st["err"] == 0
     assert n <= st["node_steps"] and st["group_nodes"] < st["node_steps"]
     assert st["group_tris"] <= st["tri_tests"]
-    one = G.trace_stats(o, d, group=1)
+    one = G.trace_stats(o, d, group=1, per_ray=True)
     assert one["node_steps"] == st["node_steps"] and one["tri_tests"] == st["tri_tests"]
+    assert int(one["steps"].sum()) == one["node_steps"] and (one["steps"] >= 1).all()
     # a ray fetches a node and tests a triangle at most once (a tree)
     assert st["group_nodes"] < one["group_nodes"] == one["node_steps"]
     assert one["group_tris"] == one["tri_tests"]
@@ -163,8 +165,10 @@ def test_trace_stats_invariants_on_camera_rays(fb):
 
 
 def test_trace_stats_edges(fb):
-    """No rays: all counts zero; a group longer than the input: one group;
-    a group size below 1 is refused."""
+    """No rays: all counts zero; a group longer than the input: one group
+    (a one-triangle tree holds its triangle on both sides of its only node:
+    two tests per ray, one distinct record); a group size below 1 is
+    refused."""
     tri = np.array([[[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]])
     from test_oracle_lbvh import _scene_from_tris
     sc = _scene_from_tris(tri)
@@ -176,6 +180,6 @@ def test_trace_stats_edges(fb):
     o = np.array([[0.25, 0.25, 1.0]] * 5, np.float32)
     d = np.array([[0.0, 0.0, -1.0]] * 5, np.float32)
     st = G.trace_stats(o, d, group=64)
-    assert st["groups"] == 1 and st["rays"] == 5 and st["tri_tests"] == 5 and st["group_tris"] == 1
+    assert st["groups"] == 1 and st["rays"] == 5 and st["tri_tests"] == 10 and st["group_tris"] == 1
     with pytest.raises(fb.FireError):
         G.trace_stats(o, d, group=0)
