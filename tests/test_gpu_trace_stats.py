@@ -183,3 +183,34 @@ def test_trace_stats_edges(fb):
     assert st["groups"] == 1 and st["rays"] == 5 and st["tri_tests"] == 10 and st["group_tris"] == 1
     with pytest.raises(fb.FireError):
         G.trace_stats(o, d, group=0)
+
+
+def test_two_level_dump_and_stats(fb):
+    """Two-level scene: the dumped shadow rays, walked on the host with the
+    sample's triangle skipped, give the device's visibility bits; the
+    statistics count top-level and bottom-level node fetches alike (at
+    least one per ray: the top root) and keep their invariants."""
+    import torch
+    w = sg.workload_frame7m(nspheres=120, cells=64)
+    G = fb.Scene.from_numpy(w.scene)
+    G.set_two_level(True)
+    G.build(w.motion.xforms())
+    for _ in range(2):
+        G.refit(w.motion.step())
+    cam = sg.Camera(w.camera.pos, w.camera.target, w.camera.up, 60.0, 64, 36, 4)
+    n = cam.width * cam.height * cam.spp
+    gb = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, w.lights, out=torch.zeros((cam.height, cam.width, 4), device="cuda"), gbuf=gb)
+    g = gbuf_of(gb)
+    q = G.dump("shadow_rays")
+    tag = q[:, 7].view(np.int32)
+    sid, light = tag >> 3, tag & 7
+    assert len(q) == G.render_info()["shadow_rays"] > 50
+    _, _, occ, err = G.trace_host(q[:, 0:3], q[:, 4:7], tmax=q[:, 3], skip=g["prim"][sid], any_hit=True)
+    assert err == 0, hex(err)
+    assert np.array_equal(~occ, ((g["vis"][sid] >> light) & 1).astype(bool))
+    o, d = _camera_rays(cam)
+    st = G.trace_stats(o, d, group=32, per_ray=True)
+    assert st["rays"] == n and st["err"] == 0 and st["bad_loads"] == 0
+    assert (st["steps"] >= 1).all() and int(st["steps"].sum()) == st["node_steps"]
+    assert st["group_nodes"] < st["node_steps"] and st["group_tris"] <= st["tri_tests"]
