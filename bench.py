@@ -848,6 +848,7 @@ def main():
             "dtype": "f32", "data": "synthetic (seeded icospheres + value-noise terrain, random rigid motion)",
             "config": workload_config(w, K), "gpu_launches": int(launches),
             "grays_per_s": grays, "grays_per_s_frame": grays_frame,
+            "samples_per_s": primary_rays / (ms_frame_rank * 1e-3),
             "rays_per_frame": {"primary": primary_rays, "shadow": shadow_rays, "hit_samples": hits},
             "stages_ms": {**avg, "build_once": build_ms},
             "serial_ms_per_frame": t_serial / K,
