@@ -257,13 +257,15 @@ __host__ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, in
 }
 
 // Stack traversal of the 4-wide tree (collapsed from the Karras binary
-// tree), children in slab4's order.  One node fetch (7 x 16 B) tests all four child
-// boxes; leaf children (one triangle each) are tested at once, so the
-// nearest-hit bound tightens early; hit internal children are ordered by
-// their keys with a 5-comparator network and all but the first pushed,
-// last first.  (Postponing leaves until the whole warp holds one -- the
-// while-while form of Aila and Laine -- measured 2x slower with one triangle
-// per leaf: the delayed bound lets rays wander into far subtrees.)
+// tree), children in slab4's order.  One node fetch (7 x 16 B) tests all
+// four child boxes; hit internal children are ordered by their keys with a
+// 5-comparator network, the first becomes the next node and the rest are
+// pushed, last first; then the node's leaf children (one triangle each) are
+// tested in the same step, so the nearest-hit bound tightens before the next
+// node's boxes are tested.  (Postponing leaves until the whole warp holds
+// one -- the while-while form of Aila and Laine -- measured 2x slower with
+// one triangle per leaf: the delayed bound lets rays wander into far
+// subtrees.)
 //   ANY:  any hit in (0, tmax) other than `skip`; returns true on a hit.
 //   else: nearest hit in (0, inf) by (t, original index) -- independent of
 //         the visiting order; prim = original index (-1 = miss), pos = sorted
