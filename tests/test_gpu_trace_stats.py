@@ -214,3 +214,31 @@ def test_two_level_dump_and_stats(fb):
     assert st["rays"] == n and st["err"] == 0 and st["bad_loads"] == 0
     assert (st["steps"] >= 1).all() and int(st["steps"].sum()) == st["node_steps"]
     assert st["group_nodes"] < st["node_steps"] and st["group_tris"] <= st["tri_tests"]
+
+
+def test_axis_aligned_rays_match_oracle(fb):
+    """Rays along the coordinate axes (two direction components exactly 0,
+    their reciprocals clamped to +-1e30, so the children's order keys are
+    huge): nearest hits and any-hit answers of the kernels' traversal code
+    equal the oracle's, and no error bit is set."""
+    w, G = _moving_scene(fb, frames=1)
+    S = oracle.OracleScene(w.scene)
+    S.update(w.motion.xforms(), rebuild=True)
+    rng = np.random.default_rng(11)
+    n = 3000
+    o = rng.uniform([-12, -3, -12], [12, 5, 12], (n, 3)).astype(np.float32)
+    d = np.zeros((n, 3), np.float32)
+    axis = rng.integers(0, 3, n)
+    d[np.arange(n), axis] = np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    prim, t, _, err = G.trace_host(o, d)
+    assert err == 0, hex(err)
+    rp, rt, _, _, rt2 = S.trace(o, d, want_t2=True)
+    bad = (prim != rp) | ((prim >= 0) & (t != rt))
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(rt2) & (np.abs(rt2 - rt) <= TIE_REL * np.abs(rt))
+    assert not (bad & ~tie).any(), int(bad.sum())
+    assert 0.05 < (rp >= 0).mean() < 0.95
+    L = rng.uniform(0.5, 20.0, n).astype(np.float32)
+    _, _, hit, err = G.trace_host(o, d, tmax=L, any_hit=True)
+    assert err == 0, hex(err)
+    assert np.array_equal(hit, S.occluded(o, d, L, np.full(n, -1, np.int32)))
