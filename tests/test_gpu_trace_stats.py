@@ -242,3 +242,20 @@ def test_axis_aligned_rays_match_oracle(fb):
     _, _, hit, err = G.trace_host(o, d, tmax=L, any_hit=True)
     assert err == 0, hex(err)
     assert np.array_equal(hit, S.occluded(o, d, L, np.full(n, -1, np.int32)))
+
+
+def test_shadow_dump_edges(fb):
+    """Before any render the shadow-ray dump is empty; a byte count that is
+    not the exact size is refused."""
+    import ctypes as C
+
+    from paper_2410_05095_b300 import fire
+    tri = np.array([[[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]])
+    from test_oracle_lbvh import _scene_from_tris
+    sc = _scene_from_tris(tri)
+    G = fb.Scene.from_numpy(sc)
+    G.build(sc.identity_xforms())
+    assert G.dump("shadow_rays").shape == (0, 8)
+    buf = np.zeros(8, np.float32)
+    rc = fire.lib().fire_debug_dump(G.h, 12, buf.ctypes.data_as(C.c_void_p), 32)
+    assert fire.ERRORS.get(rc) == "FIRE_ERR_INVALID_ARG"
