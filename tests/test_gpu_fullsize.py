@@ -63,6 +63,31 @@ def test_fullsize_refit_and_sampled_render(frame7m):
     assert (g["prim"] >= 0).mean() > 0.3
 
 
+def test_fullsize_frame99_sampled_render(frame7m):
+    """Frame 99 of the sequence: the topology of frame 0's build with the
+    boxes of frame 99's poses (a refit recomputes every box from the poses,
+    so one refit gives the boxes of 99), where the tree is loosest.  Boxes
+    and triangle records bit for bit; 20,000 sampled samples by the
+    agreement rule."""
+    torch = torch_cuda()
+    w, G, S = frame7m
+    w99 = sg.workload_frame7m()
+    for _ in range(99):
+        xf = w99.motion.step()
+    G.refit(xf)
+    S.update(xf, rebuild=False)
+    assert np.array_equal(G.dump("boxes"), S.get("boxes"))
+    assert_tris_equal(G, S, w.scene)
+    cam = w.camera
+    gb = torch.zeros((cam.width * cam.height * cam.spp, 4), dtype=torch.int32, device="cuda")
+    G.render(cam, w.lights, gbuf=gb)
+    assert G.sync_status() == 0
+    g = gbuf_of(gb)
+    ids = np.random.default_rng(99).choice(cam.width * cam.height * cam.spp, 20000, replace=False)
+    compare_samples(g, _oracle_samples(S, cam, w.lights, ids), ids)
+    assert (g["prim"] >= 0).mean() > 0.3
+
+
 def test_fullsize_pipelined_bench_configuration():
     torch = torch_cuda()
     import paper_2410_05095_b300 as fb
