@@ -63,17 +63,19 @@ def test_fullsize_refit_and_sampled_render(frame7m):
     assert (g["prim"] >= 0).mean() > 0.3
 
 
-def test_fullsize_frame99_sampled_render(frame7m):
-    """Frame 99 of the sequence: the topology of frame 0's build with the
-    boxes of frame 99's poses (a refit recomputes every box from the poses,
-    so one refit gives the boxes of 99), where the tree is loosest.  Boxes
-    and triangle records bit for bit; 20,000 sampled samples by the
-    agreement rule."""
+@pytest.mark.parametrize("frame", [0, 1, 50, 99])
+def test_fullsize_sequence_frames_sampled_render(frame7m, frame):
+    """Frames 0, 1, 50 and 99 of the sequence: the topology of frame 0's
+    build with the boxes of that frame's poses (a refit recomputes every box
+    from the poses, so one refit gives the boxes of frame k); frame 99 is
+    where the tree is loosest.  Boxes and triangle records bit for bit;
+    20,000 sampled samples by the agreement rule."""
     torch = torch_cuda()
     w, G, S = frame7m
-    w99 = sg.workload_frame7m()
-    for _ in range(99):
-        xf = w99.motion.step()
+    wk = sg.workload_frame7m()
+    xf = wk.motion.xforms()
+    for _ in range(frame):
+        xf = wk.motion.step()
     G.refit(xf)
     S.update(xf, rebuild=False)
     assert np.array_equal(G.dump("boxes"), S.get("boxes"))
@@ -83,7 +85,7 @@ def test_fullsize_frame99_sampled_render(frame7m):
     G.render(cam, w.lights, gbuf=gb)
     assert G.sync_status() == 0
     g = gbuf_of(gb)
-    ids = np.random.default_rng(99).choice(cam.width * cam.height * cam.spp, 20000, replace=False)
+    ids = np.random.default_rng(frame).choice(cam.width * cam.height * cam.spp, 20000, replace=False)
     compare_samples(g, _oracle_samples(S, cam, w.lights, ids), ids)
     assert (g["prim"] >= 0).mean() > 0.3
 
