@@ -180,6 +180,18 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
       next = stack[--sp];
     } else if (cnt == 1) {
       next = h0 ? v0 : h1 ? v1 : h2 ? v2 : v3;
+#ifdef __CUDA_ARCH__
+    } else if (!__any_sync(__activemask(), cnt > 2)) {  // two children: one compare-exchange
+      const bool a01 = h0 && h1, a02 = h0 && h2, a12 = h1 && h2;
+      int va = h0 ? v0 : h1 ? v1 : v2;
+      float ka = h0 ? k0 : h1 ? k1 : k2;
+      int vb = h3 ? v3 : (a01 ? v1 : (a02 || a12) ? v2 : v3);
+      float kb = h3 ? k3 : (a01 ? k1 : (a02 || a12) ? k2 : k3);
+      cswap(ka, va, kb, vb);
+      if (sp + 1 <= STACK) stack[sp++] = vb;
+      else M::fail(c.err, kErrStack);
+      next = va;
+#endif
     } else {
       k0 = h0 ? k0 : inf_f();
       k1 = h1 ? k1 : inf_f();
