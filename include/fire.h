@@ -356,11 +356,14 @@ int fire_shade_backward_noalloc(fire_scene s, const fire_gbuffer_rec* gbuf, cons
  *                                       out[6]); two-level: the bottom levels
  * two-level scenes only (else FIRE_ERR_INVALID_ARG):
  *  8 bottom-level root of each body      int32[nbody] (-1: no triangles)
- *  9 top level of the current buffer    128 B x (nbody + 2) (4-wide nodes; leaf
- *                                       link ~body; unused nodes undefined)
+ *  9 top level of the current buffer    128 B x 1026 (4-wide nodes; leaf link
+ *                                       ~entry; unused nodes undefined)
  * 10 its record                         16 B: float eps, float span, int32 nodes
  *                                       in use, int32 error (nonzero: not built)
  * 11 body matrices of the current buffer float[nbody*12]
+ * 13 the top level's entries            int32[1024*2]: (bottom-level 4-wide
+ *                                       node, body) in body order; (-1, -1)
+ *                                       past the last
  * any scene:
  * 12 the last fire_render's shadow rays in the order its shadow pass takes
  *    them (light by light, each light's rays in task order)  float[n*8]:
@@ -373,8 +376,13 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes);
  * once, a top level over the instances rebuilt every frame).  enable = 1:
  * the next fire_bvh_build builds one bottom level per body over the REST
  * pose (an LBVH with body-prefixed keys: each body's subtree, collapsed into
- * its own 4-wide tree, never refit) and a top level over the bodies' world
- * boxes (the 8 corners of the rest box through the body's matrix, widened by
+ * its own 4-wide tree, never refit), cuts each body's bottom level into
+ * subtrees -- the top level's entries, so that a body whose parts lie far
+ * apart gets tight boxes: breadth first from the body's root, a node whose
+ * members are all inner nodes is replaced by them while the body's entries
+ * stay within its share (1024 / bodies with triangles, at most 64) -- and
+ * builds a top level over the entries' world boxes (the 8 corners of the
+ * entry's rest box through its body's matrix, widened by
  * 2^-10 (1 + largest |coordinate|)); each fire_bvh_refit then only rebuilds
  * the top level (one block) into the other frame buffer.  Rays meet a body's
  * triangles in the body's frame, o' = R^T (o - t), d' = R^T d (R, t: the

@@ -168,7 +168,7 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   if (int e = cuda_check(cudaDeviceSynchronize(), "sync")) return e;
   std::vector<Node4> tlas, nodes;
   std::vector<float4> tris;
-  std::vector<int32_t> roots;
+  std::vector<int32_t> inst;  // top-level entries (bottom-level node, body)
   std::vector<float4> xf;  // 3 rows per body (16-B aligned, as the device buffer)
   std::vector<TlasInfo> info;
   const size_t nb = (size_t)s->nbody;
@@ -178,16 +178,17 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   g_regions.clear();
   if (s->two_level) {
     if (int e = fetch(info, s->tinfo, 1)) return e;
-    if (int e = fetch(tlas, s->tlas, nb + 2)) return e;
-    if (int e = fetch(roots, s->blas_root, nb)) return e;
+    if (int e = fetch(tlas, s->tlas, (size_t)kMaxTlasBodies + 2)) return e;
+    if (int e = fetch(inst, s->inst, 2 * (size_t)kMaxTlasBodies)) return e;
     if (int e = fetch(xf, s->xf_buf[s->cur], 3 * nb)) return e;
     if (info[0].err) *err_out |= kErrStack;
-    g_regions.push_back({reinterpret_cast<const char*>(tlas.data()), sizeof(Node4) * (nb + 2), kNodes});
+    g_regions.push_back({reinterpret_cast<const char*>(tlas.data()), sizeof(Node4) * ((size_t)kMaxTlasBodies + 2),
+                         kNodes});
   }
   g_regions.push_back({reinterpret_cast<const char*>(nodes.data()), sizeof(Node4) * (size_t)s->n4, kNodes});
   g_regions.push_back({reinterpret_cast<const char*>(tris.data()), sizeof(float4) * 3 * (size_t)s->nt, kTris});
   if (s->two_level) {
-    g_regions.push_back({reinterpret_cast<const char*>(roots.data()), 4 * nb, kOther});
+    g_regions.push_back({reinterpret_cast<const char*>(inst.data()), 8 * (size_t)kMaxTlasBodies, kOther});
     g_regions.push_back({reinterpret_cast<const char*>(xf.data()), 48 * nb, kOther});
   }
   g_bad_loads = 0;
@@ -197,8 +198,9 @@ int emulate(fire_scene s, const float* o3, const float* d3, const float* tmax, c
   TraceCtx v1{};
   if (s->two_level) {
     const TlasInfo ti = info[0];
-    v2 = Trace2View{tlas.data(), std::min<int64_t>(ti.n, (int64_t)nb + 2), nodes.data(), s->n4, tris.data(), s->nt,
-                    roots.data(), reinterpret_cast<const float*>(xf.data()), s->nbody, ti.span, cap, &err};
+    v2 = Trace2View{tlas.data(), std::min<int64_t>(ti.n, (int64_t)kMaxTlasBodies + 2), nodes.data(), s->n4,
+                    tris.data(), s->nt, inst.data(), kMaxTlasBodies, reinterpret_cast<const float*>(xf.data()),
+                    s->nbody, ti.span, cap, &err};
   } else {
     v1 = TraceCtx{nodes.data(), s->n4, scene_span<HostCheckedLoads>(nodes.data(), s->nt), tris.data(), s->nt, cap,
                   &err};

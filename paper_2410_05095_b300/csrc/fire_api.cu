@@ -212,7 +212,8 @@ void free_scene(fire_scene_s* s) {
                   s->tris_buf[1], s->nodes4_buf[0], s->nodes4_buf[1], s->cen,
                   s->keys_alt, s->vals_alt, s->hist, s->ctrl, s->gscratch, s->bwd_partials, s->jobs,
                   s->lvl_aux, s->q4, s->rank, s->rkeys, s->rdirs, s->pieces, s->graze,
-                  s->blas_root, s->body_box, s->body_range, s->xf_ident, s->tlas_buf[0], s->tlas_buf[1],
+                  s->blas_root, s->body_box, s->body_range, s->xf_ident, s->inst, s->inst_box, s->tlas_buf[0],
+                  s->tlas_buf[1],
                   s->tinfo_buf[0], s->tinfo_buf[1], s->stage, s->qperm, s->qaux, s->tl_node, s->tl_refs,
                   s->tl_info, s->tl_top, s->tl_grp, s->nunion, s->tl_scratch};
   for (void* p : ptrs)
@@ -287,22 +288,24 @@ int alloc_lbvh(fire_scene_s* s) {
 }
 
 // Two-level buffers (first two-level build): bottom-level roots, rest boxes,
-// body ranges, identity matrices, and per frame buffer the top level and its
-// record.
+// body ranges, identity matrices, the top level's entries and their rest
+// boxes, and per frame buffer the top level and its record.
 int alloc_two_level(fire_scene_s* s, cudaStream_t st) {
   if (s->blas_root) return FIRE_OK;
   const size_t nb = (size_t)s->nbody;
   struct A { void** p; size_t b; } list[] = {
       {(void**)&s->blas_root, 4 * nb},     {(void**)&s->body_box, 32 * nb},
       {(void**)&s->body_range, 8 * nb},    {(void**)&s->xf_ident, 48 * nb},
-      {(void**)&s->tlas_buf[0], 128 * (nb + 2)}, {(void**)&s->tlas_buf[1], 128 * (nb + 2)},
+      {(void**)&s->inst, 8 * (size_t)kMaxTlasBodies}, {(void**)&s->inst_box, 32 * (size_t)kMaxTlasBodies},
+      {(void**)&s->tlas_buf[0], 128 * ((size_t)kMaxTlasBodies + 2)},
+      {(void**)&s->tlas_buf[1], 128 * ((size_t)kMaxTlasBodies + 2)},
       {(void**)&s->tinfo_buf[0], sizeof(TlasInfo)}, {(void**)&s->tinfo_buf[1], sizeof(TlasInfo)},
   };
   for (auto& a : list)
     if (cudaError_t e = dev_alloc(a.p, a.b, &s->bytes)) return cuda_check(e, "two-level buffers");
   // every pointer the traversal reads with 16-B loads is 16-B aligned (cudaMalloc gives 256)
   for (const void* p : {(const void*)s->tlas_buf[0], (const void*)s->tlas_buf[1], (const void*)s->tinfo_buf[0],
-                        (const void*)s->tinfo_buf[1], (const void*)s->body_box})
+                        (const void*)s->tinfo_buf[1], (const void*)s->body_box, (const void*)s->inst_box})
     if (reinterpret_cast<uintptr_t>(p) & 15u) return set_error(FIRE_ERR_CUDA, "misaligned two-level buffer");
   std::vector<float> id(12 * nb, 0.0f);
   for (size_t b = 0; b < nb; ++b) id[12 * b] = id[12 * b + 5] = id[12 * b + 10] = 1.0f;
@@ -879,7 +882,8 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
       if (!s->two_level) return set_error(FIRE_ERR_INVALID_ARG, "two-level dump of a single-level scene");
       const size_t nb = (size_t)s->nbody;
       if (what == 8) return need(4 * nb) ? get(host_dst, s->blas_root, 4 * nb) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
-      if (what == 9) return need(128 * (nb + 2)) ? get(host_dst, s->tlas, 128 * (nb + 2)) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
+      const size_t ntl = (size_t)kMaxTlasBodies + 2;
+      if (what == 9) return need(128 * ntl) ? get(host_dst, s->tlas, 128 * ntl) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
       if (what == 10) return need(sizeof(TlasInfo)) ? get(host_dst, s->tinfo, sizeof(TlasInfo)) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
       return need(48 * nb) ? get(host_dst, s->xf_buf[s->cur], 48 * nb) : set_error(FIRE_ERR_INVALID_ARG, "dump size mismatch");
     }
@@ -910,6 +914,10 @@ int fire_debug_dump(fire_scene s, int32_t what, void* host_dst, size_t bytes) {
       }
       return FIRE_OK;
     }
+    case 13:  // the top level's entries
+      if (!s->two_level) return set_error(FIRE_ERR_INVALID_ARG, "two-level dump of a single-level scene");
+      if (!need(8 * (size_t)kMaxTlasBodies)) break;
+      return get(host_dst, s->inst, 8 * (size_t)kMaxTlasBodies);
     default:
       return set_error(FIRE_ERR_INVALID_ARG, "unknown dump selector");
   }

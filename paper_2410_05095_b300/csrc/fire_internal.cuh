@@ -60,9 +60,10 @@ constexpr int kEmptyLink = (int)0x80000000;
 // Two-level acceleration structure (§IV-B-3: one bottom level per mesh,
 // built once; a top level over the instances, rebuilt every frame).  The
 // bottom levels are the bodies' 4-wide subtrees of an LBVH built over the
-// rest pose with body-prefixed keys; the top level is a 4-wide tree over the
-// bodies' world boxes (the 8 transformed corners of the rest box), whose
-// leaf links are ~body.  Per frame buffer: the top-level nodes and this
+// rest pose with body-prefixed keys; the top level is a 4-wide tree over
+// entries that cut the bodies' bottom levels into subtrees (the world box of
+// an entry: the 8 corners of its rest box through its body's matrix), whose
+// leaf links are ~entry.  Per frame buffer: the top-level nodes and this
 // record.
 struct __align__(16) TlasInfo {
   float eps;    // shadow-ray lift: 1e-4 x diagonal of the union of the instances' world boxes
@@ -214,7 +215,9 @@ struct fire_scene_s {
   float4* body_box = nullptr;     // [2*nbody] rest box of each body (lo, hi; xyz)
   int32_t* body_range = nullptr;  // [2*nbody] first and last sorted position of each body (build)
   float* xf_ident = nullptr;      // [nbody*12] identity matrices (the bottom levels are built at rest)
-  fire::Node4* tlas_buf[2] = {nullptr, nullptr};       // [nbody + 2] each
+  int32_t* inst = nullptr;        // [2*kMaxTlasBodies] top-level entries: (bottom-level node, body); -1: unused
+  float4* inst_box = nullptr;     // [2*kMaxTlasBodies] rest box of each entry (lo, hi; xyz)
+  fire::Node4* tlas_buf[2] = {nullptr, nullptr};       // [kMaxTlasBodies + 2] each
   fire::TlasInfo* tinfo_buf[2] = {nullptr, nullptr};
   fire::Node4* tlas = nullptr;    // current frame buffer's top level
   fire::TlasInfo* tinfo = nullptr;
@@ -289,11 +292,12 @@ struct RenderArgs {
   // [j*qseg + 32t, +qcnt[j*ntasks + t]) of the primary pass's sparse queue
   int32_t* qcnt;
   int64_t qseg;                 // 32 x tasks of the full image
-  // two-level mode (tlas != nullptr): top level, its record, each body's
-  // bottom-level root; bxf holds the frame's body matrices
+  // two-level mode (tlas != nullptr): top level, its record, the top
+  // level's entries (bottom-level node, body); bxf holds the frame's body
+  // matrices
   const Node4* tlas;
   const TlasInfo* tinfo;
-  const int32_t* blas_root;
+  const int32_t* inst;
   int nbody;
 };
 // Raster primary pass (raster.cu).  Words of fire_scene_s::ctrl it uses:
@@ -338,7 +342,7 @@ inline void set_smooth_args(RenderArgs* a, const fire_scene_s* s) {
 inline void set_level_args(RenderArgs* a, const fire_scene_s* s) {
   a->tlas = s->two_level ? s->tlas : nullptr;
   a->tinfo = s->two_level ? s->tinfo : nullptr;
-  a->blas_root = s->blas_root;
+  a->inst = s->inst;
   a->nbody = s->nbody;
 }
 // lbvh.cu: number of triangles whose three vertices do not share one body

@@ -676,18 +676,135 @@ __global__ void k_body_boxes(const Node4* __restrict__ nodes4, int64_t n4, const
   body_box[2 * b + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
 }
 
+// Top-level entries (each two-level build): a body whose parts lie far
+// apart has a rest box that covers mostly empty space, so the top level is
+// built over subtrees of the bodies' bottom levels instead.  Thread b cuts
+// body b's bottom level breadth first from its root: on each level, in
+// order, a node whose members are all inner 4-wide nodes is replaced by its
+// members while the body's entries stay within its share (kMaxTlasBodies /
+// bodies with triangles, at most kEntriesPerBody); every triangle of the
+// body lies under exactly one entry.  Entries are written in body order (at
+// the scan of the counts) as (node, body) with their rest boxes (the node's
+// slot in its parent, or the body's rest box for a root); the slots past the
+// last hold (-1, -1).  One block of kMaxTlasBodies threads.
+// (shares capped at 2, 4, 8 entries per body measured slower on the
+// 7.3M-triangle scene, 65 bodies: the full share of 15 is used there)
+constexpr int kEntriesPerBody = 64;
+__global__ void __launch_bounds__(1024) k_top_entries(const Node4* __restrict__ nodes4, int64_t n4,
+                                                      const int32_t* __restrict__ blas_root,
+                                                      const float4* __restrict__ body_box, int nbody,
+                                                      int32_t* __restrict__ inst, float4* __restrict__ inst_box,
+                                                      uint32_t* err) {
+  __shared__ int32_t scan[kMaxTlasBodies];
+  const int b = threadIdx.x;
+  const int32_t root = b < nbody ? blas_root[b] : -1;
+  const bool has = root >= 0 && root < n4;
+  if (b < nbody && root >= n4) atomicOr(err, kErrCorrupt);
+  auto block_scan = [&](int32_t v) {  // inclusive, over the block
+    scan[b] = v;
+    __syncthreads();
+    for (int off = 1; off < kMaxTlasBodies; off <<= 1) {
+      const int32_t a = b >= off ? scan[b - off] : 0;
+      __syncthreads();
+      scan[b] += a;
+      __syncthreads();
+    }
+    const int32_t r = scan[b], total = scan[kMaxTlasBodies - 1];
+    __syncthreads();
+    return make_int2(r, total);
+  };
+  const int nbodies = block_scan(has ? 1 : 0).y;
+  const int share = nbodies > 0 ? max(1, min(kEntriesPerBody, kMaxTlasBodies / nbodies)) : 1;
+  // entries of the current level: node, and where its rest box is (parent
+  // node * 4 + slot; -1: the body's root)
+  int32_t ent[kEntriesPerBody], from[kEntriesPerBody], nxt[kEntriesPerBody], nfrom[kEntriesPerBody];
+  int n = 0;
+  if (has) {
+    ent[0] = root;
+    from[0] = -1;
+    n = 1;
+  }
+  for (int level = 0; level < 64 && n > 0; ++level) {
+    // invariant: m + (n - k) <= share before entry k, so m never passes share
+    int m = 0;
+    bool split = false;
+    for (int k = 0; k < n; ++k) {
+      const int32_t v = ent[k];
+      const int4 lk = nodes4[v].link;
+      const int l[4] = {lk.x, lk.y, lk.z, lk.w};
+      int kids = 0;
+      bool inner = true;
+      for (int c = 0; c < 4; ++c) {
+        if (l[c] == kEmptyLink) continue;
+        if (l[c] < 0 || l[c] >= n4) inner = false;  // a triangle (a link past the nodes: corrupt)
+        else ++kids;
+        if (l[c] >= n4) atomicOr(err, kErrCorrupt);
+      }
+      if (inner && kids > 0 && m + kids + (n - k - 1) <= share) {
+        for (int c = 0; c < 4; ++c) {
+          if (l[c] == kEmptyLink) continue;
+          nxt[m] = l[c];
+          nfrom[m] = 4 * v + c;
+          ++m;
+        }
+        split = true;
+      } else {
+        nxt[m] = v;
+        nfrom[m] = from[k];
+        ++m;
+      }
+    }
+    for (int k = 0; k < m; ++k) {
+      ent[k] = nxt[k];
+      from[k] = nfrom[k];
+    }
+    n = m;
+    if (!split) break;
+  }
+  const int2 sc = block_scan(n);
+  const int base = sc.x - n;
+  for (int k = 0; k < n; ++k) {
+    const int i = base + k;  // < kMaxTlasBodies: the shares add up to at most that
+    if (i >= kMaxTlasBodies) {
+      atomicOr(err, kErrCorrupt);
+      break;
+    }
+    float4 lo, hi;
+    if (from[k] < 0) {
+      lo = body_box[2 * b];
+      hi = body_box[2 * b + 1];
+    } else {
+      const float* f = &nodes4[from[k] >> 2].lox.x;  // lox loy loz hix hiy hiz, 4 slots each
+      const int c = from[k] & 3;
+      lo = make_float4(f[c], f[4 + c], f[8 + c], 0.0f);
+      hi = make_float4(f[12 + c], f[16 + c], f[20 + c], 0.0f);
+    }
+    inst[2 * i] = ent[k];
+    inst[2 * i + 1] = b;
+    inst_box[2 * i] = lo;
+    inst_box[2 * i + 1] = hi;
+  }
+  for (int i = sc.y + b; i < kMaxTlasBodies; i += blockDim.x) {
+    inst[2 * i] = -1;
+    inst[2 * i + 1] = -1;
+  }
+}
+
 // ----------------------------------------------------------------------------
-// Top level of one frame (one block of 1024 threads, nbody <= 1024).
-//   1. world box of every body with triangles: the 8 corners of its rest box
-//      through its matrix, x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row;
-//      their union gives the frame's shadow-ray lift eps = 1e-4 |hi - lo|;
-//      span = largest |coordinate| of the union and of the rest boxes
-//   2. the boxes widened by 2^-10 (1 + span) on every side (the body-frame
-//      ray's rounding against the world box test), keyed by the 30-bit Morton
-//      code of their centres (10 bits per axis) above the instance index,
+// Top level of one frame (one block of 1024 threads, one per top-level
+// entry).
+//   1. world box of every body with triangles and of every entry: the 8
+//      corners of its rest box through its (body's) matrix,
+//      x' = fma(m0,x, fma(m1,y, fma(m2,z, m3))) per row; the union of the
+//      bodies' boxes gives the frame's shadow-ray lift eps = 1e-4 |hi - lo|;
+//      span = largest |coordinate| of that union and of the bodies' rest boxes
+//   2. the entries' boxes widened by 2^-10 (1 + span) on every side (the
+//      body-frame ray's rounding against the world box test), keyed by the
+//      30-bit Morton code of their centres (10 bits per axis) above the entry
+//      index,
 //      sorted (bitonic), Karras topology, node boxes by range union
 //   3. collapse into 4-wide nodes (thread 0, breadth first, opening the
-//      member of largest surface area), leaf links ~body
+//      member of largest surface area), leaf links ~entry
 // Also copies the matrices into the frame buffer (xfb).
 // ----------------------------------------------------------------------------
 struct TlasSmem {
@@ -713,7 +830,9 @@ __device__ __forceinline__ uint32_t spread10(uint32_t x) {
 
 __global__ void __launch_bounds__(1024) k_tlas(const float* __restrict__ xf, int nbody,
                                                const int32_t* __restrict__ blas_root,
-                                               const float4* __restrict__ body_box, Node4* __restrict__ tlas,
+                                               const float4* __restrict__ body_box,
+                                               const int32_t* __restrict__ inst,
+                                               const float4* __restrict__ inst_box, Node4* __restrict__ tlas,
                                                TlasInfo* __restrict__ info, float* __restrict__ xfb,
                                                uint32_t* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -721,24 +840,33 @@ __global__ void __launch_bounds__(1024) k_tlas(const float* __restrict__ xf, int
   const int tid = threadIdx.x;
   for (int i = tid; i < 12 * nbody; i += blockDim.x) xfb[i] = xf[i];
   if (tid < 8) S.red[tid] = tid < 3 ? 0xffffffffu : 0u;  // [0..2] min lo, [3..5] max hi, [6] span, [7] unused
-  const bool has = tid < nbody && blas_root[tid] >= 0;
-  float3 wlo = f3(0, 0, 0), whi = f3(0, 0, 0);
-  float rspan = 0.0f;
-  if (has) {
-    const float* m = xf + 12 * tid;
-    const float4 rl = body_box[2 * tid], rh = body_box[2 * tid + 1];
-    rspan = fmaxf(fmaxf(fmaxf(fabsf(rl.x), fabsf(rh.x)), fmaxf(fabsf(rl.y), fabsf(rh.y))),
-                  fmaxf(fabsf(rl.z), fabsf(rh.z)));
+  // world box of a rest box: its 8 corners through the matrix m
+  auto world_box = [](const float* m, float4 rl, float4 rh, float3& lo, float3& hi) {
     for (int c = 0; c < 8; ++c) {
       const float x = (c & 1) ? rh.x : rl.x, y = (c & 2) ? rh.y : rl.y, z = (c & 4) ? rh.z : rl.z;
       const float3 p = f3(fmaf(m[0], x, fmaf(m[1], y, fmaf(m[2], z, m[3]))),
                           fmaf(m[4], x, fmaf(m[5], y, fmaf(m[6], z, m[7]))),
                           fmaf(m[8], x, fmaf(m[9], y, fmaf(m[10], z, m[11]))));
-      wlo = c ? f3(fminf(wlo.x, p.x), fminf(wlo.y, p.y), fminf(wlo.z, p.z)) : p;
-      whi = c ? f3(fmaxf(whi.x, p.x), fmaxf(whi.y, p.y), fmaxf(whi.z, p.z)) : p;
+      lo = c ? f3(fminf(lo.x, p.x), fminf(lo.y, p.y), fminf(lo.z, p.z)) : p;
+      hi = c ? f3(fmaxf(hi.x, p.x), fmaxf(hi.y, p.y), fmaxf(hi.z, p.z)) : p;
     }
+  };
+  // the frame's union, lift and span come from the bodies' boxes (the
+  // instances of the method); the top level's leaves are the entries
+  const bool bhas = tid < nbody && blas_root[tid] >= 0;
+  float3 blo = f3(0, 0, 0), bhi = f3(0, 0, 0);
+  float rspan = 0.0f;
+  if (bhas) {
+    const float4 rl = body_box[2 * tid], rh = body_box[2 * tid + 1];
+    rspan = fmaxf(fmaxf(fmaxf(fabsf(rl.x), fabsf(rh.x)), fmaxf(fabsf(rl.y), fabsf(rh.y))),
+                  fmaxf(fabsf(rl.z), fabsf(rh.z)));
+    world_box(xf + 12 * tid, rl, rh, blo, bhi);
   }
-  // compaction: instance index = rank among the bodies with triangles
+  const int32_t eb = tid < kMaxTlasBodies ? inst[2 * tid + 1] : -1;  // the entry's body
+  const bool has = tid < kMaxTlasBodies && inst[2 * tid] >= 0 && eb >= 0 && eb < nbody;
+  float3 wlo = f3(0, 0, 0), whi = f3(0, 0, 0);
+  if (has) world_box(xf + 12 * eb, inst_box[2 * tid], inst_box[2 * tid + 1], wlo, whi);
+  // compaction: rank among the entries in use (the entries come first)
   S.scan[tid] = has ? 1 : 0;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {
@@ -748,13 +876,13 @@ __global__ void __launch_bounds__(1024) k_tlas(const float* __restrict__ xf, int
     __syncthreads();
   }
   const int ninst = S.scan[1023];
-  if (has) {
-    atomicMin(&S.red[0], f2ord(wlo.x));
-    atomicMin(&S.red[1], f2ord(wlo.y));
-    atomicMin(&S.red[2], f2ord(wlo.z));
-    atomicMax(&S.red[3], f2ord(whi.x));
-    atomicMax(&S.red[4], f2ord(whi.y));
-    atomicMax(&S.red[5], f2ord(whi.z));
+  if (bhas) {
+    atomicMin(&S.red[0], f2ord(blo.x));
+    atomicMin(&S.red[1], f2ord(blo.y));
+    atomicMin(&S.red[2], f2ord(blo.z));
+    atomicMax(&S.red[3], f2ord(bhi.x));
+    atomicMax(&S.red[4], f2ord(bhi.y));
+    atomicMax(&S.red[5], f2ord(bhi.z));
     atomicMax(&S.red[6], __float_as_uint(rspan));  // non-negative: bits order as values
   }
   __syncthreads();
@@ -1524,8 +1652,11 @@ int lbvh_build(fire_scene_s* s, cudaStream_t st) {
                            "copy"))
       return e;
     k_fill4<<<grid_for(s->n4, 256), 256, 0, st>>>(s->nodes, s->nodes4, s->n4);
-    if (s->two_level)
+    if (s->two_level) {
       k_body_boxes<<<grid_for(s->nbody, 256), 256, 0, st>>>(s->nodes4, s->n4, s->blas_root, s->nbody, s->body_box);
+      k_top_entries<<<1, kMaxTlasBodies, 0, st>>>(s->nodes4, s->n4, s->blas_root, s->body_box, s->nbody, s->inst,
+                                                  s->inst_box, s->ctrl + 8);
+    }
     if (int e = cuda_check(cudaGetLastError(), "4-wide tree")) return e;
     if (int e = cuda_check(cudaStreamSynchronize(st), "sync")) return e;  // lvl4 host vector copied
   }
@@ -1542,7 +1673,8 @@ int tlas_build(fire_scene_s* s, cudaStream_t st) {
   });
   if (int e = cuda_check(attr, "top-level shared memory")) return e;
   if (s->nbody > kMaxTlasBodies) return set_error(FIRE_ERR_INVALID_ARG, "two-level mode: too many bodies");
-  k_tlas<<<1, 1024, sizeof(TlasSmem), st>>>(s->xf, s->nbody, s->blas_root, s->body_box, s->tlas_buf[s->cur],
+  k_tlas<<<1, 1024, sizeof(TlasSmem), st>>>(s->xf, s->nbody, s->blas_root, s->body_box, s->inst, s->inst_box,
+                                            s->tlas_buf[s->cur],
                                             s->tinfo_buf[s->cur], s->xf_buf[s->cur], s->ctrl + 8);
   return cuda_check(cudaGetLastError(), "k_tlas");
 }

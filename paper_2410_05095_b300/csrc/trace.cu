@@ -25,7 +25,7 @@ namespace {
 // from the top level's record (single level: from the tree's root box).
 __device__ __forceinline__ Trace2View view2(const RenderArgs& a) {
   const TlasInfo ti = *a.tinfo;
-  return Trace2View{a.tlas, ti.n, a.nodes4, a.n4, a.tris, a.nt, a.blas_root, a.bxf, a.nbody, ti.span,
+  return Trace2View{a.tlas, ti.n, a.nodes4, a.n4, a.tris, a.nt, a.inst, kMaxTlasBodies, a.bxf, a.nbody, ti.span,
                     a.iter_cap, a.ctrl + 8};
 }
 __device__ __forceinline__ float frame_eps(const RenderArgs& a) {

@@ -2,11 +2,12 @@
 // per mesh built once, a top level over the instances rebuilt every frame),
 // and the hit frame of its triangles.
 //
-// The top level is searched with the world ray.  Reaching an instance (leaf
-// link ~body) turns the ray into the body's frame,
+// The top level is searched with the world ray.  Reaching an entry (leaf
+// link ~entry: a subtree of body b's bottom level) turns the ray into the
+// body's frame,
 //   o' = R^T (o - t_b),  d' = R^T d  (rows of R^T: the columns of the 3x4
 //   matrix, fmaf(m0, q.x, fmaf(m4, q.y, m8 q.z)) etc.),
-// pushes an exit marker and searches the body's bottom level (rest-pose
+// pushes an exit marker and searches the entry's subtree (rest-pose
 // triangle records) with it; popping the marker restores the world ray.
 // Hits rank by (t of the body-frame ray, original index), and a shadow ray's
 // hits count for t in (0, t_max) of the body-frame ray, the world t_max.
@@ -30,7 +31,8 @@ struct Trace2View {
   int64_t nblas;
   const float4* tris;     // rest-pose triangle records
   int64_t nt;
-  const int32_t* blas_root;  // [nbody]
+  const int32_t* inst;    // [2*ninst] top-level entries: (bottom-level node, body); node -1: unused
+  int ninst;
   const float* xf;        // [nbody*12] the frame's body matrices (16-B aligned)
   int nbody;
   float span;             // box-test slack scale (TlasInfo::span)
@@ -108,18 +110,18 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
       cur = stack[--sp];
       continue;
     }
-    if (!in_body && cur < 0) {  // enter instance ~cur
-      const int b = ~cur;
-      if (b < 0 || b >= c.nbody) {
+    if (!in_body && cur < 0) {  // enter top-level entry ~cur: a subtree of body b's bottom level
+      const int e = ~cur;
+      if (e < 0 || e >= c.ninst) {
         M::fail(c.err, kErrCorrupt);
         return false;
       }
-      const int root = M::i1(c.blas_root + b);
-      if (root < 0) {  // a body without triangles (never entered: it has no box)
+      const int root = M::i1(c.inst + 2 * e), b = M::i1(c.inst + 2 * e + 1);
+      if (root < 0) {  // an unused entry (never entered: it has no box)
         cur = stack[--sp];
         continue;
       }
-      if (root >= c.nblas) {
+      if (root >= c.nblas || b < 0 || b >= c.nbody) {
         M::fail(c.err, kErrCorrupt);
         return false;
       }

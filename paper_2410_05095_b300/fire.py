@@ -21,7 +21,7 @@ ERRORS = {-1: "FIRE_ERR_INVALID_ARG", -2: "FIRE_ERR_OOM", -3: "FIRE_ERR_CUDA",
 
 DUMP = {"morton": 0, "order": 1, "children": 2, "parent": 3, "boxes": 4, "tris": 5,
         "centroid_bounds": 6, "nodes4": 7, "blas_root": 8, "tlas": 9, "tlas_info": 10, "body_xforms": 11,
-        "shadow_rays": 12}
+        "shadow_rays": 12, "top_entries": 13}
 
 EXPORTS = ["fire_scene_create", "fire_scene_destroy", "fire_scene_set_materials", "fire_scene_info",
            "fire_bvh_build", "fire_bvh_refit", "fire_render", "fire_render_batch", "fire_shade",
@@ -60,6 +60,7 @@ class RenderOpts(C.Structure):
 
 
 GBUF_REC_BYTES = 16
+MAX_TOP_ENTRIES = 1024  # top-level entries of a two-level scene (its dump holds this many + 2 nodes)
 
 _lib = None
 
@@ -325,8 +326,9 @@ class Scene:
                   "children": (np.int32, (max(T - 1, 0), 2)), "parent": (np.int32, (max(2 * T - 1, 0),)),
                   "boxes": (np.float32, (max(2 * T - 1, 0), 6)), "tris": (np.float32, (T, 12)),
                   "centroid_bounds": (np.float32, (6,)), "nodes4": (np.float32, (self.info()["n4"], 32)),
-                  "blas_root": (np.int32, (nb,)), "tlas": (np.float32, (nb + 2, 32)),
-                  "tlas_info": (np.float32, (4,)), "body_xforms": (np.float32, (nb, 12))}
+                  "blas_root": (np.int32, (nb,)), "tlas": (np.float32, (MAX_TOP_ENTRIES + 2, 32)),
+                  "tlas_info": (np.float32, (4,)), "body_xforms": (np.float32, (nb, 12)),
+                  "top_entries": (np.int32, (MAX_TOP_ENTRIES, 2))}
         if what == "shadow_rays":
             shapes[what] = (np.float32, (self.render_info()["shadow_rays"], 8))
         dt, shp = shapes[what]

@@ -1,6 +1,7 @@
 """The two-level acceleration structure on the GPU (fire_scene_set_two_level:
 a bottom level per rigid body built once over the rest pose, a top level
-over the bodies rebuilt every frame, §IV-B-3) against the oracle's
+over subtrees of the bodies' bottom levels rebuilt every frame, §IV-B-3)
+against the oracle's
 two-level mode (bodies as instances of rest-space geometry, rays met in
 each body's frame).
 
@@ -62,7 +63,59 @@ def _segments(rng, n, lo, hi):
     return o, d, L
 
 
-# ------------------------------------------------------------- host emulation first
+# ------------------------------------------------------------- build, then host emulation
+def test_top_entries_cut_bodies(fb):
+    """The top level is built over subtrees of the bodies' bottom levels:
+    every triangle of a body lies under exactly one of that body's entries,
+    the entries come in body order within each body's share of the 1,024
+    slots (the unused slots after them), a body of spheres spread over the
+    scene gets more than one entry, and an entry's rest box holds its
+    subtree's triangles and is tight around them."""
+    w, _ = _moving(nspheres=40, cells=32, frames=1)
+    G = fb.Scene.from_numpy(w.scene)
+    G.set_two_level(True)
+    G.build(w.motion.xforms())
+    E, N, R = G.dump("top_entries"), G.dump("nodes4"), G.dump("tris")
+    roots, nb, nt = G.dump("blas_root"), G.nbody, G.nt
+    k = int((E[:, 0] >= 0).sum())
+    assert (E[:k] >= 0).all() and (E[k:] == -1).all()
+    assert np.all(np.diff(E[:k, 1]) >= 0)
+    share = max(1, min(64, 1024 // int((roots >= 0).sum())))
+    counts = np.bincount(E[:k, 1], minlength=nb)
+    assert counts.max() <= share and k > int((roots >= 0).sum())
+    assert np.array_equal(counts > 0, roots >= 0)
+    links = N[:, 24:28].copy().view(np.int32)
+    lo_n, hi_n = N[:, 0:12].reshape(-1, 3, 4), N[:, 12:24].reshape(-1, 3, 4)
+    body = R[:, 11].copy().view(np.int32)
+    v0 = R[:, 0:3].astype(np.float64)
+    tri_lo = np.minimum(v0, np.minimum(v0 + R[:, 4:7], v0 + R[:, 8:11]))
+    tri_hi = np.maximum(v0, np.maximum(v0 + R[:, 4:7], v0 + R[:, 8:11]))
+    seen = np.zeros(nt, np.int64)
+    box = {}  # rest box of each node from its parent's slot
+    for q in range(len(N)):
+        for c in range(4):
+            if links[q, c] >= 0:
+                box[int(links[q, c])] = (lo_n[q, :, c], hi_n[q, :, c])
+    for q, b in E[:k]:
+        stack, under = [int(q)], []
+        while stack:
+            v = stack.pop()
+            for l in links[v]:
+                if l == -2**31:
+                    continue
+                (under.append(~int(l)) if l < 0 else stack.append(int(l)))
+        under = np.array(under)
+        seen[under] += 1
+        assert (body[under] == b).all()
+        lo, hi = tri_lo[under].min(0), tri_hi[under].max(0)
+        tol = 1e-5 * (1.0 + np.abs(np.concatenate([lo, hi])).max())
+        if int(q) in box:
+            blo, bhi = box[int(q)]
+            assert (blo <= lo + tol).all() and (bhi >= hi - tol).all()
+            assert (np.abs(blo - lo) <= tol).all() and (np.abs(bhi - hi) <= tol).all()
+    assert (seen == 1).all()
+
+
 def test_emulated_traversal_matches_oracle(fb):
     """Built on the GPU (bottom levels at rest, top level for frame 3's
     poses), walked on the host by the render kernels' traversal code: every
