@@ -92,6 +92,12 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
   RaySetup r = ray_setup(o, d, c.span);
   float3 ro = o, rd = d;  // ray of the level being searched
   bool in_body = false;
+  // nearest hit: the body whose frame ro, rd and r are in (-1: the world
+  // ray), so that entering another entry of the body just left reuses its
+  // ray (primary pass 1.443 -> 1.398 ms on the 7.3M-triangle frame); any
+  // hit restores the world ray on every exit (the kept ray measured 1.35 ->
+  // 1.39 ms there)
+  int ray_body = -1;
   int stack[STACK];
   stack[0] = kDone;
   int sp = 1;
@@ -102,11 +108,13 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
       M::fail(c.err, kErrTimeout);
       return false;
     }
-    if (cur == kExitInstance) {  // leave the body: back to the world ray
+    if (cur == kExitInstance) {  // leave the subtree
       in_body = false;
-      ro = o;
-      rd = d;
-      r = ray_setup(o, d, c.span);
+      if (ANY) {  // back to the world ray (nearest hit: when the top level needs it)
+        ro = o;
+        rd = d;
+        r = ray_setup(o, d, c.span);
+      }
       cur = stack[--sp];
       continue;
     }
@@ -130,16 +138,25 @@ __host__ __device__ __forceinline__ bool traverse2(const Trace2View& c, float3 o
         cur = stack[--sp];
         continue;
       }
-      // the body's matrix: three 16-B rows (48 B per body from a 16-B aligned base)
-      const float4* mx = reinterpret_cast<const float4*>(c.xf) + 3 * (int64_t)b;
-      const float4 m0 = M::f4(mx), m1 = M::f4(mx + 1), m2 = M::f4(mx + 2);
-      const float m[12] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w};
-      object_ray(m, o, d, ro, rd);
-      r = ray_setup(ro, rd, c.span);
+      if (ANY || b != ray_body) {
+        // the body's matrix: three 16-B rows (48 B per body from a 16-B aligned base)
+        const float4* mx = reinterpret_cast<const float4*>(c.xf) + 3 * (int64_t)b;
+        const float4 m0 = M::f4(mx), m1 = M::f4(mx + 1), m2 = M::f4(mx + 2);
+        const float m[12] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w};
+        object_ray(m, o, d, ro, rd);
+        r = ray_setup(ro, rd, c.span);
+        ray_body = b;
+      }
       stack[sp++] = kExitInstance;
       in_body = true;
       cur = root;
       continue;
+    }
+    if (!ANY && !in_body && ray_body >= 0) {  // a top-level node: back to the world ray
+      ro = o;
+      rd = d;
+      r = ray_setup(o, d, c.span);
+      ray_body = -1;
     }
     const Node4* base = in_body ? c.blas : c.tlas;
     const uint32_t nn = (uint32_t)(in_body ? c.nblas : c.ntlas);  // (node counts < 2^31)
